@@ -1,0 +1,429 @@
+"""Pins of the oracle to things other than itself (closed forms, invariants,
+brute force, an independent ODE solver, statistics).
+
+Each test names what fixes the expected value.  Everything here is CPU-only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2607_24908_gb300.workloads import plane_wave, white_noise_state
+
+W1 = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
+W0 = -(2.0 ** (1.0 / 3.0)) / (2.0 - 2.0 ** (1.0 / 3.0))
+
+
+def lattice_omega2(p, n, m2):
+    """m^2 + sum_i (2/dx sin(k_i dx/2))^2 with k_i = kIR n_i (eigenvalue of
+    -Lap + m^2 on exp(i k.x))."""
+    return m2 + sum((2.0 / p.dx * math.sin(p.kIR * ni * p.dx / 2.0)) ** 2 for ni in n)
+
+
+# --- 1. exact discrete plane wave (free field) ------------------------------
+
+@pytest.mark.parametrize("integ", [o.VERLET, o.LEAPFROG])
+def test_plane_wave_exact_discrete_solution(integ):
+    """phi_n = A cos(k.x) cos(n W dt), pi_n = -A cos(k.x) sin(n W dt) sin(W dt)/dt,
+    cos(W dt) = 1 - dt^2 w_lat^2/2 (the leapfrog/VV recursion solved exactly)."""
+    p = o.Params(N=16, nf=1, kIR=0.5, lam=0.0, m2=(1.0, 0, 0))
+    n = (1, 2, 3)
+    dt, steps = 0.05, 400
+    phi0 = plane_wave(16, n)[None]
+    pi0 = np.zeros_like(phi0)
+    phi, pi, _, _ = o.run(p, phi0, pi0, 1.0, 0.0, dt, steps, integ)
+    w2 = lattice_omega2(p, n, 1.0)
+    Wdt = math.acos(1.0 - dt * dt * w2 / 2.0)
+    ex_phi = phi0 * math.cos(steps * Wdt)
+    ex_pi = -phi0 * math.sin(steps * Wdt) * math.sin(Wdt) / dt
+    assert np.max(np.abs(phi - ex_phi)) < 1e-12
+    assert np.max(np.abs(pi - ex_pi)) < 1e-12
+
+
+# --- 2. order of accuracy against the continuous-time solution --------------
+
+@pytest.mark.parametrize("integ,order", [(o.VERLET, 2), (o.YOSHIDA4, 4)])
+def test_convergence_order_plane_wave(integ, order):
+    """Semi-discrete exact solution A cos(k.x) cos(w_lat t); the error at fixed
+    T falls by 2^order per halving of dt (VV: 2, Yoshida-4: 4)."""
+    p = o.Params(N=16, nf=1, kIR=0.5, lam=0.0, m2=(1.0, 0, 0))
+    n = (1, 2, 3)
+    w = math.sqrt(lattice_omega2(p, n, 1.0))
+    phi0 = plane_wave(16, n)[None]
+    T = 2.0
+    errs = []
+    for dt in (0.1, 0.05):
+        phi, _, _, _ = o.run(p, phi0, np.zeros_like(phi0), 1.0, 0.0, dt, int(round(T / dt)), integ)
+        errs.append(np.max(np.abs(phi - phi0 * math.cos(w * T))))
+    ratio = errs[0] / errs[1]
+    assert 2 ** order * 0.8 < ratio < 2 ** order * 1.2, (errs, ratio)
+
+
+# --- 3. exact VV invariant per Fourier mode ----------------------------------
+
+def test_vv_modified_energy_per_mode():
+    """For VV on x'' = -w^2 x the quantity v^2/(2(1 - dt^2 w^2/4)) + w^2 x^2/2 is
+    conserved exactly; each lattice Fourier mode of a free field is such an
+    oscillator with w^2 = m^2 + sum_i (2/dx sin(pi n_i/N))^2."""
+    N, m2, dt = 8, 1.0, 0.1
+    p = o.Params(N=N, nf=1, kIR=0.5, lam=0.0, m2=(m2, 0, 0))
+    phi0, pi0 = white_noise_state(N, 1, seed=3, phi0=(0.0,), sigma_phi=1.0, sigma_pi=1.0)
+    phi, pi, _, _ = o.run(p, phi0, pi0, 1.0, 0.0, dt, 300, o.VERLET)
+    n = np.rint(np.fft.fftfreq(N, 1.0 / N))
+    nz, ny, nx = np.meshgrid(n, n, n, indexing="ij")
+    w2 = m2 + sum((2.0 / p.dx * np.sin(np.pi * c / N)) ** 2 for c in (nx, ny, nz))
+
+    def inv(f, g):
+        fh, gh = np.fft.fftn(f[0]), np.fft.fftn(g[0])
+        return np.abs(gh) ** 2 / (2.0 * (1.0 - dt * dt * w2 / 4.0)) + w2 * np.abs(fh) ** 2 / 2.0
+
+    I0, I1 = inv(phi0, pi0), inv(phi, pi)
+    assert np.max(np.abs(I1 - I0)) / np.max(I0) < 1e-12
+
+
+# --- 4. energy conservation at O(dt^2), static, coupled fields --------------
+
+@pytest.mark.parametrize("nf", [1, 2, 3])
+def test_energy_conservation_second_order(nf):
+    """Static background: the lattice Hamiltonian sum(K+G+V) is conserved up to
+    O(dt^2) oscillations; the max deviation shrinks 4x per dt halving.  A wrong
+    dV/dphi (sign, factor, coupling) breaks this."""
+    p = o.Params(N=8, nf=nf, kIR=0.5, lam=1.0, q=10.0, m2=(0.0, 0.5, 1.0)[:3])
+    phi0, pi0 = white_noise_state(8, nf, seed=5, phi0=(1.0, 0.5, 0.3), sigma_phi=0.1, sigma_pi=0.1)
+    T = 4.0
+    devs = []
+    for dt in (0.04, 0.02):
+        phi, pi = phi0, pi0
+        E0 = np.sum(o.energies(p, phi, pi))
+        dev = 0.0
+        for _ in range(int(round(T / dt))):
+            phi, pi, _, _ = o.run(p, phi, pi, 1.0, 0.0, dt, 1, o.VERLET)
+            dev = max(dev, abs(np.sum(o.energies(p, phi, pi)) - E0) / E0)
+        devs.append(dev)
+    assert devs[1] < 5e-3
+    assert 3.5 < devs[0] / devs[1] < 4.5, devs
+
+
+# --- 5. Hubble constraint at O(dt^2), expanding --------------------------------
+
+def _b0(p, phi, pi, a0=1.0):
+    E = o.energies(p, phi, pi, a0)
+    return a0 ** (1.0 + p.alpha) * math.sqrt(p.fstar_over_mp ** 2 * np.sum(E) / 3.0)
+
+
+@pytest.mark.parametrize("alpha,nf", [(0.0, 1), (1.0, 1), (1.0, 2), (2.0, 1)])
+def test_hubble_constraint_second_order(alpha, nf):
+    """(a'/a)^2 = a^(2 alpha) mu2 rho/3 holds at t=0 by construction and is
+    then preserved to O(dt^2) only if the field and scale-factor equations are
+    mutually consistent (every weight a^(..) and the (alpha-2, alpha,
+    alpha+1) coefficients)."""
+    p = o.Params(N=8, nf=nf, kIR=0.5, expanding=True, alpha=alpha, lam=1.0, q=10.0, m2=(0.2, 0.5, 0))
+    phi0, pi0 = white_noise_state(8, nf, seed=7, phi0=(1.0, 0.3), sigma_phi=0.1, sigma_pi=0.1)
+    b0 = _b0(p, phi0, pi0)
+    assert o.hubble_residual(p, o.energies(p, phi0, pi0, 1.0), 1.0, b0) < 1e-14
+    T = 2.0
+    res = []
+    for dt in (0.02, 0.01):
+        phi, pi, a, b = phi0, pi0, 1.0, b0
+        r = 0.0
+        for _ in range(int(round(T / dt))):
+            phi, pi, a, b = o.run(p, phi, pi, a, b, dt, 1, o.VERLET)
+            r = max(r, o.hubble_residual(p, o.energies(p, phi, pi, a), a, b))
+        res.append(r)
+    assert a > 1.2  # the box really expanded
+    assert res[1] < 1e-3
+    assert 3.3 < res[0] / res[1] < 4.7, res
+
+
+# --- 6. closed-form expansion: homogeneous kinetic domination ----------------
+
+@pytest.mark.parametrize("alpha", [0.0, 1.0, 3.0])
+def test_kinetic_domination_closed_form(alpha):
+    """V = 0, homogeneous field: pi = pi0 is constant and (a'/a)^2 =
+    a^(2 alpha) mu2 pi0^2/(6 a^6) integrates to a = (1 + (3-alpha) c eta)^(1/(3-alpha)),
+    phi = phi0 + pi0 ln(1 + (3-alpha) c eta)/((3-alpha) c) (alpha = 3: a = e^(c eta),
+    phi = phi0 + pi0 eta), c = mu pi0/sqrt(6)."""
+    p = o.Params(N=4, nf=1, kIR=0.5, expanding=True, alpha=alpha, lam=0.0, m2=(0.0, 0, 0))
+    phi0 = np.full((1, 4, 4, 4), 0.3)
+    pi0 = np.full((1, 4, 4, 4), 0.5)
+    b0 = _b0(p, phi0, pi0)
+    c = 0.5 / math.sqrt(6.0)
+    eta = 2.0
+    if alpha == 3.0:
+        a_ex, phi_ex = math.exp(c * eta), 0.3 + 0.5 * eta
+    else:
+        s = 3.0 - alpha
+        a_ex = (1.0 + s * c * eta) ** (1.0 / s)
+        phi_ex = 0.3 + 0.5 * math.log(1.0 + s * c * eta) / (s * c)
+    b_ex = c * a_ex ** (alpha - 2.0)
+    errs = []
+    for dt in (0.02, 0.01):
+        phi, pi, a, b = o.run(p, phi0, pi0, 1.0, b0, dt, int(round(eta / dt)), o.VERLET)
+        assert np.max(np.abs(pi - 0.5)) == 0.0
+        errs.append(max(abs(a - a_ex) / a_ex, abs(b - b_ex) / b_ex, abs(phi[0, 0, 0, 0] - phi_ex)))
+    assert errs[1] < 1e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
+# --- 7. time reversibility ------------------------------------------------------
+
+@pytest.mark.parametrize("integ", [o.VERLET, o.YOSHIDA4, o.LEAPFROG])
+def test_time_reversibility(integ):
+    """Symmetric schemes: n steps with dt then n with -dt return to the start."""
+    p = o.Params(N=8, nf=2, kIR=0.5, expanding=True, alpha=1.0, lam=1.0, q=50.0, m2=(0, 0.1, 0))
+    phi0, pi0 = white_noise_state(8, 2, seed=11, phi0=(1.0, 0.2), sigma_phi=0.1, sigma_pi=0.1)
+    b0 = _b0(p, phi0, pi0)
+    phi, pi, a, b = o.run(p, phi0, pi0, 1.0, b0, 0.01, 60, integ)
+    assert a > 1.1
+    phi, pi, a, b = o.run(p, phi, pi, a, b, -0.01, 60, integ)
+    assert np.max(np.abs(phi - phi0)) / np.max(np.abs(phi0)) < 1e-12
+    assert np.max(np.abs(pi - pi0)) / np.max(np.abs(pi0)) < 1e-12
+    assert abs(a - 1.0) < 1e-13 and abs(b - b0) / b0 < 1e-12
+
+
+# --- 8. brute force on 4^3 with dense matrices ---------------------------------
+
+def _dense_ops(N, dx):
+    """Forward-difference matrices D_i on the periodic N^3 grid ([z,y,x] order)
+    and the Laplacian built as -sum_i D_i^T D_i (summation by parts)."""
+    n3 = N ** 3
+    idx = lambda z, y, x: ((z % N) * N + (y % N)) * N + (x % N)
+    D = [np.zeros((n3, n3)) for _ in range(3)]
+    for z in range(N):
+        for y in range(N):
+            for x in range(N):
+                s = idx(z, y, x)
+                for i, t in enumerate((idx(z, y, x + 1), idx(z, y + 1, x), idx(z + 1, y, x))):
+                    D[i][s, t] += 1.0 / dx
+                    D[i][s, s] -= 1.0 / dx
+    Lap = -sum(Di.T @ Di for Di in D)
+    return D, Lap
+
+
+class _Dense:
+    """The model written independently with dense matrices (fields as [nf, n3])."""
+
+    def __init__(self, p):
+        self.p = p
+        self.D, self.Lap = _dense_ops(p.N, p.dx)
+
+    def dV(self, ph):
+        p = self.p
+        out = np.empty_like(ph)
+        others = np.sum(ph[1:] ** 2, axis=0)
+        out[0] = p.m2[0] * ph[0] + p.lam * ph[0] ** 3 + p.q * ph[0] * others
+        for f in range(1, p.nf):
+            out[f] = p.m2[f] * ph[f] + p.q * ph[0] ** 2 * ph[f]
+        return out
+
+    def V(self, ph):
+        p = self.p
+        v = sum(0.5 * p.m2[f] * ph[f] ** 2 for f in range(p.nf)) + 0.25 * p.lam * ph[0] ** 4
+        return v + 0.5 * p.q * ph[0] ** 2 * np.sum(ph[1:] ** 2, axis=0)
+
+    def F(self, ph, a):
+        al = self.p.alpha
+        return a ** (1 + al) * (ph @ self.Lap.T) - a ** (3 + al) * self.dV(ph)
+
+    def rho_parts(self, ph, pp, a):
+        K = 0.5 * a ** -6 * np.mean(pp ** 2)
+        G = 0.5 * a ** -2 * np.mean(sum((ph @ Di.T) ** 2 for Di in self.D)) * self.p.nf
+        V = np.mean(self.V(ph))
+        return K * self.p.nf, G, V
+
+    def Fb(self, ph, pp, a):
+        al, mu2 = self.p.alpha, self.p.fstar_over_mp ** 2
+        K, G, V = self.rho_parts(ph, pp, a)
+        return a ** (2 * al + 1) * mu2 / 3.0 * ((al - 2) * K + al * G + (al + 1) * V)
+
+    def vv(self, ph, pp, a, b, s):
+        b = b + s / 2 * self.Fb(ph, pp, a)
+        pp = pp + s / 2 * self.F(ph, a)
+        a1 = a + s * b
+        ph = ph + s * ((a + a1) / 2) ** (self.p.alpha - 3) * pp
+        pp = pp + s / 2 * self.F(ph, a1)
+        b = b + s / 2 * self.Fb(ph, pp, a1)
+        return ph, pp, a1, b
+
+    def rhs(self, t, y):
+        p, nf, n3 = self.p, self.p.nf, self.p.N ** 3
+        ph = y[:nf * n3].reshape(nf, n3)
+        pp = y[nf * n3:2 * nf * n3].reshape(nf, n3)
+        a, b = y[-2], y[-1]
+        dph = a ** (p.alpha - 3) * pp
+        dpp = self.F(ph, a)
+        return np.concatenate([dph.ravel(), dpp.ravel(), [b, self.Fb(ph, pp, a)]])
+
+
+def test_bruteforce_dense_4cubed():
+    """Oracle VV == the same VV on dense matrices (independent Laplacian built
+    from forward differences), expanding, two coupled fields."""
+    p = o.Params(N=4, nf=2, kIR=0.5, expanding=True, alpha=1.0, lam=1.0, q=20.0, m2=(0.1, 0.3, 0))
+    phi0, pi0 = white_noise_state(4, 2, seed=13, phi0=(1.0, 0.2), sigma_phi=0.2, sigma_pi=0.2)
+    b0 = _b0(p, phi0, pi0)
+    d = _Dense(p)
+    ph, pp, a, b = phi0.reshape(2, -1), pi0.reshape(2, -1), 1.0, b0
+    for _ in range(50):
+        ph, pp, a, b = d.vv(ph, pp, a, b, 0.02)
+    phi, pi, ao, bo = o.run(p, phi0, pi0, 1.0, b0, 0.02, 50, o.VERLET)
+    assert np.max(np.abs(phi.reshape(2, -1) - ph)) / np.max(np.abs(ph)) < 1e-13
+    assert np.max(np.abs(pi.reshape(2, -1) - pp)) / np.max(np.abs(pp)) < 1e-13
+    assert abs(ao - a) < 1e-13 and abs(bo - b) / abs(b) < 1e-12
+
+
+def test_yoshida_against_adaptive_ode_solver():
+    """Oracle Yoshida-4 solves the stated ODE system: compare with scipy's
+    DOP853 on the dense-matrix right-hand side (tight tolerances)."""
+    integrate = pytest.importorskip("scipy.integrate")
+    p = o.Params(N=4, nf=2, kIR=0.5, expanding=True, alpha=1.0, lam=1.0, q=20.0, m2=(0.1, 0.3, 0))
+    phi0, pi0 = white_noise_state(4, 2, seed=17, phi0=(1.0, 0.2), sigma_phi=0.2, sigma_pi=0.2)
+    b0 = _b0(p, phi0, pi0)
+    d = _Dense(p)
+    T = 1.0
+    y0 = np.concatenate([phi0.ravel(), pi0.ravel(), [1.0, b0]])
+    sol = integrate.solve_ivp(d.rhs, (0.0, T), y0, method="DOP853", rtol=1e-12, atol=1e-13)
+    yT = sol.y[:, -1]
+    n = 2 * 64
+    errs = []
+    for dt in (0.02, 0.01):
+        phi, pi, a, b = o.run(p, phi0, pi0, 1.0, b0, dt, int(round(T / dt)), o.YOSHIDA4)
+        errs.append(max(np.max(np.abs(phi.ravel() - yT[:n])), np.max(np.abs(pi.ravel() - yT[n:2 * n])),
+                        abs(a - yT[-2]), abs(b - yT[-1])))
+    assert errs[1] < 2e-4
+    assert 13.0 < errs[0] / errs[1] < 19.0, errs
+
+
+# --- 9. static background: alpha plays no role; LF == VV --------------------------
+
+def test_static_alpha_independence_and_leapfrog_equals_verlet():
+    phi0, pi0 = white_noise_state(8, 2, seed=19, phi0=(1.0, 0.1), sigma_phi=0.1, sigma_pi=0.1)
+    runs = []
+    for alpha in (0.0, 1.0, 3.0):
+        p = o.Params(N=8, nf=2, kIR=0.5, alpha=alpha, lam=1.0, q=100.0)
+        runs.append(o.run(p, phi0, pi0, 1.0, 0.0, 0.01, 40, o.VERLET))
+    for r in runs[1:]:
+        assert np.array_equal(r[0], runs[0][0]) and np.array_equal(r[1], runs[0][1])
+    p = o.Params(N=8, nf=2, kIR=0.5, lam=1.0, q=100.0)
+    lf = o.run(p, phi0, pi0, 1.0, 0.0, 0.01, 40, o.LEAPFROG)
+    assert np.max(np.abs(lf[0] - runs[0][0])) < 1e-13
+    assert np.max(np.abs(lf[1] - runs[0][1])) < 1e-12
+
+
+def test_leapfrog_equals_verlet_expanding():
+    p = o.Params(N=8, nf=1, kIR=0.5, expanding=True, alpha=1.0, lam=1.0)
+    phi0, pi0 = white_noise_state(8, 1, seed=23, sigma_phi=0.1, sigma_pi=0.1)
+    b0 = _b0(p, phi0, pi0)
+    vv = o.run(p, phi0, pi0, 1.0, b0, 0.01, 50, o.VERLET)
+    lf = o.run(p, phi0, pi0, 1.0, b0, 0.01, 50, o.LEAPFROG)
+    assert np.max(np.abs(lf[0] - vv[0])) < 1e-13
+    assert np.max(np.abs(lf[1] - vv[1])) < 1e-12
+    assert abs(lf[2] - vv[2]) < 1e-14 and abs(lf[3] - vv[3]) < 1e-13
+
+
+# --- 10. energies of a plane wave in closed form -----------------------------------
+
+def test_energies_plane_wave_closed_form():
+    """phi = A cos(k.x), pi = B cos(k.x): <pi^2> = B^2/2, <(grad+ phi)^2> =
+    A^2 sum_i (2 sin(k_i dx/2)/dx)^2 / 2, <cos^4> = 3/8; with a != 1 the
+    weights a^-6 (K) and a^-2 (G)."""
+    N = 16
+    n = (1, 2, 3)
+    A, B, a = 0.7, 0.4, 1.3
+    p = o.Params(N=N, nf=1, kIR=0.5, expanding=True, alpha=1.0, lam=2.0, m2=(1.5, 0, 0))
+    phi = plane_wave(N, n, A)[None]
+    pi = plane_wave(N, n, B)[None]
+    K, G, V = o.energies(p, phi, pi, a)
+    kg2 = lattice_omega2(p, n, 0.0)
+    assert abs(K - 0.5 * a ** -6 * B * B / 2) < 1e-15
+    assert abs(G - 0.5 * a ** -2 * A * A * kg2 / 2) < 1e-14
+    assert abs(V - (1.5 * A * A / 4 + 2.0 * A ** 4 * 3.0 / 32.0)) < 1e-14
+
+
+# --- 11. initial Gaussian random field: statistics fixed by its definition -------
+
+def test_initial_field_spectrum_and_variance():
+    """Each live mode pair has <|d|^2> = P(k)/L^3 with P = A/(2 omega_k):
+    shell means of the measured spectrum match the shell mean of P within
+    4 sigma (|d|^2 is exponential; pairs are copies, so count/2 draws);
+    the field variance matches sum_n P(k_n)/L^3; the field is real."""
+    N, A, m2 = 32, 1e-10, 3.0
+    p = o.Params(N=N, nf=1, kIR=0.5)
+    Pk = lambda k: A / (2.0 * np.sqrt(k * k + m2))
+    d = o.gaussian_modes(N, p.kIR, Pk, seed=1, stream=0)
+    assert np.max(np.abs(np.fft.ifftn(d).imag)) < 1e-14 * np.max(np.abs(np.fft.ifftn(d).real))
+    f = o.modes_to_field(d)
+    k, P, cnt = o.spectrum(p, f)
+    n = np.rint(np.fft.fftfreq(N, 1.0 / N))
+    nz, ny, nx = np.meshgrid(n, n, n, indexing="ij")
+    r = np.sqrt(nx ** 2 + ny ** 2 + nz ** 2).ravel()
+    b = np.floor(r + 0.5).astype(int)
+    expect = np.bincount(b, weights=Pk(p.kIR * r) * ((r > 0) & (r < N / 2)), minlength=len(P)) / np.maximum(cnt, 1)
+    for bb in range(1, N // 2 - 1):
+        sig = math.sqrt(2.0 / cnt[bb])
+        assert abs(P[bb] / expect[bb] - 1.0) < 4 * sig, (bb, P[bb] / expect[bb], sig)
+    z = (P[1:N // 2 - 1] / expect[1:N // 2 - 1] - 1.0) / np.sqrt(2.0 / cnt[1:N // 2 - 1])
+    assert abs(np.mean(z)) < 4.0 / math.sqrt(len(z))
+    var_expect = np.sum(Pk(p.kIR * r[(r > 0) & (r < N / 2)])) / p.L ** 3
+    assert abs(np.var(f) / var_expect - 1.0) < 0.05
+    assert abs(np.mean(f)) < 1e-20  # k = 0 excluded
+    assert P[0] < 1e-30
+
+
+def test_init_fluctuations_two_fields_independent_and_b0():
+    p = o.Params(N=16, nf=2, kIR=0.5, expanding=True, alpha=1.0, lam=1.0, q=100.0)
+    spec = o.InitSpec(A=1e-10, meff2=(3.0, 100.0, 0), phi0=(1.0, 0.0, 0))
+    phi, pi, a0, b0 = o.init_fluctuations(p, 7, spec)
+    d0, d1 = phi[0] - 1.0, phi[1]
+    corr = np.sum(d0 * d1) / math.sqrt(np.sum(d0 * d0) * np.sum(d1 * d1))
+    assert abs(corr) < 0.05
+    assert np.std(d1) < np.std(d0)  # heavier field, smaller vacuum amplitude
+    assert o.hubble_residual(p, o.energies(p, phi, pi, a0), a0, b0) < 1e-14
+    phi2, _, _, _ = o.init_fluctuations(p, 7, spec)
+    phi3, _, _, _ = o.init_fluctuations(p, 8, spec)
+    assert np.array_equal(phi, phi2) and not np.array_equal(phi, phi3)
+
+
+# --- 12. spectrum estimator ------------------------------------------------------------
+
+def test_spectrum_single_mode_closed_form_and_parseval():
+    """cos(k.x) puts |d|^2 = 1/4 on n and -n; bin round(|n|) = 4 for n=(1,2,3);
+    P_4 = L^3 (2/4)/count_4.  Parseval: sum_b P_b count_b / L^3 = <f^2>."""
+    N = 16
+    p = o.Params(N=N, nf=1, kIR=0.5)
+    f = plane_wave(N, (1, 2, 3), 1.0) + 0.25
+    k, P, cnt = o.spectrum(p, f)
+    assert round(math.sqrt(14)) == 4
+    assert abs(P[4] - p.L ** 3 * 0.5 / cnt[4]) < 1e-12 * P[4]
+    assert abs(P[0] - p.L ** 3 * 0.0625) < 1e-12
+    others = [bb for bb in range(len(P)) if bb not in (0, 4)]
+    assert np.max(P[others]) < 1e-25
+    assert abs(np.sum(P * cnt) / p.L ** 3 - np.mean(f * f)) < 1e-13
+    assert cnt.sum() == N ** 3
+    # bin 1 holds |n| = 1 (6 modes) and |n| = sqrt(2) (12 modes)
+    assert cnt[1] == 18
+    assert abs(k[1] - p.kIR * (6 + 12 * math.sqrt(2)) / 18) < 1e-15
+
+
+# --- 13. Philox-2x64-10: statistics only (parity unpinned against a KAT) -------------
+
+def test_philox_uniform_statistics():
+    n = 200_000
+    w = o.philox2x64(np.arange(n, dtype=np.uint64), 0, 12345)
+    u = (w >> np.uint64(11)).astype(np.float64) / 2.0 ** 53
+    for col in (0, 1):
+        x = u[:, col]
+        assert abs(x.mean() - 0.5) < 4 * math.sqrt(1 / 12 / n)
+        assert abs(x.var() - 1 / 12) < 0.005
+        h, _ = np.histogram(x, bins=64, range=(0, 1))
+        chi2 = np.sum((h - n / 64) ** 2 / (n / 64))
+        assert chi2 < 63 + 6 * math.sqrt(2 * 63)
+    c = np.corrcoef(u[:-1, 0], u[1:, 0])[0, 1]
+    assert abs(c) < 5 / math.sqrt(n)
+    c2 = np.corrcoef(u[:, 0], u[:, 1])[0, 1]
+    assert abs(c2) < 5 / math.sqrt(n)
+    # every counter word, the second counter word and the key change the output
+    w2 = o.philox2x64(np.arange(n, dtype=np.uint64), 1, 12345)
+    w3 = o.philox2x64(np.arange(n, dtype=np.uint64), 0, 12346)
+    assert not np.any(np.all(w == w2, axis=1)) and not np.any(np.all(w == w3, axis=1))
+    assert len(np.unique(w[:, 0])) == n
