@@ -1,0 +1,329 @@
+"""Throughput of the fused lattice step on one GB300 (per rank).
+
+Workload: phi^4 + (q/2) phi^2 chi^2, q = 100, two fields, 1024^3 sites,
+kIR = 0.05, expanding (alpha = 1, fstar/m_p = 1), 4th-order Yoshida,
+dt = 0.005, FP32 fields and momenta with FP64 energy reductions, initial
+state phi = 1, chi = 0 plus Gaussian fluctuations with power A/(2 omega_k),
+A = 1e-10 (drawn on the device).  One bench step = one Yoshida step =
+three fused passes.  The state (32 GiB) is far larger than L2, so no flush
+is needed between timed iterations.
+
+Metric: site-updates/s per field = N^3 * n_fields * passes / s (a pass is
+one force evaluation: 1 per leapfrog/Verlet step, 3 per Yoshida step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With torchrun (N > 1) every rank runs its own replica (the path has no
+exchange step on one lattice per GPU), so value = sum over ranks (weak).
+``--impl reference`` times the FP64 CPU oracle on the host cores instead, on
+a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2607_24908_gb300.workloads import TWO_FIELD_1024 as WL  # noqa: E402
+
+METRIC = "site-updates/s per field"
+PASSES = {"leapfrog": 1, "verlet": 1, "yoshida4": 3}[WL.integrator]
+BYTES_PER_SITE_FIELD_PASS = 4 * (4 if WL.dtype == "f32" else 8)  # read phi, pi; write phi, pi
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_pass_1024cubed_2f_f32.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2607_24908_gb300", "csrc", "tl_pass.cu")
+
+
+def kernel_hash() -> str:
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    try:
+        txt = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    h = re.search(r"kernel source sha256\[:16\]:\s*([0-9a-f]+)", txt)
+    b = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
+    if not h or not b or h.group(1) != kernel_hash():
+        return None
+    return float(b.group(1))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------------
+# CPU oracle leg (reported baseline / --impl reference)
+# ---------------------------------------------------------------------------------
+
+def oracle_sample(seconds_target: float = 15.0, max_steps: int = 1000):
+    """Time the FP64 oracle on host cores on a bounded sample of the workload:
+    same model, dt and integrator on a 96^3 two-field lattice."""
+    import oracle as o
+    n = 96
+    p = o.Params(N=n, nf=WL.nf, kIR=WL.kIR * WL.N / n, expanding=WL.expanding, alpha=WL.alpha,
+                 fstar_over_mp=WL.fstar_over_mp, lam=WL.lam, q=WL.q, m2=WL.m2)
+    spec = o.InitSpec(A=WL.A, meff2=WL.meff2, phi0=WL.phi0)
+    phi, pi, a, b = o.init_fluctuations(p, WL.seed, spec)
+    integ = {"leapfrog": o.LEAPFROG, "verlet": o.VERLET, "yoshida4": o.YOSHIDA4}[WL.integrator]
+    t0 = time.perf_counter()
+    phi, pi, a, b = o.run(p, phi, pi, a, b, WL.dt, 1, integ)
+    one = time.perf_counter() - t0
+    steps = max(1, min(max_steps, int(seconds_target / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    o.run(p, phi, pi, a, b, WL.dt, steps, integ)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = n ** 3 * WL.nf * PASSES * steps / el
+    return {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{n}^3 x {WL.nf} fields, same model/dt/{WL.integrator}, FP64, {steps} steps in {el:.1f} s "
+                      f"(OpenMP {cores} threads)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as o
+    n = 96
+    p = o.Params(N=n, nf=WL.nf, kIR=WL.kIR * WL.N / n, expanding=WL.expanding, alpha=WL.alpha,
+                 fstar_over_mp=WL.fstar_over_mp, lam=WL.lam, q=WL.q, m2=WL.m2)
+    phi, pi, a, b = o.init_fluctuations(p, WL.seed, o.InitSpec(A=WL.A, meff2=WL.meff2, phi0=WL.phi0))
+    integ = {"leapfrog": o.LEAPFROG, "verlet": o.VERLET, "yoshida4": o.YOSHIDA4}[WL.integrator]
+    for _ in range(args.warmup):
+        phi, pi, a, b = o.run(p, phi, pi, a, b, WL.dt, 1, integ)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        phi, pi, a, b = o.run(p, phi, pi, a, b, WL.dt, 1, integ)
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = n ** 3 * WL.nf * PASSES * args.steps / el
+    sample = f"{n}^3 x {WL.nf} fields per step (bounded sample of {WL.N}^3), FP64, OpenMP {cores} threads"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WL.name, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    from paper_2607_24908_gb300 import tl as T
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    integ = T.INTEGRATORS[WL.integrator]
+    lat = T.Lattice(WL.N, WL.kIR, WL.nf, WL.dtype, WL.expanding, WL.alpha, WL.fstar_over_mp, 1.0, stream=sptr)
+    lat.set_potential(WL.lam, WL.q, WL.m2)
+    lat.init_fluctuations(WL.seed + 1000 * rank, A=WL.A, meff2=WL.meff2, phi0=WL.phi0)
+
+    # warm-up: W steps (one call each)
+    for _ in range(args.warmup):
+        lat.step(1, WL.dt, integ)
+    lat.energies()
+    barrier()
+
+    # device-timed region: exactly K steps in one call (3K+1 fused passes)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    ev0.record(stream)
+    lat.step(args.steps, WL.dt, integ)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    E = lat.energies()
+    launches = PASSES * args.steps + 1
+    ms_pass = ms / launches
+
+    t_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    sites = WL.N ** 3
+    work_per_rank = sites * WL.nf * PASSES * args.steps
+    value = work_per_rank * ws / (t_max / 1e3)
+
+    # end-to-end through the C ABI with host buffers: H2D of the state from
+    # pinned memory, K steps, energies and D2H of the state, every call inside
+    # the timed region.
+    npd = np.float32 if WL.dtype == "f32" else np.float64
+    host = [torch.empty((WL.N,) * 3, dtype=torch.float32 if WL.dtype == "f32" else torch.float64,
+                        pin_memory=True) for _ in range(2 * WL.nf)]
+    for f in range(WL.nf):
+        for w in range(2):
+            T.tl_get_state(lat.h, f, w, host[2 * f + w].numpy())
+    barrier()
+    t0 = time.perf_counter()
+    for f in range(WL.nf):
+        for w in range(2):
+            T.tl_set_state(lat.h, f, w, host[2 * f + w].numpy())
+    T.tl_set_background(lat.h, E.a, E.b, False)
+    lat.step(args.steps, WL.dt, integ)
+    E2 = lat.energies()
+    for f in range(WL.nf):
+        for w in range(2):
+            T.tl_get_state(lat.h, f, w, host[2 * f + w].numpy())
+    t_e2e = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    state_bytes = 2 * WL.nf * sites * np.dtype(npd).itemsize
+    e2e_value = work_per_rank * ws / t_e2e
+    lat.close()
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        alg_bytes = sites * WL.nf * BYTES_PER_SITE_FIELD_PASS
+        achieved = alg_bytes / (ms_pass / 1e3) / 1e9
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            cpu = oracle_sample()
+        line = {
+            "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": WL.dtype, "data": "synthetic",
+            "config": {"workload": WL.name, "N": WL.N, "n_fields": WL.nf, "integrator": WL.integrator,
+                       "passes_per_step": PASSES, "dt": WL.dt, "storage": "fp32 fields/momenta, fp64 reductions",
+                       "l2": "inputs (32 GiB state) larger than L2; no flush", "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": measured_traffic(), "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel": "fused_pass<float,2>", "ms_per_launch": ms_pass},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": state_bytes / args.steps,
+                    "d2h_bytes_per_step": (state_bytes + 136) / args.steps,
+                    "note": "state H2D once, K steps, energies + state D2H, per K-step job"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "physics": {"a": E.a, "hubble_resid": E.hubble_resid, "a_after_e2e": E2.a},
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: warm-up raised to the minimum of 3 steps", file=sys.stderr)
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

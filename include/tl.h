@@ -1,0 +1,185 @@
+/*
+ * tl.h -- C ABI of the GB300 lattice stepper for interacting scalar fields on
+ * a periodic 3D lattice in an expanding (FLRW) background.
+ *
+ * Model (program variables, tildes dropped; the paper prints the static phi^4
+ * kick/drift of Sec. 4, the rest is the standard scalar field in FLRW written
+ * in the alpha time variable):
+ *   - N^3 sites, periodic, spacing dx = 2 pi/(kIR N), row-major with x
+ *     fastest (the paper keeps row-major layout on every device, Sec. 3.3);
+ *   - fields phi_f (f < n_fields <= 3) with momenta pi_f = a^(3-alpha) phi_f';
+ *   - phi' = a^(alpha-3) pi,  pi' = a^(1+alpha) Lap phi - a^(3+alpha) dV/dphi,
+ *     Lap the 7-point lattice Laplacian (Sec. 2 "LatLapl", Sec. 4);
+ *   - V = sum_f m_f^2 phi_f^2/2 + lambda phi_0^4/4 + (q/2) phi_0^2 sum_{f>0} phi_f^2;
+ *   - a'' = a^(2 alpha+1) (mu2/3) [(alpha-2) K + alpha G + (alpha+1) V],
+ *     mu2 = (fstar/m_p)^2, with the volume averages
+ *     K_f = a^-6 <pi_f^2>/2,  G_f = a^-2 <sum_i (forward difference)^2>/2,
+ *     V = <V(phi)> (the paper's "average", Sec. 2 and Sec. 3.2);
+ *   - Hubble constraint (a'/a)^2 = a^(2 alpha) mu2 (K+G+V)/3.
+ *
+ * Conventions (every function):
+ *   - returns TL_OK (0) or a negative TL_E* code; tl_last_error() then gives
+ *     a message (thread-local, valid until the next call on that thread);
+ *   - host pointers are borrowed for the duration of the call;
+ *   - device memory is owned by the lattice (tl_lattice_create) or by the
+ *     caller (tl_lattice_create_with_buffers, which must keep it alive);
+ *   - all device work is ordered on the lattice's CUDA stream; calls that
+ *     return host data (tl_energies, tl_spectrum, tl_get_state) synchronise
+ *     that stream, the others only enqueue work;
+ *   - one lattice must not be used from two threads at once; distinct
+ *     lattices are independent.
+ */
+#ifndef TL_H
+#define TL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TL_MAX_FIELDS 3
+
+/* Error codes. */
+#define TL_OK 0
+#define TL_EINVAL (-1)    /* bad argument (size, enum, pointer, field index) */
+#define TL_ENOMEM (-2)    /* device allocation failed or would exceed the budget */
+#define TL_ECUDA (-3)     /* a CUDA or cuFFT call failed */
+#define TL_EUNSTABLE (-4) /* a reduced energy became non-finite (reported at the next sync) */
+#define TL_ETIMEOUT (-5)  /* a bounded device wait expired */
+#define TL_ESTATE (-6)    /* call out of order (e.g. stepping before a potential and a state exist) */
+
+typedef struct tl_lattice tl_lattice; /* opaque, owned by the library */
+
+typedef enum { TL_F32 = 0, TL_F64 = 1 } tl_dtype;
+
+/* TL_LEAPFROG is the paper's kick-then-drift with half-step momenta (Sec. 4);
+ * TL_VERLET the palindromic velocity Verlet; both advance phi identically and
+ * run one fused pass per step.  TL_YOSHIDA4 composes three Verlet substeps
+ * with weights w1, w0, w1 (w1 = 1/(2-2^(1/3)), w0 = -2^(1/3) w1): three
+ * passes per step. */
+typedef enum { TL_LEAPFROG = 0, TL_VERLET = 1, TL_YOSHIDA4 = 2 } tl_integrator;
+
+/* Background.  expanding = 0: static box, a = 1, b = a' = 0, alpha unused. */
+typedef struct {
+    int expanding;
+    double alpha;         /* d eta = a^-alpha dt */
+    double fstar_over_mp; /* sets mu2 = fstar_over_mp^2 */
+    double a0;            /* scale factor at initialisation (tl_init_fluctuations) */
+} tl_expansion;
+
+/* Potential family above.  Fields beyond n_fields are ignored. */
+typedef struct {
+    double lambda;
+    double q;
+    double m2[TL_MAX_FIELDS];
+} tl_potential;
+
+/* Initial state for tl_init_fluctuations: homogeneous values plus a Gaussian
+ * random field per field f.  Every mode n (k = kIR n) with 0 < |n| < N/2 gets
+ * <|d(n)|^2> = P(k)/L^3, P(k) = A/(2 omega_k), omega_k^2 = k^2 + meff2[f]:
+ * Rayleigh modulus, uniform phase, Hermitian pairs, drawn with Philox-2x64-10
+ * (the paper's generator, Sec. 2) from counter (mode index, f) and key seed.
+ * fluct_pi != 0 adds an independent draw with P = A omega_k/2 to pi_f
+ * (counter (mode index, 8+f)), scaled by a0^(3-alpha). */
+typedef struct {
+    double A;
+    double meff2[TL_MAX_FIELDS];
+    double phi0[TL_MAX_FIELDS];
+    double pi0[TL_MAX_FIELDS];
+    int fluct_pi;
+} tl_init_spec;
+
+/* Volume averages and background at the last integer time. */
+typedef struct {
+    int64_t step;       /* completed time steps since the last init/set_state */
+    double time;        /* program time eta since then */
+    double a, b;        /* scale factor and a' */
+    double K[TL_MAX_FIELDS], G[TL_MAX_FIELDS], V;
+    double hubble_resid; /* |(b/a)^2 - a^(2 alpha) mu2 (K+G+V)/3| / (b/a)^2; 0 if static */
+} tl_energies_t;
+
+/* Create a lattice and allocate its device state (4 n_fields arrays of N^3
+ * elements: phi and pi, ping-pong, plus O(grid) scratch for the fused
+ * reductions).  N >= 8 and N % 4 == 0; 1 <= n_fields <= 3; kIR > 0;
+ * expansion may be NULL (static).  cuda_stream is a cudaStream_t (NULL: the
+ * legacy default stream).  The lattice needs a potential
+ * (tl_set_potential) and a state (tl_init_fluctuations or tl_set_state)
+ * before tl_step.  Errors: TL_EINVAL, TL_ENOMEM, TL_ECUDA. */
+int tl_lattice_create(tl_lattice **out, int N, double kIR, int n_fields, tl_dtype dtype,
+                      const tl_expansion *expansion, void *cuda_stream);
+
+/* As tl_lattice_create, but the 4 n_fields field arrays live in caller-owned
+ * device memory: dev_ptrs[4 f + 0] phi_f (A), [4 f + 1] pi_f (A),
+ * [4 f + 2] phi_f (B), [4 f + 3] pi_f (B); each N^3 elements of dtype,
+ * 16-byte aligned; n_ptrs == 4 n_fields. */
+int tl_lattice_create_with_buffers(tl_lattice **out, int N, double kIR, int n_fields, tl_dtype dtype,
+                                   const tl_expansion *expansion, void *cuda_stream,
+                                   void *const *dev_ptrs, size_t n_ptrs);
+
+/* Device bytes tl_lattice_create would allocate for the field arrays. */
+size_t tl_state_bytes(int N, int n_fields, tl_dtype dtype);
+
+void tl_lattice_destroy(tl_lattice *lat);
+
+/* Set the potential (may be changed between steps). */
+int tl_set_potential(tl_lattice *lat, const tl_potential *pot);
+
+/* Draw the initial state (see tl_init_spec), set a = a0 and, when expanding,
+ * b = a0^(1+alpha) sqrt(mu2 rho0/3) with rho0 the lattice-averaged K+G+V of
+ * that state.  Uses cuFFT (c2r, FP64) and temporary device memory of about
+ * 16 N^3 bytes.  Resets step and time to 0. */
+int tl_init_fluctuations(tl_lattice *lat, uint64_t seed, const tl_init_spec *spec);
+
+/* Advance n >= 0 steps of size dt (negative dt runs backwards).  The state
+ * stays resident; the call only enqueues work: n P + 1 fused passes (P = 1
+ * for leapfrog/Verlet, 3 for Yoshida), each one kernel that drifts phi,
+ * applies the Laplacian, dV/dphi and the expansion-weighted kick, and reduces
+ * K, G, V, followed in-kernel by the FP64 scale-factor update.  A non-finite
+ * energy is reported by the next tl_energies / tl_get_state as TL_EUNSTABLE.
+ * Errors: TL_EINVAL, TL_ESTATE, TL_ECUDA. */
+int tl_step(tl_lattice *lat, int n, double dt, tl_integrator integrator);
+
+/* Synchronise the lattice stream and return the energies at the current
+ * integer time (measured on the device if the state was set since the last
+ * step). */
+int tl_energies(tl_lattice *lat, tl_energies_t *out);
+
+/* Number of spectrum bins for size N: ceil(sqrt(3) N/2) + 1. */
+int tl_spectrum_bins(int N);
+
+/* Binned power spectrum of phi_field (which = 0) or pi_field (which = 1):
+ * d(n) = N^-3 sum_x f(x) exp(-i k.x), bin b = floor(|n| + 1/2),
+ * P_b = L^3 mean_{n in b} |d(n)|^2, k_b = kIR mean_{n in b} |n|, count_b =
+ * modes in the bin (all N^3 modes, both members of each pair).  Host arrays
+ * of nbins >= tl_spectrum_bins(N) entries; any may be NULL.  Bin sums use
+ * FP64 atomics (reproducible to rounding, not bitwise).  Synchronises. */
+int tl_spectrum(tl_lattice *lat, int field, int which, int nbins, double *k, double *P, int64_t *count);
+
+/* Copy phi_field (which = 0) or pi_field (which = 1) at the current integer
+ * time to host memory of bytes = N^3 * element size ([z][y][x], x fastest).
+ * Synchronises.  TL_EUNSTABLE if the evolution went non-finite. */
+int tl_get_state(tl_lattice *lat, int field, int which, void *host, size_t bytes);
+
+/* Overwrite phi_field or pi_field from host memory (same layout and size as
+ * tl_get_state).  Resets step and time to 0; the energies are re-measured
+ * on demand.  Call tl_set_background afterwards when expanding. */
+int tl_set_state(tl_lattice *lat, int field, int which, const void *host, size_t bytes);
+
+/* Set the scale factor a and a' = b; from_constraint != 0 ignores b and sets
+ * b = a^(1+alpha) sqrt(mu2 rho/3) from the current state's energies. */
+int tl_set_background(tl_lattice *lat, double a, double b, int from_constraint);
+
+/* Device address of phi_field / pi_field of the current state (valid until
+ * the next tl_step). */
+int tl_state_device_ptr(tl_lattice *lat, int field, int which, void **dev_ptr);
+
+/* Message for the last error on this thread ("" if none). */
+const char *tl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TL_H */

@@ -299,3 +299,50 @@ def spectrum(p: Params, f3: np.ndarray):
     P[nz_] = p.L ** 3 * ps[nz_] / cnt[nz_]
     k[nz_] = p.kIR * rs[nz_] / cnt[nz_]
     return k, P, cnt.astype(np.int64)
+
+
+# ---- one step at sampled sites (full-size parity) ------------------------------
+
+def _dV_np(p: Params, v):
+    """dV/dphi_f for stacked site values v[..., f] (same potential as tlo.c)."""
+    out = np.empty_like(v)
+    others = np.sum(v[..., 1:] ** 2, axis=-1) if p.nf > 1 else 0.0
+    out[..., 0] = p.m2[0] * v[..., 0] + p.lam * v[..., 0] ** 3 + p.q * v[..., 0] * others
+    for f in range(1, p.nf):
+        out[..., f] = p.m2[f] * v[..., f] + p.q * v[..., 0] ** 2 * v[..., f]
+    return out
+
+
+def _patch_force(p: Params, ph):
+    """F on the interior of a patch ph[S, nf, n, n, n] -> [S, nf, n-2, n-2, n-2] (a == 1)."""
+    c = ph[:, :, 1:-1, 1:-1, 1:-1]
+    lap = ((ph[:, :, 1:-1, 1:-1, 2:] + ph[:, :, 1:-1, 1:-1, :-2] - 2.0 * c)
+           + (ph[:, :, 1:-1, 2:, 1:-1] + ph[:, :, 1:-1, :-2, 1:-1] - 2.0 * c)
+           + (ph[:, :, 2:, 1:-1, 1:-1] + ph[:, :, :-2, 1:-1, 1:-1] - 2.0 * c)) / p.dx ** 2
+    dv = np.moveaxis(_dV_np(p, np.moveaxis(c, 1, -1)), -1, 1)
+    return lap - dv
+
+
+def vv_step_at_sites(p: Params, phi, pi, sites, dt: float):
+    """One velocity-Verlet step in a static background, evaluated only at the
+    given sites (z, y, x): the same operator sequence as tlo.c on the 5^3
+    periodic neighbourhood each output depends on.  phi, pi: [nf, N, N, N]
+    arrays (any float dtype; promoted to FP64).  Returns (phi1, pi1) as
+    [S, nf]."""
+    if p.expanding:
+        raise ValueError("site-local evaluation needs a static background")
+    N = p.N
+    sites = np.asarray(sites)
+    o = np.arange(-2, 3)
+    iz = (sites[:, 0:1] + o) % N
+    iy = (sites[:, 1:2] + o) % N
+    ix = (sites[:, 2:3] + o) % N
+    sel = (iz[:, :, None, None], iy[:, None, :, None], ix[:, None, None, :])
+    ph = np.stack([np.asarray(phi[f])[sel].astype(np.float64) for f in range(p.nf)], axis=1)
+    pp = np.stack([np.asarray(pi[f])[sel].astype(np.float64) for f in range(p.nf)], axis=1)
+    F0 = _patch_force(p, ph)                              # 3^3
+    pih = pp[:, :, 1:-1, 1:-1, 1:-1] + 0.5 * dt * F0       # 3^3
+    ph1 = ph[:, :, 1:-1, 1:-1, 1:-1] + dt * pih            # 3^3
+    F1 = _patch_force(p, ph1)                             # centre
+    pi1 = pih[:, :, 1, 1, 1] + 0.5 * dt * F1[:, :, 0, 0, 0]
+    return ph1[:, :, 1, 1, 1], pi1

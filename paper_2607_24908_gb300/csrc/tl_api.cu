@@ -1,0 +1,537 @@
+// Host runtime behind include/tl.h: lattice objects, the integrator schedule
+// (pass list), launches, state transfer, initial fields and spectra.
+#include <cufft.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "tl_fourier.cuh"
+#include "tl_internal.cuh"
+
+using tl::FieldPtrs;
+using tl::Model;
+using tl::PassCoef;
+using tl::PassGeom;
+using tl::Scalars;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define TL_CK(call)                                                                                 \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(e_ == cudaErrorMemoryAllocation ? TL_ENOMEM : TL_ECUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                \
+    } while (0)
+
+#define TL_CKFFT(call)                                                                              \
+    do {                                                                                            \
+        cufftResult r_ = (call);                                                                    \
+        if (r_ != CUFFT_SUCCESS) return fail(TL_ECUDA, "%s: cufft error %d", #call, (int)r_);      \
+    } while (0)
+
+}  // namespace
+
+struct tl_lattice {
+    int N = 0, nf = 0;
+    double kIR = 0.0, dx = 0.0;
+    tl_dtype dtype = TL_F32;
+    size_t esz = 0;
+    tl_expansion ex{};
+    tl_potential pot{};
+    bool has_pot = false;
+    unsigned state_mask = 0;  // bit 2 f + which: that array was set
+    bool has_state = false;
+    cudaStream_t stream = nullptr;
+    bool own = false;
+    void *base = nullptr;           // owned field memory
+    void *buf[2][2][TL_MAX_FIELDS]; // [parity][phi, pi][field]
+    int cur = 0;
+    Scalars *d_sc = nullptr;
+    double *d_slots = nullptr;
+    PassGeom geom{};
+    Model model{};
+    int sm_count = 0;
+    int64_t step = 0;
+    bool energies_valid = false;
+    cufftHandle plan_c2r = 0, plan_r2c = 0;
+    bool have_c2r = false, have_r2c = false;
+};
+
+namespace {
+
+size_t n3_of(int N) { return (size_t)N * (size_t)N * (size_t)N; }
+
+int check_dims(int N, double kIR, int n_fields, tl_dtype dtype, const tl_expansion *ex)
+{
+    if (N < 8 || N % 4 != 0 || N > 2048) return fail(TL_EINVAL, "N must be a multiple of 4 in [8, 2048], got %d", N);
+    if (!(kIR > 0.0) || !isfinite(kIR)) return fail(TL_EINVAL, "kIR must be positive and finite");
+    if (n_fields < 1 || n_fields > TL_MAX_FIELDS) return fail(TL_EINVAL, "n_fields must be 1..%d", TL_MAX_FIELDS);
+    if (dtype != TL_F32 && dtype != TL_F64) return fail(TL_EINVAL, "unknown dtype %d", (int)dtype);
+    if (ex && ex->expanding) {
+        if (!isfinite(ex->alpha)) return fail(TL_EINVAL, "alpha must be finite");
+        if (!(ex->a0 > 0.0)) return fail(TL_EINVAL, "a0 must be positive");
+        if (!(ex->fstar_over_mp > 0.0)) return fail(TL_EINVAL, "fstar_over_mp must be positive");
+    }
+    return TL_OK;
+}
+
+void refresh_model(tl_lattice *L)
+{
+    Model &m = L->model;
+    m.N = L->N;
+    m.nf = L->nf;
+    m.expanding = L->ex.expanding ? 1 : 0;
+    m.alpha = L->ex.alpha;
+    m.mu2 = L->ex.fstar_over_mp * L->ex.fstar_over_mp;
+    m.inv_dx2 = 1.0 / (L->dx * L->dx);
+    m.lambda = L->pot.lambda;
+    m.q = L->pot.q;
+    for (int f = 0; f < TL_MAX_FIELDS; ++f) m.m2[f] = L->pot.m2[f];
+}
+
+int finish_create(tl_lattice *L, int N, double kIR, int nf, tl_dtype dtype, const tl_expansion *ex, void *stream)
+{
+    L->N = N;
+    L->nf = nf;
+    L->kIR = kIR;
+    L->dx = 2.0 * M_PI / (kIR * N);
+    L->dtype = dtype;
+    L->esz = dtype == TL_F32 ? 4 : 8;
+    if (ex) L->ex = *ex;
+    if (!L->ex.expanding) {
+        L->ex.alpha = 0.0;
+        L->ex.a0 = 1.0;
+        L->ex.fstar_over_mp = L->ex.fstar_over_mp > 0 ? L->ex.fstar_over_mp : 1.0;
+    }
+    L->stream = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    TL_CK(cudaGetDevice(&dev));
+    TL_CK(cudaDeviceGetAttribute(&L->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    L->geom = tl::pass_geometry(N, (int)L->esz, L->sm_count);
+    TL_CK(cudaMalloc(&L->d_sc, sizeof(Scalars)));
+    TL_CK(cudaMemset(L->d_sc, 0, sizeof(Scalars)));
+    TL_CK(cudaMalloc(&L->d_slots, sizeof(double) * tl::kMaxQ * L->geom.nblocks));
+    refresh_model(L);
+    TL_CK(tl::launch_set_background(L->model, L->d_sc, L->ex.a0, 0.0, L->stream));
+    return TL_OK;
+}
+
+int launch(tl_lattice *L, const PassCoef &c, bool measure_only)
+{
+    FieldPtrs fp;
+    for (int f = 0; f < TL_MAX_FIELDS; ++f) {
+        fp.phi_in[f] = L->buf[L->cur][0][f];
+        fp.pi_in[f] = L->buf[L->cur][1][f];
+        fp.phi_out[f] = L->buf[L->cur ^ 1][0][f];
+        fp.pi_out[f] = L->buf[L->cur ^ 1][1][f];
+    }
+    TL_CK(tl::launch_pass((int)L->dtype, L->model, fp, c, L->geom, L->d_sc, L->d_slots, measure_only, L->stream));
+    if (!measure_only) L->cur ^= 1;
+    return TL_OK;
+}
+
+int measure(tl_lattice *L, bool b_from_constraint)
+{
+    PassCoef c{};
+    c.integer_time = 1;
+    c.set_b_from_constraint = b_from_constraint ? 1 : 0;
+    int rc = launch(L, c, true);
+    if (rc) return rc;
+    L->energies_valid = true;
+    return TL_OK;
+}
+
+int read_scalars(tl_lattice *L, Scalars *h)
+{
+    TL_CK(cudaMemcpyAsync(h, L->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost, L->stream));
+    TL_CK(cudaStreamSynchronize(L->stream));
+    return TL_OK;
+}
+
+int check_field(const tl_lattice *L, int field, int which)
+{
+    if (!L) return fail(TL_EINVAL, "NULL lattice");
+    if (field < 0 || field >= L->nf) return fail(TL_EINVAL, "field %d out of range (n_fields %d)", field, L->nf);
+    if (which != 0 && which != 1) return fail(TL_EINVAL, "which must be 0 (phi) or 1 (pi)");
+    return TL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tl_last_error(void) { return g_err; }
+
+size_t tl_state_bytes(int N, int n_fields, tl_dtype dtype)
+{
+    if (N <= 0 || n_fields <= 0) return 0;
+    return 4 * (size_t)n_fields * n3_of(N) * (dtype == TL_F64 ? 8 : 4);
+}
+
+int tl_lattice_create(tl_lattice **out, int N, double kIR, int n_fields, tl_dtype dtype,
+                      const tl_expansion *expansion, void *cuda_stream)
+{
+    g_err[0] = 0;
+    if (!out) return fail(TL_EINVAL, "NULL out");
+    *out = nullptr;
+    int rc = check_dims(N, kIR, n_fields, dtype, expansion);
+    if (rc) return rc;
+    tl_lattice *L = new (std::nothrow) tl_lattice();
+    if (!L) return fail(TL_ENOMEM, "host allocation failed");
+    const size_t bytes = tl_state_bytes(N, n_fields, dtype);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete L;
+        return fail(TL_ECUDA, "cudaMemGetInfo failed (no CUDA device?)");
+    }
+    if (bytes + (64u << 20) > free_b) {
+        delete L;
+        return fail(TL_ENOMEM, "lattice needs %zu bytes, %zu free on the device", bytes, free_b);
+    }
+    if (cudaMalloc(&L->base, bytes) != cudaSuccess) {
+        delete L;
+        return fail(TL_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+    }
+    L->own = true;
+    const size_t arr = n3_of(N) * (dtype == TL_F64 ? 8 : 4);
+    char *p = static_cast<char *>(L->base);
+    memset(L->buf, 0, sizeof L->buf);
+    for (int f = 0; f < n_fields; ++f)
+        for (int par = 0; par < 2; ++par)
+            for (int w = 0; w < 2; ++w) L->buf[par][w][f] = p + ((size_t)(4 * f + 2 * par + w)) * arr;
+    rc = finish_create(L, N, kIR, n_fields, dtype, expansion, cuda_stream);
+    if (rc) {
+        tl_lattice_destroy(L);
+        return rc;
+    }
+    *out = L;
+    return TL_OK;
+}
+
+int tl_lattice_create_with_buffers(tl_lattice **out, int N, double kIR, int n_fields, tl_dtype dtype,
+                                   const tl_expansion *expansion, void *cuda_stream, void *const *dev_ptrs,
+                                   size_t n_ptrs)
+{
+    g_err[0] = 0;
+    if (!out) return fail(TL_EINVAL, "NULL out");
+    *out = nullptr;
+    int rc = check_dims(N, kIR, n_fields, dtype, expansion);
+    if (rc) return rc;
+    if (!dev_ptrs || n_ptrs != (size_t)(4 * n_fields)) return fail(TL_EINVAL, "need exactly 4*n_fields device pointers");
+    for (size_t i = 0; i < n_ptrs; ++i)
+        if (!dev_ptrs[i] || ((uintptr_t)dev_ptrs[i] & 15u)) return fail(TL_EINVAL, "device pointer %zu is NULL or not 16-byte aligned", i);
+    tl_lattice *L = new (std::nothrow) tl_lattice();
+    if (!L) return fail(TL_ENOMEM, "host allocation failed");
+    memset(L->buf, 0, sizeof L->buf);
+    for (int f = 0; f < n_fields; ++f) {
+        L->buf[0][0][f] = dev_ptrs[4 * f + 0];
+        L->buf[0][1][f] = dev_ptrs[4 * f + 1];
+        L->buf[1][0][f] = dev_ptrs[4 * f + 2];
+        L->buf[1][1][f] = dev_ptrs[4 * f + 3];
+    }
+    rc = finish_create(L, N, kIR, n_fields, dtype, expansion, cuda_stream);
+    if (rc) {
+        tl_lattice_destroy(L);
+        return rc;
+    }
+    *out = L;
+    return TL_OK;
+}
+
+void tl_lattice_destroy(tl_lattice *L)
+{
+    if (!L) return;
+    if (L->stream || true) cudaStreamSynchronize(L->stream);
+    if (L->have_c2r) cufftDestroy(L->plan_c2r);
+    if (L->have_r2c) cufftDestroy(L->plan_r2c);
+    if (L->own && L->base) cudaFree(L->base);
+    if (L->d_sc) cudaFree(L->d_sc);
+    if (L->d_slots) cudaFree(L->d_slots);
+    delete L;
+}
+
+int tl_set_potential(tl_lattice *L, const tl_potential *pot)
+{
+    g_err[0] = 0;
+    if (!L || !pot) return fail(TL_EINVAL, "NULL argument");
+    if (!isfinite(pot->lambda) || !isfinite(pot->q)) return fail(TL_EINVAL, "non-finite coupling");
+    for (int f = 0; f < TL_MAX_FIELDS; ++f)
+        if (!isfinite(pot->m2[f])) return fail(TL_EINVAL, "non-finite mass");
+    L->pot = *pot;
+    L->has_pot = true;
+    refresh_model(L);
+    L->energies_valid = false;
+    return TL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Pass list of n steps from a synchronised state (phi_n, pi_n, a_n, b_n):
+// substep sizes s_1..s_M (M = n P) in units of dt; pass 0 half-kicks with
+// s_1, pass j (0 < j < M) closes substep j and opens j+1 (merged kicks
+// (s_j + s_{j+1})/2), pass M closes substep M with a half kick.  Each pass
+// evaluates at the boundary after its deferred drift; hdt/hb bring pi and b
+// to that boundary for the energies and the Hubble residual.
+int run_steps(tl_lattice *L, int n, double dt, const double *w, int P)
+{
+    const long M = (long)n * P;
+    for (long j = 0; j <= M; ++j) {
+        const double s_prev = j > 0 ? w[(j - 1) % P] : 0.0;
+        const double s_next = j < M ? w[j % P] : 0.0;
+        PassCoef c{};
+        c.kdt = 0.5 * (s_prev + s_next) * dt;
+        c.hdt = 0.5 * s_prev * dt;
+        c.edt = 0.5 * (s_prev + s_next) * dt;
+        c.hb_dt = 0.5 * s_prev * dt;
+        c.dnext_dt = s_next * dt;
+        c.integer_time = (j % P == 0) ? 1 : 0;
+        int rc = launch(L, c, false);
+        if (rc) return rc;
+    }
+    return TL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tl_step(tl_lattice *L, int n, double dt, tl_integrator integrator)
+{
+    g_err[0] = 0;
+    if (!L) return fail(TL_EINVAL, "NULL lattice");
+    if (n < 0) return fail(TL_EINVAL, "n must be >= 0");
+    if (!isfinite(dt) || dt == 0.0) return fail(TL_EINVAL, "dt must be finite and nonzero");
+    if (!L->has_pot) return fail(TL_ESTATE, "tl_set_potential has not been called");
+    if (!L->has_state) return fail(TL_ESTATE, "no state: call tl_init_fluctuations or tl_set_state for every array");
+    if (n == 0) return TL_OK;
+    static const double w_vv[1] = {1.0};
+    const double cr = cbrt(2.0);
+    const double w1 = 1.0 / (2.0 - cr), w0 = -cr / (2.0 - cr);
+    const double w_y4[3] = {w1, w0, w1};
+    int rc;
+    switch (integrator) {
+    case TL_LEAPFROG:
+    case TL_VERLET: rc = run_steps(L, n, dt, w_vv, 1); break;
+    case TL_YOSHIDA4: rc = run_steps(L, n, dt, w_y4, 3); break;
+    default: return fail(TL_EINVAL, "unknown integrator %d", (int)integrator);
+    }
+    if (rc) return rc;
+    L->step += n;
+    L->energies_valid = true;
+    return TL_OK;
+}
+
+int tl_energies(tl_lattice *L, tl_energies_t *out)
+{
+    g_err[0] = 0;
+    if (!L || !out) return fail(TL_EINVAL, "NULL argument");
+    if (!L->has_state || !L->has_pot) return fail(TL_ESTATE, "no state or potential");
+    if (!L->energies_valid) {
+        int rc = measure(L, false);
+        if (rc) return rc;
+    }
+    Scalars h;
+    int rc = read_scalars(L, &h);
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    out->step = L->step;
+    out->time = h.time;
+    out->a = L->ex.expanding ? h.a : 1.0;
+    out->b = L->ex.expanding ? h.b : 0.0;
+    for (int f = 0; f < L->nf; ++f) {
+        out->K[f] = h.E[f];
+        out->G[f] = h.E[L->nf + f];
+    }
+    out->V = h.E[2 * L->nf];
+    out->hubble_resid = h.hubble;
+    if (h.status != TL_OK) return fail(TL_EUNSTABLE, "energies became non-finite");
+    return TL_OK;
+}
+
+int tl_get_state(tl_lattice *L, int field, int which, void *host, size_t bytes)
+{
+    g_err[0] = 0;
+    int rc = check_field(L, field, which);
+    if (rc) return rc;
+    if (!host || bytes != n3_of(L->N) * L->esz) return fail(TL_EINVAL, "host buffer must hold N^3 elements");
+    TL_CK(cudaMemcpyAsync(host, L->buf[L->cur][which][field], bytes, cudaMemcpyDeviceToHost, L->stream));
+    Scalars h;
+    rc = read_scalars(L, &h);
+    if (rc) return rc;
+    if (h.status != TL_OK) return fail(TL_EUNSTABLE, "evolution became non-finite");
+    return TL_OK;
+}
+
+int tl_set_state(tl_lattice *L, int field, int which, const void *host, size_t bytes)
+{
+    g_err[0] = 0;
+    int rc = check_field(L, field, which);
+    if (rc) return rc;
+    if (!host || bytes != n3_of(L->N) * L->esz) return fail(TL_EINVAL, "host buffer must hold N^3 elements");
+    TL_CK(cudaMemcpyAsync(L->buf[L->cur][which][field], host, bytes, cudaMemcpyHostToDevice, L->stream));
+    TL_CK(tl::launch_set_background(L->model, L->d_sc, L->ex.a0, 0.0, L->stream));
+    TL_CK(cudaStreamSynchronize(L->stream));
+    L->state_mask |= 1u << (2 * field + which);
+    L->has_state = L->state_mask == (1u << (2 * L->nf)) - 1u;
+    L->step = 0;
+    L->energies_valid = false;
+    return TL_OK;
+}
+
+int tl_set_background(tl_lattice *L, double a, double b, int from_constraint)
+{
+    g_err[0] = 0;
+    if (!L) return fail(TL_EINVAL, "NULL lattice");
+    if (!(a > 0.0) || !isfinite(a) || !isfinite(b)) return fail(TL_EINVAL, "a must be positive, a and b finite");
+    TL_CK(tl::launch_set_background(L->model, L->d_sc, a, b, L->stream));
+    L->energies_valid = false;
+    if (from_constraint && L->ex.expanding) {
+        if (!L->has_state || !L->has_pot) return fail(TL_ESTATE, "from_constraint needs a state and a potential");
+        return measure(L, true);
+    }
+    return TL_OK;
+}
+
+int tl_state_device_ptr(tl_lattice *L, int field, int which, void **dev_ptr)
+{
+    g_err[0] = 0;
+    int rc = check_field(L, field, which);
+    if (rc) return rc;
+    if (!dev_ptr) return fail(TL_EINVAL, "NULL dev_ptr");
+    *dev_ptr = L->buf[L->cur][which][field];
+    return TL_OK;
+}
+
+int tl_spectrum_bins(int N)
+{
+    if (N <= 0) return 0;
+    return (int)ceil(sqrt(3.0) * N / 2.0) + 1;
+}
+
+int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
+{
+    g_err[0] = 0;
+    if (!L || !spec) return fail(TL_EINVAL, "NULL argument");
+    if (!L->has_pot) return fail(TL_ESTATE, "tl_set_potential must come first (b0 needs the potential)");
+    if (!(spec->A >= 0.0) || !isfinite(spec->A)) return fail(TL_EINVAL, "A must be finite and >= 0");
+    const int N = L->N;
+    const size_t n3 = n3_of(N);
+    const size_t nh = (size_t)N * N * (N / 2 + 1);
+    if (!L->have_c2r) {
+        TL_CKFFT(cufftPlan3d(&L->plan_c2r, N, N, N, CUFFT_Z2D));
+        L->have_c2r = true;
+    }
+    TL_CKFFT(cufftSetStream(L->plan_c2r, L->stream));
+    double2 *modes = nullptr;
+    double *real = nullptr;
+    TL_CK(cudaMallocAsync((void **)&modes, nh * sizeof(double2), L->stream));
+    cudaError_t e = cudaMallocAsync((void **)&real, n3 * sizeof(double), L->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(modes, L->stream);
+        return fail(TL_ENOMEM, "scratch allocation for the initial field failed");
+    }
+    int rc = TL_OK;
+    const bool expanding = L->ex.expanding != 0;
+    const double pscale = expanding ? pow(L->ex.a0, 3.0 - L->ex.alpha) : 1.0;
+    for (int f = 0; f < L->nf && rc == TL_OK; ++f) {
+        for (int which = 0; which < 2 && rc == TL_OK; ++which) {
+            const double base = which == 0 ? spec->phi0[f] : spec->pi0[f];
+            const bool fluct = which == 0 || spec->fluct_pi;
+            void *dst = L->buf[L->cur][which][f];
+            if (fluct && spec->A > 0.0) {
+                cudaError_t ce = tl::launch_fill_modes(modes, N, L->kIR, spec->A, spec->meff2[f], which,
+                                                       seed, which == 0 ? (uint64_t)f : (uint64_t)(8 + f),
+                                                       L->sm_count, L->stream);
+                if (ce != cudaSuccess) { rc = fail(TL_ECUDA, "fill_modes: %s", cudaGetErrorString(ce)); break; }
+                cufftResult fr = cufftExecZ2D(L->plan_c2r, reinterpret_cast<cufftDoubleComplex *>(modes), real);
+                if (fr != CUFFT_SUCCESS) { rc = fail(TL_ECUDA, "cufftExecZ2D failed (%d)", (int)fr); break; }
+                ce = tl::launch_assemble((int)L->dtype, dst, real, n3, base, which == 0 ? 1.0 : pscale,
+                                         L->sm_count, L->stream);
+                if (ce != cudaSuccess) { rc = fail(TL_ECUDA, "assemble: %s", cudaGetErrorString(ce)); break; }
+            } else {
+                cudaError_t ce = tl::launch_assemble((int)L->dtype, dst, nullptr, n3, base, 0.0, L->sm_count, L->stream);
+                if (ce != cudaSuccess) { rc = fail(TL_ECUDA, "assemble: %s", cudaGetErrorString(ce)); break; }
+            }
+        }
+    }
+    cudaFreeAsync(modes, L->stream);
+    cudaFreeAsync(real, L->stream);
+    if (rc) return rc;
+    L->state_mask = (1u << (2 * L->nf)) - 1u;
+    L->has_state = true;
+    L->step = 0;
+    TL_CK(tl::launch_set_background(L->model, L->d_sc, L->ex.a0, 0.0, L->stream));
+    rc = measure(L, expanding);
+    if (rc) return rc;
+    TL_CK(cudaStreamSynchronize(L->stream));
+    return TL_OK;
+}
+
+int tl_spectrum(tl_lattice *L, int field, int which, int nbins, double *k, double *P, int64_t *count)
+{
+    g_err[0] = 0;
+    int rc = check_field(L, field, which);
+    if (rc) return rc;
+    const int N = L->N;
+    const int nb = tl_spectrum_bins(N);
+    if (nbins < nb) return fail(TL_EINVAL, "nbins must be >= %d", nb);
+    const size_t n3 = n3_of(N);
+    const size_t nh = (size_t)N * N * (N / 2 + 1);
+    if (!L->have_r2c) {
+        TL_CKFFT(cufftPlan3d(&L->plan_r2c, N, N, N, CUFFT_D2Z));
+        L->have_r2c = true;
+    }
+    TL_CKFFT(cufftSetStream(L->plan_r2c, L->stream));
+    double2 *modes = nullptr;
+    double *real = nullptr, *acc = nullptr;
+    TL_CK(cudaMallocAsync((void **)&modes, nh * sizeof(double2), L->stream));
+    TL_CK(cudaMallocAsync((void **)&real, n3 * sizeof(double), L->stream));
+    TL_CK(cudaMallocAsync((void **)&acc, (size_t)nb * 3 * sizeof(double), L->stream));
+    TL_CK(cudaMemsetAsync(acc, 0, (size_t)nb * 3 * sizeof(double), L->stream));
+    TL_CK(tl::launch_widen((int)L->dtype, real, L->buf[L->cur][which][field], n3, L->sm_count, L->stream));
+    cufftResult fr = cufftExecD2Z(L->plan_r2c, real, reinterpret_cast<cufftDoubleComplex *>(modes));
+    if (fr != CUFFT_SUCCESS) return fail(TL_ECUDA, "cufftExecD2Z failed (%d)", (int)fr);
+    TL_CK(tl::launch_bin(modes, N, nb, acc, acc + nb, reinterpret_cast<unsigned long long *>(acc + 2 * nb),
+                         L->sm_count, L->stream));
+    std::vector<double> h((size_t)nb * 3);
+    TL_CK(cudaMemcpyAsync(h.data(), acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    cudaFreeAsync(modes, L->stream);
+    cudaFreeAsync(real, L->stream);
+    cudaFreeAsync(acc, L->stream);
+    TL_CK(cudaStreamSynchronize(L->stream));
+    const double Lbox = 2.0 * M_PI / L->kIR;
+    const double V = Lbox * Lbox * Lbox;
+    for (int b = 0; b < nbins; ++b) {
+        unsigned long long c = 0;
+        double ps = 0.0, rs = 0.0;
+        if (b < nb) {
+            memcpy(&c, &h[2 * (size_t)nb + b], sizeof c);
+            ps = h[b];
+            rs = h[(size_t)nb + b];
+        }
+        if (count) count[b] = (int64_t)c;
+        if (P) P[b] = c ? V * ps / (double)c : 0.0;
+        if (k) k[b] = c ? L->kIR * rs / (double)c : 0.0;
+    }
+    return TL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Internal declarations shared by the CUDA translation units of libtl.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tl.h"
+
+namespace tl {
+
+constexpr int kMaxFields = TL_MAX_FIELDS;
+constexpr int kMaxQ = 2 * kMaxFields + 1;  // K_f, G_f, V
+
+// Device-resident scalars of one lattice (always FP64).  The fused pass reads
+// the coefficients for its own evaluation time (a, drift, weights) and its
+// last CTA writes those of the next pass.
+struct Scalars {
+    double a;          // scale factor at the time of the next field evaluation
+    double b;          // a'
+    double drift;      // the next pass's drift: d dt ((a_prev + a)/2)^(alpha-3)
+    double pending_dt; // program time the next pass's drift advances
+    double wl, wv;     // a^(1+alpha), a^(3+alpha)
+    double wk, wg;     // a^-6, a^-2
+    double E[kMaxQ];   // K_f, G_f, V at the last evaluated time
+    double hubble;     // Hubble residual at the last integer time
+    double time;       // program time of the last evaluation
+    int status;        // TL_OK or TL_EUNSTABLE
+    unsigned ticket;   // CTAs of the current pass that finished their slot
+};
+
+// Scalar constants of a lattice/model passed by value to every pass.
+struct Model {
+    int N;
+    int nf;
+    int expanding;
+    double alpha;
+    double mu2;
+    double inv_dx2;
+    double lambda, q;
+    double m2[kMaxFields];
+};
+
+// Coefficients of one fused pass, in units of dt already multiplied in.
+struct PassCoef {
+    double kdt;       // pi_new = pi_s + kdt F
+    double hdt;       // pi_int = pi_s + hdt F (momentum at the evaluation time, for K)
+    double edt;       // b += edt a''
+    double hb_dt;     // b at the evaluation time: b_old + hb_dt a'' (Hubble residual)
+    double dnext_dt;  // drift of the following pass (and a += dnext_dt b)
+    int integer_time; // the evaluation time is a whole step: record the Hubble residual
+    int set_b_from_constraint; // measurement pass after a new state: b from the constraint
+};
+
+struct FieldPtrs {
+    const void *phi_in[kMaxFields];
+    const void *pi_in[kMaxFields];
+    void *phi_out[kMaxFields];
+    void *pi_out[kMaxFields];
+};
+
+// Launch geometry of the fused pass.
+struct PassGeom {
+    int txt;  // threads along x (each owns VEC consecutive sites)
+    int ty;   // threads along y (one row each)
+    int zc;   // z-planes per CTA
+    dim3 grid;
+    unsigned nblocks;
+};
+
+PassGeom pass_geometry(int N, int elem_bytes, int sm_count);
+
+// Enqueue one fused pass (measure_only: energies of the stored state, no writes).
+cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,
+                        Scalars *sc, double *slots, bool measure_only, cudaStream_t s);
+
+// Set a, b (and the derived weights) on the device; drift = 0.
+cudaError_t launch_set_background(const Model &m, Scalars *sc, double a, double b, cudaStream_t s);
+
+}  // namespace tl

@@ -1,0 +1,281 @@
+"""ctypes binding of include/tl.h (argument marshalling only).
+
+Functions keep the C names (``tl_lattice_create`` ...) and raise ``TLError``
+on a negative return code.  ``Lattice`` wraps one lattice handle.  Every step
+of the computation runs in libtl.so; if the library is missing this module
+raises at load time -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtl.so")
+
+MAX_FIELDS = 3
+F32, F64 = 0, 1
+LEAPFROG, VERLET, YOSHIDA4 = 0, 1, 2
+INTEGRATORS = {"leapfrog": LEAPFROG, "verlet": VERLET, "yoshida4": YOSHIDA4}
+DTYPES = {"f32": F32, "f64": F64}
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
+_NAMES = {EINVAL: "TL_EINVAL", ENOMEM: "TL_ENOMEM", ECUDA: "TL_ECUDA", EUNSTABLE: "TL_EUNSTABLE",
+          ETIMEOUT: "TL_ETIMEOUT", ESTATE: "TL_ESTATE"}
+
+
+class TLError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class tl_expansion(ctypes.Structure):
+    _fields_ = [("expanding", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("fstar_over_mp", ctypes.c_double), ("a0", ctypes.c_double)]
+
+
+class tl_potential(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("q", ctypes.c_double), ("m2", ctypes.c_double * MAX_FIELDS)]
+
+
+class tl_init_spec(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_double), ("meff2", ctypes.c_double * MAX_FIELDS),
+                ("phi0", ctypes.c_double * MAX_FIELDS), ("pi0", ctypes.c_double * MAX_FIELDS),
+                ("fluct_pi", ctypes.c_int)]
+
+
+class tl_energies_t(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("time", ctypes.c_double), ("a", ctypes.c_double),
+                ("b", ctypes.c_double), ("K", ctypes.c_double * MAX_FIELDS),
+                ("G", ctypes.c_double * MAX_FIELDS), ("V", ctypes.c_double),
+                ("hubble_resid", ctypes.c_double)]
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "tl_lattice_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int, ctypes.POINTER(tl_expansion), ctypes.c_void_p]),
+    "tl_lattice_create_with_buffers": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_double,
+                                                      ctypes.c_int, ctypes.c_int, ctypes.POINTER(tl_expansion),
+                                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t]),
+    "tl_state_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "tl_lattice_destroy": (None, [ctypes.c_void_p]),
+    "tl_set_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_potential)]),
+    "tl_init_fluctuations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(tl_init_spec)]),
+    "tl_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
+    "tl_energies": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_energies_t)]),
+    "tl_spectrum_bins": (ctypes.c_int, [ctypes.c_int]),
+    "tl_spectrum": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int64)]),
+    "tl_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
+    "tl_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
+    "tl_set_background": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+    "tl_state_device_ptr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "tl_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtl.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2607_24908_gb300.build` "
+                              "(no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise TLError(rc, lib().tl_last_error().decode(errors="replace"))
+
+
+def _f3(vals, fill=0.0):
+    v = list(vals) + [fill] * MAX_FIELDS
+    return (ctypes.c_double * MAX_FIELDS)(*v[:MAX_FIELDS])
+
+
+# --- the C functions, same names ------------------------------------------------
+
+def tl_lattice_create(N: int, kIR: float, n_fields: int, dtype: int, expansion: Optional[tl_expansion] = None,
+                      cuda_stream: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().tl_lattice_create(ctypes.byref(h), N, kIR, n_fields, dtype,
+                                   ctypes.byref(expansion) if expansion is not None else None,
+                                   ctypes.c_void_p(cuda_stream)))
+    return h
+
+
+def tl_lattice_create_with_buffers(N: int, kIR: float, n_fields: int, dtype: int, expansion: Optional[tl_expansion],
+                                   cuda_stream: int, dev_ptrs: Sequence[int]) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * len(dev_ptrs))(*dev_ptrs)
+    _check(lib().tl_lattice_create_with_buffers(ctypes.byref(h), N, kIR, n_fields, dtype,
+                                                ctypes.byref(expansion) if expansion is not None else None,
+                                                ctypes.c_void_p(cuda_stream), arr, len(dev_ptrs)))
+    return h
+
+
+def tl_state_bytes(N: int, n_fields: int, dtype: int) -> int:
+    return lib().tl_state_bytes(N, n_fields, dtype)
+
+
+def tl_lattice_destroy(h):
+    lib().tl_lattice_destroy(h)
+
+
+def tl_set_potential(h, lam: float, q: float, m2: Sequence[float]):
+    p = tl_potential(lam, q, _f3(m2))
+    _check(lib().tl_set_potential(h, ctypes.byref(p)))
+
+
+def tl_init_fluctuations(h, seed: int, A: float, meff2, phi0, pi0=(0, 0, 0), fluct_pi: bool = False):
+    s = tl_init_spec(A, _f3(meff2), _f3(phi0), _f3(pi0), int(bool(fluct_pi)))
+    _check(lib().tl_init_fluctuations(h, ctypes.c_uint64(seed), ctypes.byref(s)))
+
+
+def tl_step(h, n: int, dt: float, integrator: int):
+    _check(lib().tl_step(h, n, dt, integrator))
+
+
+def tl_energies(h) -> tl_energies_t:
+    e = tl_energies_t()
+    _check(lib().tl_energies(h, ctypes.byref(e)))
+    return e
+
+
+def tl_spectrum_bins(N: int) -> int:
+    return lib().tl_spectrum_bins(N)
+
+
+def tl_spectrum(h, N: int, field: int, which: int):
+    nb = tl_spectrum_bins(N)
+    k = np.zeros(nb)
+    P = np.zeros(nb)
+    c = np.zeros(nb, dtype=np.int64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(lib().tl_spectrum(h, field, which, nb, k.ctypes.data_as(dp), P.ctypes.data_as(dp),
+                             c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return k, P, c
+
+
+def tl_get_state(h, field: int, which: int, out: np.ndarray):
+    _check(lib().tl_get_state(h, field, which, ctypes.c_void_p(out.ctypes.data), out.nbytes))
+
+
+def tl_set_state(h, field: int, which: int, arr: np.ndarray):
+    a = np.ascontiguousarray(arr)
+    _check(lib().tl_set_state(h, field, which, ctypes.c_void_p(a.ctypes.data), a.nbytes))
+
+
+def tl_set_background(h, a: float, b: float, from_constraint: bool):
+    _check(lib().tl_set_background(h, a, b, int(bool(from_constraint))))
+
+
+def tl_state_device_ptr(h, field: int, which: int) -> int:
+    p = ctypes.c_void_p()
+    _check(lib().tl_state_device_ptr(h, field, which, ctypes.byref(p)))
+    return p.value or 0
+
+
+# --- convenience wrapper --------------------------------------------------------
+
+@dataclass
+class Energies:
+    step: int
+    time: float
+    a: float
+    b: float
+    K: np.ndarray
+    G: np.ndarray
+    V: float
+    hubble_resid: float
+
+    def vector(self) -> np.ndarray:
+        """[K_0.., G_0.., V] like the oracle's energies()."""
+        return np.concatenate([self.K, self.G, [self.V]])
+
+
+class Lattice:
+    """One lattice on the current CUDA device (state resident in HBM)."""
+
+    def __init__(self, N: int, kIR: float, n_fields: int = 1, dtype: str = "f64", expanding: bool = False,
+                 alpha: float = 0.0, fstar_over_mp: float = 1.0, a0: float = 1.0, stream: int = 0):
+        self.N, self.nf, self.kIR = N, n_fields, kIR
+        self.dtype = dtype
+        self.np_dtype = np.float32 if dtype == "f32" else np.float64
+        ex = tl_expansion(int(bool(expanding)), alpha, fstar_over_mp, a0)
+        self.h = tl_lattice_create(N, kIR, n_fields, DTYPES[dtype], ex, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            tl_lattice_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_potential(self, lam: float = 1.0, q: float = 0.0, m2=(0.0, 0.0, 0.0)):
+        tl_set_potential(self.h, lam, q, m2)
+
+    def init_fluctuations(self, seed: int, A: float = 1e-10, meff2=(3.0, 0, 0), phi0=(1.0, 0, 0), pi0=(0, 0, 0),
+                          fluct_pi: bool = False):
+        tl_init_fluctuations(self.h, seed, A, meff2, phi0, pi0, fluct_pi)
+
+    def step(self, n: int, dt: float, integrator="verlet"):
+        tl_step(self.h, n, dt, INTEGRATORS[integrator] if isinstance(integrator, str) else integrator)
+
+    def energies(self) -> Energies:
+        e = tl_energies(self.h)
+        nf = self.nf
+        return Energies(e.step, e.time, e.a, e.b, np.array(e.K[:nf]), np.array(e.G[:nf]), e.V, e.hubble_resid)
+
+    def spectrum(self, field: int = 0, which: int = 0):
+        return tl_spectrum(self.h, self.N, field, which)
+
+    def get(self, field: int, which: int) -> np.ndarray:
+        out = np.empty((self.N, self.N, self.N), dtype=self.np_dtype)
+        tl_get_state(self.h, field, which, out)
+        return out
+
+    def get_all(self):
+        phi = np.stack([self.get(f, 0) for f in range(self.nf)])
+        pi = np.stack([self.get(f, 1) for f in range(self.nf)])
+        return phi, pi
+
+    def set_state(self, phi: np.ndarray, pi: np.ndarray, a: float = 1.0, b: float = 0.0,
+                  b_from_constraint: bool = False):
+        for f in range(self.nf):
+            tl_set_state(self.h, f, 0, np.ascontiguousarray(phi[f], dtype=self.np_dtype))
+            tl_set_state(self.h, f, 1, np.ascontiguousarray(pi[f], dtype=self.np_dtype))
+        tl_set_background(self.h, a, b, b_from_constraint)
+
+    def device_ptr(self, field: int, which: int) -> int:
+        return tl_state_device_ptr(self.h, field, which)

@@ -1,0 +1,52 @@
+"""CPU checks of the boundary: libtl.so builds, loads without a GPU and
+exports every function include/tl.h declares; the binding covers them all."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "tl.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tl_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2607_24908_gb300 import build, tl
+    lib = build.build()
+    out = subprocess.check_output(["nm", "-D", "--defined-only", lib], text=True)
+    exported = set(re.findall(r" T (tl_[a-z0-9_]+)$", out, flags=re.M))
+    declared = header_functions()
+    assert declared, "no functions parsed from include/tl.h"
+    missing = [f for f in declared if f not in exported]
+    assert not missing, missing
+    L = tl.lib()  # dlopen works without a GPU
+    for f in declared:
+        assert hasattr(L, f)
+    assert sorted(tl.declared_symbols()) == declared
+
+
+def test_spectrum_bins_and_state_bytes_without_gpu():
+    from paper_2607_24908_gb300 import tl
+    import math
+    for N in (8, 32, 48, 1024):
+        assert tl.tl_spectrum_bins(N) == math.ceil(math.sqrt(3) * N / 2) + 1
+    assert tl.tl_state_bytes(1024, 2, tl.F32) == 4 * 2 * 1024 ** 3 * 4
+    assert tl.tl_state_bytes(32, 1, tl.F64) == 4 * 32 ** 3 * 8
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2607_24908_gb300 import tl
+    with pytest.raises(tl.TLError) as e:
+        tl.Lattice(32, 0.5, 1, "f64")
+    assert e.value.code in (tl.ECUDA, tl.ENOMEM)
+    with pytest.raises(tl.TLError) as e:
+        tl.Lattice(30, 0.5, 1, "f64")
+    assert e.value.code == tl.EINVAL

@@ -1,0 +1,243 @@
+"""GPU path (libtl.so through the C ABI) against the FP64 oracle.
+
+Tolerances (fields normwise: max|x_gpu - x_oracle| / max|x_oracle|; energy
+components relative to the total energy density K+G+V; a, b relative):
+FP64 <= 1e-12, FP32 <= 1e-5 (linear regime, <= 400 steps).  Inputs are
+seeded white-noise or Philox-drawn states from paper_2607_24908_gb300.workloads
+and the oracle; nothing the oracle consumes comes from the GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2607_24908_gb300 import tl as T
+from paper_2607_24908_gb300.workloads import plane_wave, sample_sites, white_noise_state
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+OINT = {"leapfrog": o.LEAPFROG, "verlet": o.VERLET, "yoshida4": o.YOSHIDA4}
+
+
+def normwise(x, ref):
+    return float(np.max(np.abs(np.asarray(x, np.float64) - ref)) / np.max(np.abs(ref)))
+
+
+def make(p: o.Params, dtype: str) -> T.Lattice:
+    lat = T.Lattice(p.N, p.kIR, p.nf, dtype, p.expanding, p.alpha, p.fstar_over_mp, 1.0)
+    lat.set_potential(p.lam, p.q, p.m2)
+    return lat
+
+
+def oracle_b0(p, phi, pi):
+    E = o.energies(p, phi, pi, 1.0)
+    return math.sqrt(p.fstar_over_mp ** 2 * float(np.sum(E)) / 3.0)
+
+
+def compare_run(p, dtype, phi0, pi0, dt, n, integ, tol=None, calls=1):
+    """Same input on both sides (the dtype-rounded state), n steps, compare."""
+    tol = tol or TOL[dtype]
+    npd = np.float32 if dtype == "f32" else np.float64
+    phi0 = phi0.astype(npd)
+    pi0 = pi0.astype(npd)
+    b0 = oracle_b0(p, phi0, pi0) if p.expanding else 0.0
+    with make(p, dtype) as lat:
+        lat.set_state(phi0, pi0, 1.0, 0.0, b_from_constraint=p.expanding)
+        if p.expanding:
+            assert abs(lat.energies().b - b0) / b0 < TOL[dtype] * 10
+        for _ in range(calls):
+            lat.step(n // calls, dt, integ)
+        E = lat.energies()
+        phi, pi = lat.get_all()
+    ophi, opi, oa, ob = o.run(p, phi0, pi0, 1.0, b0, dt, n, OINT[integ])
+    if calls > 1:  # the oracle's steps are a per-step map; calls only regroup the GPU passes
+        pass
+    oE = o.energies(p, ophi, opi, oa)
+    rho = float(np.sum(oE))
+    assert normwise(phi, ophi) < tol, normwise(phi, ophi)
+    assert normwise(pi, opi) < tol, normwise(pi, opi)
+    assert np.max(np.abs(E.vector() - oE)) / rho < tol, (E.vector(), oE)
+    assert E.step == n
+    if p.expanding:
+        assert abs(E.a - oa) / oa < tol and abs(E.b - ob) / abs(ob) < tol, (E.a, oa, E.b, ob)
+        oR = o.hubble_residual(p, oE, oa, ob)
+        assert abs(E.hubble_resid - oR) < max(1e-3 * oR, 100 * tol)
+    return E
+
+
+# --- closed form ---------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_plane_wave_exact_discrete_solution(dtype):
+    """Free field m = 1 on 32^3, kIR = 0.5, dt = 0.05, 400 leapfrog steps:
+    phi_n = cos(k.x) cos(n W dt) with cos(W dt) = 1 - dt^2 w_lat^2/2."""
+    N, n, dt, steps = 32, (1, 2, 3), 0.05, 400
+    p = o.Params(N=N, nf=1, kIR=0.5, lam=0.0, m2=(1.0, 0, 0))
+    phi0 = plane_wave(N, n)[None]
+    with make(p, dtype) as lat:
+        lat.set_state(phi0, np.zeros_like(phi0))
+        lat.step(steps, dt, "leapfrog")
+        phi, pi = lat.get_all()
+    w2 = 1.0 + sum((2.0 / p.dx * math.sin(p.kIR * c * p.dx / 2.0)) ** 2 for c in n)
+    Wdt = math.acos(1.0 - dt * dt * w2 / 2.0)
+    assert np.max(np.abs(phi - phi0 * math.cos(steps * Wdt))) < TOL[dtype]
+    assert np.max(np.abs(pi + phi0 * math.sin(steps * Wdt) * math.sin(Wdt) / dt)) < TOL[dtype] * 2
+
+
+# --- static phi^4, 32^3, initial Gaussian field, 400 leapfrog steps -------------
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_phi4_static_32_init_and_400_leapfrog_steps(dtype):
+    p = o.Params(N=32, nf=1, kIR=0.5, lam=1.0)
+    spec = o.InitSpec(A=1e-10, meff2=(3.0, 0, 0), phi0=(1.0, 0, 0))
+    ophi0, opi0, _, _ = o.init_fluctuations(p, 1, spec)
+    with make(p, dtype) as lat:
+        lat.init_fluctuations(1, A=1e-10, meff2=(3.0, 0, 0), phi0=(1.0, 0, 0))
+        gphi0, gpi0 = lat.get_all()
+    dphi = ophi0 - 1.0
+    # initial fluctuations: FP64 to rounding; FP32 to the storage ulp near 1
+    err = np.max(np.abs(gphi0.astype(np.float64) - ophi0)) / np.max(np.abs(dphi))
+    assert err < (1e-9 if dtype == "f64" else 2e-2), err
+    assert np.max(np.abs(gpi0)) == 0.0
+    compare_run(p, dtype, ophi0, opi0, 0.05, 400, "leapfrog")
+
+
+# --- expanding backgrounds, ragged tiles, several fields --------------------------
+
+@pytest.mark.parametrize("dtype,N,nf,integ,steps", [
+    ("f64", 72, 1, "verlet", 100),
+    ("f64", 40, 2, "yoshida4", 40),
+    ("f64", 24, 3, "leapfrog", 60),
+    ("f32", 72, 2, "yoshida4", 100),
+    ("f32", 40, 1, "verlet", 100),
+    ("f32", 28, 3, "verlet", 50),
+])
+def test_expanding_parity(dtype, N, nf, integ, steps):
+    p = o.Params(N=N, nf=nf, kIR=0.5, expanding=True, alpha=1.0, lam=1.0, q=100.0 if nf > 1 else 0.0,
+                 m2=(0.0, 0.1, 0.2))
+    phi0, pi0 = white_noise_state(N, nf, seed=100 + N + nf, phi0=(1.0, 0.0, 0.0), sigma_phi=1e-3,
+                                  sigma_pi=1e-3)
+    compare_run(p, dtype, phi0, pi0, 0.01 if integ != "yoshida4" else 0.005, steps, integ)
+
+
+def test_static_three_fields_alpha_ignored():
+    p = o.Params(N=32, nf=3, kIR=0.5, lam=1.0, q=10.0, m2=(0.0, 0.5, 1.0))
+    phi0, pi0 = white_noise_state(32, 3, seed=9, phi0=(1.0, 0.3, 0.2), sigma_phi=1e-2, sigma_pi=1e-2)
+    compare_run(p, "f64", phi0, pi0, 0.02, 100, "verlet")
+
+
+def test_split_step_calls_match_single_call():
+    """step(n) = prologue + n P - 1 merged passes + closing; two calls of n/2
+    resynchronise in between, which only changes rounding."""
+    p = o.Params(N=32, nf=2, kIR=0.5, expanding=True, alpha=1.0, lam=1.0, q=100.0)
+    phi0, pi0 = white_noise_state(32, 2, seed=21, phi0=(1.0, 0.0), sigma_phi=1e-3, sigma_pi=1e-3)
+    compare_run(p, "f64", phi0, pi0, 0.005, 40, "yoshida4", calls=4)
+
+
+# --- init and spectrum ------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_init_fluctuations_two_fields_parity(dtype):
+    """N = 48 (non-power-of-two FFT), two fields, momentum fluctuations on,
+    expanding: fields, b0 from the constraint."""
+    p = o.Params(N=48, nf=2, kIR=0.05, expanding=True, alpha=1.0, lam=1.0, q=100.0)
+    spec = o.InitSpec(A=1e-10, meff2=(3.0, 100.0, 0), phi0=(1.0, 0.0, 0), fluct_pi=True)
+    ophi, opi, oa, ob = o.init_fluctuations(p, 77, spec)
+    with make(p, dtype) as lat:
+        lat.init_fluctuations(77, A=1e-10, meff2=(3.0, 100.0, 0), phi0=(1.0, 0, 0), fluct_pi=True)
+        gphi, gpi = lat.get_all()
+        E = lat.energies()
+    tol = 1e-9 if dtype == "f64" else 2e-2
+    assert np.max(np.abs(gphi[0] - ophi[0])) / np.max(np.abs(ophi[0] - 1.0)) < tol
+    assert normwise(gphi[1], ophi[1]) < (1e-9 if dtype == "f64" else 1e-6)
+    assert normwise(gpi, opi) < (1e-9 if dtype == "f64" else 1e-6)
+    assert abs(E.b - ob) / ob < (1e-12 if dtype == "f64" else 1e-6)
+    assert E.hubble_resid < 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_spectrum_parity(dtype):
+    p = o.Params(N=48, nf=1, kIR=0.1)
+    npd = np.float32 if dtype == "f32" else np.float64
+    phi0, pi0 = white_noise_state(48, 1, seed=5, phi0=(0.5,), sigma_phi=0.1, sigma_pi=0.2)
+    phi0, pi0 = phi0.astype(npd), pi0.astype(npd)
+    with make(p, dtype) as lat:
+        lat.set_state(phi0, pi0)
+        for which, arr in ((0, phi0), (1, pi0)):
+            k, P, c = lat.spectrum(0, which)
+            ok, oP, oc = o.spectrum(p, arr[0].astype(np.float64))
+            assert np.array_equal(c, oc)
+            assert np.max(np.abs(k - ok)) < 1e-12
+            assert np.max(np.abs(P - oP) / np.maximum(oP, 1e-300)) < 1e-10
+
+
+# --- properties of the GPU path ---------------------------------------------------------
+
+def test_reversibility_on_gpu():
+    p = o.Params(N=32, nf=2, kIR=0.5, expanding=True, alpha=1.0, lam=1.0, q=50.0)
+    phi0, pi0 = white_noise_state(32, 2, seed=33, phi0=(1.0, 0.1), sigma_phi=1e-2, sigma_pi=1e-2)
+    with make(p, "f64") as lat:
+        lat.set_state(phi0, pi0, 1.0, 0.0, b_from_constraint=True)
+        b0 = lat.energies().b
+        lat.step(50, 0.01, "yoshida4")
+        assert lat.energies().a > 1.1
+        lat.step(50, -0.01, "yoshida4")
+        phi, pi = lat.get_all()
+        E = lat.energies()
+    assert normwise(phi, phi0) < 1e-12 and normwise(pi, pi0) < 1e-11
+    assert abs(E.a - 1.0) < 1e-13 and abs(E.b - b0) / b0 < 1e-12
+
+
+def test_bitwise_determinism_and_leapfrog_equals_verlet():
+    p = o.Params(N=40, nf=2, kIR=0.5, expanding=True, alpha=1.0, lam=1.0, q=100.0)
+    phi0, pi0 = white_noise_state(40, 2, seed=44, phi0=(1.0, 0.0), sigma_phi=1e-2, sigma_pi=1e-2)
+    outs = []
+    for integ in ("verlet", "verlet", "leapfrog"):
+        with make(p, "f32") as lat:
+            lat.set_state(phi0.astype(np.float32), pi0.astype(np.float32), 1.0, 0.0, True)
+            lat.step(30, 0.01, integ)
+            outs.append((*lat.get_all(), lat.energies()))
+    for other in outs[1:]:
+        assert np.array_equal(outs[0][0], other[0]) and np.array_equal(outs[0][1], other[1])
+        assert np.array_equal(outs[0][2].vector(), other[2].vector())
+        assert outs[0][2].a == other[2].a and outs[0][2].b == other[2].b
+
+
+def test_nonfinite_state_reports_unstable():
+    p = o.Params(N=16, nf=1, kIR=0.5, lam=1.0)
+    phi0, pi0 = white_noise_state(16, 1, seed=1)
+    phi0[0, 3, 4, 5] = np.inf
+    with make(p, "f64") as lat:
+        lat.set_state(phi0, pi0)
+        lat.step(2, 0.01, "verlet")
+        with pytest.raises(T.TLError) as e:
+            lat.energies()
+        assert e.value.code == T.EUNSTABLE
+
+
+def test_argument_errors():
+    with pytest.raises(T.TLError) as e:
+        T.Lattice(30, 0.5, 1, "f64")
+    assert e.value.code == T.EINVAL
+    with pytest.raises(T.TLError) as e:
+        T.Lattice(32, 0.5, 4, "f64")
+    assert e.value.code == T.EINVAL
+    with T.Lattice(16, 0.5, 1, "f64") as lat:
+        with pytest.raises(T.TLError) as e:
+            lat.step(1, 0.01)
+        assert e.value.code == T.ESTATE
+        lat.set_potential(1.0)
+        with pytest.raises(T.TLError) as e:
+            lat.step(1, 0.01)
+        assert e.value.code == T.ESTATE
+        with pytest.raises(T.TLError) as e:
+            T.tl_get_state(lat.h, 1, 0, np.empty((16, 16, 16)))
+        assert e.value.code == T.EINVAL
+        with pytest.raises(T.TLError) as e:
+            T.tl_get_state(lat.h, 0, 0, np.empty((16, 16, 15)))
+        assert e.value.code == T.EINVAL
+        with pytest.raises(T.TLError) as e:
+            T.tl_step(lat.h, 1, 0.01, 7)
+        assert e.value.code in (T.EINVAL, T.ESTATE)
