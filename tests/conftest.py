@@ -10,4 +10,4 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300); calls through the C-ABI library")
-    config.addinivalue_line("markers", "slow: long-running test")
+    config.addinivalue_line("markers", "slow: long-running test (large lattices)")

@@ -427,3 +427,18 @@ def test_philox_uniform_statistics():
     w3 = o.philox2x64(np.arange(n, dtype=np.uint64), 0, 12346)
     assert not np.any(np.all(w == w2, axis=1)) and not np.any(np.all(w == w3, axis=1))
     assert len(np.unique(w[:, 0])) == n
+
+
+# --- 14. site-local step equals the whole-lattice step -------------------------------
+
+def test_vv_step_at_sites_matches_full_step():
+    """The sampled-site evaluation used at full lattice sizes is the same
+    operator sequence restricted to each output's 5^3 neighbourhood."""
+    from paper_2607_24908_gb300.workloads import sample_sites
+    p = o.Params(N=12, nf=2, kIR=0.5, lam=1.0, q=30.0, m2=(0.1, 0.2, 0))
+    phi, pi = white_noise_state(12, 2, seed=3, phi0=(1.0, 0.2), sigma_phi=0.1, sigma_pi=0.1)
+    s = sample_sites(12, 300, seed=1)
+    a, b = o.vv_step_at_sites(p, phi, pi, s, 0.03)
+    f, g, _, _ = o.run(p, phi, pi, 1.0, 0.0, 0.03, 1, o.VERLET)
+    assert np.max(np.abs(a - f[:, s[:, 0], s[:, 1], s[:, 2]].T)) < 1e-15
+    assert np.max(np.abs(b - g[:, s[:, 0], s[:, 1], s[:, 2]].T)) < 1e-15
