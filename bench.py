@@ -88,7 +88,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -212,7 +212,9 @@ def run_ours(args):
             torch.cuda.synchronize()
 
     integ = T.INTEGRATORS[WL.integrator]
-    lat = T.Lattice(WL.N, WL.kIR, WL.nf, WL.dtype, WL.expanding, WL.alpha, WL.fstar_over_mp, 1.0, stream=sptr)
+    N = args.N or WL.N
+    kIR = WL.kIR * WL.N / N  # same lattice spacing dx when N is reduced for profiling
+    lat = T.Lattice(N, kIR, WL.nf, WL.dtype, WL.expanding, WL.alpha, WL.fstar_over_mp, 1.0, stream=sptr)
     lat.set_potential(WL.lam, WL.q, WL.m2)
     lat.init_fluctuations(WL.seed + 1000 * rank, A=WL.A, meff2=WL.meff2, phi0=WL.phi0)
 
@@ -244,7 +246,7 @@ def run_ours(args):
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_max = float(t.item())
-    sites = WL.N ** 3
+    sites = N ** 3
     work_per_rank = sites * WL.nf * PASSES * args.steps
     value = work_per_rank * ws / (t_max / 1e3)
 
@@ -252,7 +254,13 @@ def run_ours(args):
     # pinned memory, K steps, energies and D2H of the state, every call inside
     # the timed region.
     npd = np.float32 if WL.dtype == "f32" else np.float64
-    host = [torch.empty((WL.N,) * 3, dtype=torch.float32 if WL.dtype == "f32" else torch.float64,
+    if args.no_e2e:
+        lat.close()
+        t_e2e, E2 = float("nan"), E
+        state_bytes = 2 * WL.nf * sites * np.dtype(npd).itemsize
+        return _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_rank, t_e2e, state_bytes,
+                       E, E2, clk)
+    host = [torch.empty((N,) * 3, dtype=torch.float32 if WL.dtype == "f32" else torch.float64,
                         pin_memory=True) for _ in range(2 * WL.nf)]
     for f in range(WL.nf):
         for w in range(2):
@@ -274,9 +282,15 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         t_e2e = float(t.item())
     state_bytes = 2 * WL.nf * sites * np.dtype(npd).itemsize
-    e2e_value = work_per_rank * ws / t_e2e
     lat.close()
+    return _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_rank, t_e2e, state_bytes,
+                   E, E2, clk)
 
+
+def _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_rank, t_e2e, state_bytes, E, E2, clk):
+    import torch
+    sites = N ** 3
+    e2e_value = work_per_rank * ws / t_e2e if t_e2e == t_e2e else None
     if rank == 0:
         peak, peak_kind = peaks()
         alg_bytes = sites * WL.nf * BYTES_PER_SITE_FIELD_PASS
@@ -288,12 +302,13 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": WL.dtype, "data": "synthetic",
-            "config": {"workload": WL.name, "N": WL.N, "n_fields": WL.nf, "integrator": WL.integrator,
+            "config": {"workload": WL.name if N == WL.N else f"{WL.name} reduced to {N}^3 (same dx)", "N": N, "n_fields": WL.nf, "integrator": WL.integrator,
                        "passes_per_step": PASSES, "dt": WL.dt, "storage": "fp32 fields/momenta, fp64 reductions",
-                       "l2": "inputs (32 GiB state) larger than L2; no flush", "parallelism": f"replicas x{ws}"},
+                       "l2": f"inputs ({4 * WL.nf * sites * (4 if WL.dtype == 'f32' else 8) / 2**30:.1f} GiB "
+                             "state) larger than L2; no flush", "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
-                         "traffic": measured_traffic(), "algorithmic_bytes_per_launch": alg_bytes,
+                         "traffic": measured_traffic() if N == WL.N else None, "algorithmic_bytes_per_launch": alg_bytes,
                          "kernel": "fused_pass<float,2>", "ms_per_launch": ms_pass},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": state_bytes / args.steps,
@@ -312,10 +327,12 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--N", type=int, default=0, help="lattice size (default: the workload's 1024; for profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: warm-up raised to the minimum of 3 steps", file=sys.stderr)
