@@ -175,6 +175,28 @@ int tl_set_background(tl_lattice *lat, double a, double b, int from_constraint);
  * the next tl_step). */
 int tl_state_device_ptr(tl_lattice *lat, int field, int which, void **dev_ptr);
 
+/* Energies of a caller-owned device state, allocating no device memory.
+ * No counterpart in the paper: this serves callers that cannot call
+ * cudaMalloc (a host framework that owns all device memory, or code that must
+ * not trigger the device synchronisation an allocation can cause).
+ * phi[f], pi[f] (f < n_fields): device arrays of N^3 elements of dtype,
+ * 16-byte aligned, laid out as in tl_get_state; pot: the potential;
+ * expansion: NULL or static for a = 1 weights, else the scale factor a
+ * weighs K by a^-6 and G by a^-2.  out: host array of 2 n_fields + 1
+ * doubles, K_0.., G_0.., V.  The pass runs on cuda_stream and the call
+ * synchronises it.
+ * Scratch: a fixed 917,760-byte array inside the library (static device memory that
+ * every GPU loading the library holds until exit) with room for 16384 CTA
+ * partial sums, enough for N <= 1024 in both precisions; larger lattices get
+ * TL_EINVAL.  The first call on each device looks up the array's address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.
+ * Errors: TL_EINVAL, TL_ECUDA, TL_EUNSTABLE (non-finite energies). */
+int tl_energies_noalloc(int N, double kIR, int n_fields, tl_dtype dtype, const tl_potential *pot,
+                        const tl_expansion *expansion, double a, const void *const *phi, const void *const *pi,
+                        void *cuda_stream, double *out);
+
 /* Message for the last error on this thread ("" if none). */
 const char *tl_last_error(void);
 

@@ -47,6 +47,12 @@ int fail(int code, const char *fmt, ...)
 
 }  // namespace
 
+int tl::set_error(int code, const char *msg, const char *detail)
+{
+    snprintf(g_err, sizeof g_err, "%s%s", msg, detail);
+    return code;
+}
+
 struct tl_lattice {
     int N = 0, nf = 0;
     double kIR = 0.0, dx = 0.0;

@@ -73,6 +73,9 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count);
 cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,
                         Scalars *sc, double *slots, bool measure_only, cudaStream_t s);
 
+// Record msg+detail as this thread's tl_last_error() text; returns code.
+int set_error(int code, const char *msg, const char *detail);
+
 // Set a, b (and the derived weights) on the device; drift = 0.
 cudaError_t launch_set_background(const Model &m, Scalars *sc, double a, double b, cudaStream_t s);
 

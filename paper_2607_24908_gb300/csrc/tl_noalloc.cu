@@ -1,0 +1,118 @@
+// tl_energies_noalloc: volume-averaged energies of a caller-owned device
+// state with no device allocation at all.
+//
+// Some callers cannot call cudaMalloc: code embedded in a host framework that
+// reserves all device memory up front and hands out only its own buffers,
+// and code that must not allocate because cudaMalloc/cudaFree may
+// synchronise the device and stall other work in flight.  For them this
+// entry point runs the fused pass in measurement mode with its reduction
+// scratch (per-CTA partial sums, the arrival ticket and the scalar block) in
+// a fixed static device array that every GPU loading this library holds
+// until the process exits.
+#include <math.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "tl_internal.cuh"
+
+namespace {
+
+// Scratch capacity: the scalar block plus kMaxSlotBlocks CTA slots of
+// kMaxQ doubles.  16384 slots cover every lattice up to 1024^3 in both
+// precisions with the default launch geometry.
+constexpr size_t kMaxSlotBlocks = 16384;
+constexpr size_t kScalarsBytes = (sizeof(tl::Scalars) + 255) / 256 * 256;
+constexpr size_t kScratchBytes = kScalarsBytes + kMaxSlotBlocks * tl::kMaxQ * sizeof(double);
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_scratch_ptr[kMaxDevices] = {nullptr};
+
+int fail(int code, const char *msg, const char *detail = "") { return tl::set_error(code, msg, detail); }
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current.
+int scratch_ptr(void **out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(TL_ECUDA, "cudaGetDevice: ", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(TL_ECUDA, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return fail(TL_ECUDA, "cudaGetSymbolAddress: ", cudaGetErrorString(e));
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return TL_OK;
+}
+
+}  // namespace
+
+extern "C" int tl_energies_noalloc(int N, double kIR, int n_fields, tl_dtype dtype, const tl_potential *pot,
+                                   const tl_expansion *expansion, double a, const void *const *phi,
+                                   const void *const *pi, void *cuda_stream, double *out)
+{
+    tl::set_error(TL_OK, "", "");
+    if (N < 8 || N % 4 != 0 || N > 2048) return fail(TL_EINVAL, "N must be a multiple of 4 in [8, 2048]");
+    if (!(kIR > 0.0)) return fail(TL_EINVAL, "kIR must be positive");
+    if (n_fields < 1 || n_fields > TL_MAX_FIELDS) return fail(TL_EINVAL, "n_fields must be 1..3");
+    if (dtype != TL_F32 && dtype != TL_F64) return fail(TL_EINVAL, "unknown dtype");
+    if (!pot || !phi || !pi || !out) return fail(TL_EINVAL, "NULL argument");
+    if (!(a > 0.0)) return fail(TL_EINVAL, "a must be positive");
+    for (int f = 0; f < n_fields; ++f)
+        if (!phi[f] || !pi[f] || ((uintptr_t)phi[f] & 15u) || ((uintptr_t)pi[f] & 15u))
+            return fail(TL_EINVAL, "field pointers must be non-NULL and 16-byte aligned");
+
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(TL_ECUDA, "device query: ", cudaGetErrorString(e));
+    const tl::PassGeom g = tl::pass_geometry(N, dtype == TL_F32 ? 4 : 8, sms);
+    if (g.nblocks > kMaxSlotBlocks)
+        return fail(TL_EINVAL, "lattice needs more reduction slots than the static scratch holds (max 16384 CTAs)");
+
+    void *base = nullptr;
+    int rc = scratch_ptr(&base);
+    if (rc) return rc;
+    tl::Scalars *sc = static_cast<tl::Scalars *>(base);
+    double *slots = reinterpret_cast<double *>(static_cast<unsigned char *>(base) + kScalarsBytes);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+    tl::Model m{};
+    m.N = N;
+    m.nf = n_fields;
+    m.expanding = (expansion && expansion->expanding) ? 1 : 0;
+    m.alpha = m.expanding ? expansion->alpha : 0.0;
+    m.mu2 = m.expanding ? expansion->fstar_over_mp * expansion->fstar_over_mp : 1.0;
+    const double dx = 2.0 * M_PI / (kIR * N);
+    m.inv_dx2 = 1.0 / (dx * dx);
+    m.lambda = pot->lambda;
+    m.q = pot->q;
+    for (int f = 0; f < TL_MAX_FIELDS; ++f) m.m2[f] = pot->m2[f];
+
+    // The scratch keeps the previous call's contents: reset the scalar block
+    // (ticket, status, weights for a) before the pass.
+    e = cudaMemsetAsync(sc, 0, sizeof(tl::Scalars), s);
+    if (e == cudaSuccess) e = tl::launch_set_background(m, sc, a, 0.0, s);
+    tl::FieldPtrs fp{};
+    for (int f = 0; f < n_fields; ++f) {
+        fp.phi_in[f] = phi[f];
+        fp.pi_in[f] = pi[f];
+    }
+    tl::PassCoef c{};
+    c.integer_time = 1;
+    if (e == cudaSuccess) e = tl::launch_pass((int)dtype, m, fp, c, g, sc, slots, true, s);
+    tl::Scalars h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(TL_ECUDA, "energy pass: ", cudaGetErrorString(e));
+    for (int i = 0; i < 2 * n_fields + 1; ++i) out[i] = h.E[i];
+    if (h.status != TL_OK) return fail(TL_EUNSTABLE, "energies are not finite");
+    return TL_OK;
+}

@@ -79,6 +79,11 @@ _SIGS = {
     "tl_set_background": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
     "tl_state_device_ptr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_void_p)]),
+    "tl_energies_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(tl_potential), ctypes.POINTER(tl_expansion),
+                                           ctypes.c_double, ctypes.POINTER(ctypes.c_void_p),
+                                           ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_double)]),
     "tl_last_error": (ctypes.c_char_p, []),
 }
 
@@ -194,6 +199,20 @@ def tl_state_device_ptr(h, field: int, which: int) -> int:
     p = ctypes.c_void_p()
     _check(lib().tl_state_device_ptr(h, field, which, ctypes.byref(p)))
     return p.value or 0
+
+
+def tl_energies_noalloc(N: int, kIR: float, n_fields: int, dtype: int, lam: float, q: float, m2,
+                        expansion: Optional[tl_expansion], a: float, phi_ptrs: Sequence[int],
+                        pi_ptrs: Sequence[int], cuda_stream: int = 0) -> np.ndarray:
+    """Energies [K_0.., G_0.., V] of caller-owned device arrays; allocates nothing on the device."""
+    pot = tl_potential(lam, q, _f3(m2))
+    ph = (ctypes.c_void_p * n_fields)(*phi_ptrs)
+    pp = (ctypes.c_void_p * n_fields)(*pi_ptrs)
+    out = np.zeros(2 * n_fields + 1)
+    _check(lib().tl_energies_noalloc(N, kIR, n_fields, dtype, ctypes.byref(pot),
+                                     ctypes.byref(expansion) if expansion is not None else None, a, ph, pp,
+                                     ctypes.c_void_p(cuda_stream), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
 
 
 # --- convenience wrapper --------------------------------------------------------
