@@ -4,6 +4,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -46,6 +47,13 @@ int fail(int code, const char *fmt, ...)
     } while (0)
 
 }  // namespace
+
+int tl::default_variant()
+{
+    const char *v = getenv("TL_PASS_VARIANT");
+    if (v && strcmp(v, "ldg") == 0) return tl::kVariantLdg;
+    return tl::kVariantBulk;
+}
 
 int tl::set_error(int code, const char *msg, const char *detail)
 {
@@ -129,7 +137,7 @@ int finish_create(tl_lattice *L, int N, double kIR, int nf, tl_dtype dtype, cons
     int dev = 0;
     TL_CK(cudaGetDevice(&dev));
     TL_CK(cudaDeviceGetAttribute(&L->sm_count, cudaDevAttrMultiProcessorCount, dev));
-    L->geom = tl::pass_geometry(N, (int)L->esz, L->sm_count);
+    L->geom = tl::pass_geometry(N, (int)L->esz, L->sm_count, nf, tl::default_variant());
     TL_CK(cudaMalloc(&L->d_sc, sizeof(Scalars)));
     TL_CK(cudaMemset(L->d_sc, 0, sizeof(Scalars)));
     TL_CK(cudaMalloc(&L->d_slots, sizeof(double) * tl::kMaxQ * L->geom.nblocks));
@@ -368,6 +376,7 @@ int tl_energies(tl_lattice *L, tl_energies_t *out)
     }
     out->V = h.E[2 * L->nf];
     out->hubble_resid = h.hubble;
+    if (h.status == TL_ETIMEOUT) return fail(TL_ETIMEOUT, "a bounded device wait expired during a pass");
     if (h.status != TL_OK) return fail(TL_EUNSTABLE, "energies became non-finite");
     return TL_OK;
 }
@@ -382,6 +391,7 @@ int tl_get_state(tl_lattice *L, int field, int which, void *host, size_t bytes)
     Scalars h;
     rc = read_scalars(L, &h);
     if (rc) return rc;
+    if (h.status == TL_ETIMEOUT) return fail(TL_ETIMEOUT, "a bounded device wait expired during a pass");
     if (h.status != TL_OK) return fail(TL_EUNSTABLE, "evolution became non-finite");
     return TL_OK;
 }

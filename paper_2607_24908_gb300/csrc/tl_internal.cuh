@@ -58,6 +58,11 @@ struct FieldPtrs {
     void *pi_out[kMaxFields];
 };
 
+// Fused-pass variants: per-thread loads through L1/L2, or z-planes staged in
+// shared memory by bulk asynchronous copies.
+constexpr int kVariantLdg = 0;
+constexpr int kVariantBulk = 1;
+
 // Launch geometry of the fused pass.
 struct PassGeom {
     int txt;  // threads along x (each owns VEC consecutive sites)
@@ -65,9 +70,15 @@ struct PassGeom {
     int zc;   // z-planes per CTA
     dim3 grid;
     unsigned nblocks;
+    int variant;   // kVariantLdg or kVariantBulk
+    int stages;    // shared-memory ring depth (bulk variant)
+    size_t smem;   // dynamic shared memory per CTA (bulk variant)
 };
 
-PassGeom pass_geometry(int N, int elem_bytes, int sm_count);
+PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, int variant);
+
+// Default variant: TL_PASS_VARIANT=ldg|bulk in the environment, else bulk.
+int default_variant();
 
 // Enqueue one fused pass (measure_only: energies of the stored state, no writes).
 cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,
