@@ -48,11 +48,16 @@ int fail(int code, const char *fmt, ...)
 
 }  // namespace
 
-int tl::default_variant()
+tl::PassTuning tl::default_tuning()
 {
+    tl::PassTuning t{tl::kVariantLdg, 8, 0, 0, -1};
     const char *v = getenv("TL_PASS_VARIANT");
-    if (v && strcmp(v, "ldg") == 0) return tl::kVariantLdg;
-    return tl::kVariantBulk;
+    if (v && strcmp(v, "bulk") == 0) t.variant = tl::kVariantBulk;
+    if ((v = getenv("TL_PREFETCH"))) t.prefetch = atoi(v);
+    if ((v = getenv("TL_BULK_WARPS"))) t.cwarps = atoi(v);
+    if ((v = getenv("TL_BULK_STAGES"))) t.stages = atoi(v);
+    if ((v = getenv("TL_PASS_ZC"))) t.zc = atoi(v);
+    return t;
 }
 
 int tl::set_error(int code, const char *msg, const char *detail)
@@ -90,6 +95,16 @@ struct tl_lattice {
 namespace {
 
 size_t n3_of(int N) { return (size_t)N * (size_t)N * (size_t)N; }
+
+// Bytes between consecutive field arrays beyond their size (TL_ARRAY_STAGGER,
+// rounded to 256 bytes; default 0).
+size_t array_stagger()
+{
+    const char *v = getenv("TL_ARRAY_STAGGER");
+    long b = v ? atol(v) : 0;
+    if (b < 0) b = 0;
+    return (size_t)((b + 255) / 256 * 256);
+}
 
 int check_dims(int N, double kIR, int n_fields, tl_dtype dtype, const tl_expansion *ex)
 {
@@ -137,7 +152,7 @@ int finish_create(tl_lattice *L, int N, double kIR, int nf, tl_dtype dtype, cons
     int dev = 0;
     TL_CK(cudaGetDevice(&dev));
     TL_CK(cudaDeviceGetAttribute(&L->sm_count, cudaDevAttrMultiProcessorCount, dev));
-    L->geom = tl::pass_geometry(N, (int)L->esz, L->sm_count, nf, tl::default_variant());
+    L->geom = tl::pass_geometry(N, (int)L->esz, L->sm_count, nf, tl::default_tuning());
     TL_CK(cudaMalloc(&L->d_sc, sizeof(Scalars)));
     TL_CK(cudaMemset(L->d_sc, 0, sizeof(Scalars)));
     TL_CK(cudaMalloc(&L->d_slots, sizeof(double) * tl::kMaxQ * L->geom.nblocks));
@@ -208,7 +223,10 @@ int tl_lattice_create(tl_lattice **out, int N, double kIR, int n_fields, tl_dtyp
     if (rc) return rc;
     tl_lattice *L = new (std::nothrow) tl_lattice();
     if (!L) return fail(TL_ENOMEM, "host allocation failed");
-    const size_t bytes = tl_state_bytes(N, n_fields, dtype);
+    // Arrays are staggered by a few KiB so that the 4 n_fields streams of a
+    // pass do not sit at identical offsets modulo large powers of two.
+    const size_t stagger = array_stagger();
+    const size_t bytes = tl_state_bytes(N, n_fields, dtype) + 4 * (size_t)n_fields * stagger;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
         delete L;
@@ -228,7 +246,10 @@ int tl_lattice_create(tl_lattice **out, int N, double kIR, int n_fields, tl_dtyp
     memset(L->buf, 0, sizeof L->buf);
     for (int f = 0; f < n_fields; ++f)
         for (int par = 0; par < 2; ++par)
-            for (int w = 0; w < 2; ++w) L->buf[par][w][f] = p + ((size_t)(4 * f + 2 * par + w)) * arr;
+            for (int w = 0; w < 2; ++w) {
+                const size_t k = (size_t)(4 * f + 2 * par + w);
+                L->buf[par][w][f] = p + k * (arr + stagger);
+            }
     rc = finish_create(L, N, kIR, n_fields, dtype, expansion, cuda_stream);
     if (rc) {
         tl_lattice_destroy(L);

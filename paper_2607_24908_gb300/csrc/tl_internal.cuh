@@ -63,6 +63,15 @@ struct FieldPtrs {
 constexpr int kVariantLdg = 0;
 constexpr int kVariantBulk = 1;
 
+// Tunable launch parameters of the fused pass (0 = choose automatically).
+struct PassTuning {
+    int variant;  // kVariantLdg or kVariantBulk
+    int cwarps;   // bulk: compute warps per CTA (4 or 8; one producer warp is added)
+    int stages;   // bulk: shared-memory ring depth in z-planes (3..8)
+    int zc;       // z-planes per CTA
+    int prefetch; // ldg: planes prefetched per thread with cp.async (0, 2, 3, 4; -1 = default 3)
+};
+
 // Launch geometry of the fused pass.
 struct PassGeom {
     int txt;  // threads along x (each owns VEC consecutive sites)
@@ -71,14 +80,17 @@ struct PassGeom {
     dim3 grid;
     unsigned nblocks;
     int variant;   // kVariantLdg or kVariantBulk
+    int cwarps;    // compute warps per CTA
     int stages;    // shared-memory ring depth (bulk variant)
-    size_t smem;   // dynamic shared memory per CTA (bulk variant)
+    int prefetch;  // per-thread prefetch depth (ldg variant)
+    size_t smem;   // dynamic shared memory per CTA
 };
 
-PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, int variant);
+PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTuning &t);
 
-// Default variant: TL_PASS_VARIANT=ldg|bulk in the environment, else bulk.
-int default_variant();
+// Tuning from the environment (TL_PASS_VARIANT=ldg|bulk, TL_PREFETCH,
+// TL_BULK_WARPS, TL_BULK_STAGES, TL_PASS_ZC), else the built-in defaults.
+PassTuning default_tuning();
 
 // Enqueue one fused pass (measure_only: energies of the stored state, no writes).
 cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,

@@ -215,7 +215,7 @@ template <int NQ>
 __device__ __forceinline__ void cta_reduce_finalize(const double (&accd)[NQ], const Model &m, const PassCoef &c,
                                                     Scalars *sc, double *slots)
 {
-    __shared__ double red[8][NQ];
+    __shared__ double red[16][NQ];
     __shared__ bool last;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -265,23 +265,43 @@ __device__ __forceinline__ void cta_reduce_finalize(const double (&accd)[NQ], co
     }
 }
 
-// ---- variant 1: register streaming --------------------------------------------
-// Each thread loads its own 128-bit words with ld.global.nc (the next plane's
-// centre, the neighbour rows and edge sites through L1/L2); no shared memory.
+// ---- variant 1: register streaming with a per-thread prefetch ring -------------
+// Each thread owns its 128-bit words.  The HBM stream (the stored phi and pi
+// of its own sites, plane after plane) is prefetched D planes ahead with
+// cp.async into a private shared-memory ring (no CTA barrier: a thread only
+// waits for its own copies); the neighbour rows and edge sites of plane z are
+// other threads' words of the same plane and come from L1/L2 with ld.global.
+// D = 0 loads the next plane directly, without the ring.
 
-template <typename T, int NF, bool MEASURE>
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int Npending>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(Npending) : "memory"); }
+
+template <typename T, int NF, bool MEASURE, int D>
 __global__ void __launch_bounds__(256) fused_pass_ldg(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
                                                       Scalars *sc, double *slots)
 {
     constexpr int W = Vec<T>::W;
     constexpr int NQ = 2 * NF + 1;
+    extern __shared__ __align__(16) unsigned char ring_raw[];
     const int N = m.N;
-    const int tx = threadIdx.x % txt, tyi = threadIdx.x / txt;
+    const int tid = threadIdx.x;
+    const int tx = tid % txt, tyi = tid / txt;
     const int x0 = (blockIdx.x * txt + tx) * W;
     const int y = blockIdx.y * ty + tyi;
     const int z0 = blockIdx.z * zc;
     const int z1 = min(z0 + zc, N);
     const bool active = (tyi < ty) && (x0 < N) && (y < N);
+    // ring slot (plane d, field f, array a) of this thread
+    auto slot = [&](int d, int f, int a) -> T * {
+        return reinterpret_cast<T *>(ring_raw) + ((size_t)((d * NF + f) * 2 + a) * blockDim.x + tid) * W;
+    };
 
     double accd[NQ];
 #pragma unroll
@@ -314,6 +334,19 @@ __global__ void __launch_bounds__(256) fused_pass_ldg(Model m, FieldPtrs fp, Pas
         auto cur_one = [&](int f, size_t off) -> T {
             return fma_t(k.drift, __ldg(pis[f] + off), __ldg(phs[f] + off));
         };
+        auto plane_off = [&](int zz) -> size_t { return (size_t)(zz >= N ? zz - N : zz) * NN + row + x0; };
+        // prefetch this thread's words of plane zz (<= z1) into ring slot d
+        auto prefetch = [&](int zz, int d) {
+            if (zz <= z1) {
+                const size_t off = plane_off(zz);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    cp_async16(slot(d, f, 0), phs[f] + off);
+                    cp_async16(slot(d, f, 1), pis[f] + off);
+                }
+            }
+            cp_async_commit();
+        };
 
         T zm[NF][W], cu[NF][W], zp[NF][W], pc[NF][W];
         {
@@ -329,22 +362,44 @@ __global__ void __launch_bounds__(256) fused_pass_ldg(Model m, FieldPtrs fp, Pas
                 for (int j = 0; j < W; ++j) cu[f][j] = fma_t(k.drift, pc[f][j], a[j]);
             }
         }
+        if (D > 0) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) prefetch(z0 + 1 + d, d);
+        }
         T acc[NQ];
 #pragma unroll
         for (int i = 0; i < NQ; ++i) acc[i] = (T)0;
 
+        int d = 0;  // ring slot holding plane z+1
         for (int z = z0; z < z1; ++z) {
             const size_t pz = (size_t)z * NN;
-            const size_t pn = (size_t)((z + 1 == N) ? 0 : z + 1) * NN;
             T pnext[NF][W];
+            if (D > 0) {
+                cp_async_wait<(D > 0 ? D - 1 : 0)>();
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    T a[W];
+                    load_vec_s(slot(d, f, 0), a);
+                    load_vec_s(slot(d, f, 1), pnext[f]);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) zp[f][j] = fma_t(k.drift, pnext[f][j], a[j]);
+                }
+                prefetch(z + 1 + D, d);
+                d = (d + 1 == D) ? 0 : d + 1;
+            } else {
+                const size_t pn = plane_off(z + 1);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    T a[W];
+                    load_vec(phs[f] + pn, a);
+                    load_vec(pis[f] + pn, pnext[f]);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) zp[f][j] = fma_t(k.drift, pnext[f][j], a[j]);
+                }
+            }
             T ym[NF][W], yp[NF][W], xlv[NF], xrv[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                T a[W];
-                load_vec(phs[f] + pn + row + x0, a);
-                load_vec(pis[f] + pn + row + x0, pnext[f]);
-#pragma unroll
-                for (int j = 0; j < W; ++j) zp[f][j] = fma_t(k.drift, pnext[f][j], a[j]);
                 cur_vec(f, pz + rowm + x0, ym[f]);
                 cur_vec(f, pz + rowp + x0, yp[f]);
                 xlv[f] = cur_one(f, pz + row + xl);
@@ -355,8 +410,8 @@ __global__ void __launch_bounds__(256) fused_pass_ldg(Model m, FieldPtrs fp, Pas
             if (!MEASURE) {
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    store_vec(pho[f] + pz + row + x0, cu[f]);
-                    store_vec(pio[f] + pz + row + x0, pnew[f]);
+                    store_vec_cs(pho[f] + pz + row + x0, cu[f]);
+                    store_vec_cs(pio[f] + pz + row + x0, pnew[f]);
                 }
             }
             if (((z - z0) & 15) == 15) {
@@ -375,6 +430,7 @@ __global__ void __launch_bounds__(256) fused_pass_ldg(Model m, FieldPtrs fp, Pas
                     pc[f][j] = pnext[f][j];
                 }
         }
+        if (D > 0) cp_async_wait<0>();
 #pragma unroll
         for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
     }
@@ -463,159 +519,173 @@ __device__ __forceinline__ void copy_row(T *dst, const T *row, int xs, int len, 
     }
 }
 
-template <typename T, int NF, bool MEASURE, int S>
-__global__ void __launch_bounds__(256) fused_pass_bulk(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
-                                                       Scalars *sc, double *slots)
+// Warp-specialised: warps 0..CW-1 compute, warp CW produces.  The producer
+// runs up to S planes ahead: before refilling a stage it waits on that
+// stage's "empty" mbarrier, which each consumer warp arrives on once it is done
+// with the plane; consumers wait on the stage's "full" mbarrier (completed by
+// the bulk copies' byte count).  No CTA-wide barrier inside the z loop.
+constexpr int kMaxStages = 8;
+
+template <typename T, int NF, bool MEASURE>
+__global__ void __launch_bounds__(288, 2) fused_pass_bulk(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
+                                                          int S, Scalars *sc, double *slots)
 {
     constexpr int W = Vec<T>::W;
     constexpr int NQ = 2 * NF + 1;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bars[S];
-    __shared__ int s_failed;
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+    __shared__ volatile int s_failed;
     T *stage_base = reinterpret_cast<T *>(smem_raw);
 
     const int N = m.N;
     const int tid = threadIdx.x;
-    const int tx = tid % txt, tyi = tid / txt;
+    const int CW = (blockDim.x >> 5) - 1;  // consumer warps
+    const bool producer = (tid >> 5) == CW;
     const int x_tile = blockIdx.x * txt * W, y_tile = blockIdx.y * ty;
-    const int x0 = x_tile + tx * W;
-    const int y = y_tile + tyi;
     const int z0 = blockIdx.z * zc;
     const int z1 = min(z0 + zc, N);
     const int K = (z1 - z0) + 2;  // planes z0-1 .. z1
-    const bool active = (tyi < ty) && (x0 < N) && (y < N);
-    const int rowe = txt * W + 2 * W;      // elements per staged row
-    const int plane = (ty + 2) * rowe;     // elements per staged plane of one array
+    const int rowe = txt * W + 2 * W;
+    const int plane = (ty + 2) * rowe;
     const uint32_t plane_bytes = (uint32_t)(NF * 2 * plane * sizeof(T));
     const size_t NN = (size_t)N * (size_t)N;
-
     auto arr = [&](int s, int f, int a) -> T * { return stage_base + (size_t)((s * NF + f) * 2 + a) * plane; };
 
-    // warp 0 issues plane k (z = z0 - 1 + k) into stage k % S
-    auto issue = [&](int k) {
-        const int s = k % S;
-        const int zg = (z0 - 1 + k + N) % N;
-        const int lane = tid & 31;
-        if (lane == 0) mbar_arrive_expect_tx(&bars[s], plane_bytes);
-        __syncwarp();
-        for (int item = lane; item < NF * 2 * (ty + 2); item += 32) {
-            const int f = item / (2 * (ty + 2));
-            const int rem = item - f * 2 * (ty + 2);
-            const int a = rem / (ty + 2);
-            const int r = rem - a * (ty + 2);
-            const int yg = (y_tile - 1 + r + N) % N;
-            const T *src = static_cast<const T *>(a == 0 ? fp.phi_in[f] : fp.pi_in[f]) + ((size_t)zg * NN + (size_t)yg * N);
-            copy_row<T>(arr(s, f, a) + r * rowe, src, x_tile - W, rowe, N, &bars[s]);
-        }
-    };
-
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CW);
+        }
         s_failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (tid < 32)
-        for (int k = 0; k < S && k < K; ++k) issue(k);
 
     double accd[NQ];
 #pragma unroll
     for (int i = 0; i < NQ; ++i) accd[i] = 0.0;
-    T acc[NQ];
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) acc[i] = (T)0;
+    int issued = 0;
 
-    const Coefs<T, NF> k(m, c, sc);
-    const int ctr = (tyi + 1) * rowe + (tx + 1) * W;  // this thread's centre word in a staged plane
-    T zm[NF][W], cu[NF][W], zp[NF][W], pc[NF][W], pn[NF][W];
-
-    // centre phi (drifted) and pi of plane kk
-    auto centre = [&](int kk, T (&ph)[NF][W], T (&pp)[NF][W]) {
-        const int s = kk % S;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) {
-            T a[W];
-            load_vec_s(arr(s, f, 0) + ctr, a);
-            load_vec_s(arr(s, f, 1) + ctr, pp[f]);
-#pragma unroll
-            for (int j = 0; j < W; ++j) ph[f][j] = fma_t(k.drift, pp[f][j], a[j]);
+    if (producer) {
+        const int lane = tid & 31;
+        for (int k = 0; k < K; ++k) {
+            const int s = k % S;
+            if (k >= S && !mbar_wait_bounded(&empty[s], ((k / S) - 1) & 1u, sc)) {
+                s_failed = 1;
+                break;
+            }
+            if (s_failed) break;
+            const int zg = (z0 - 1 + k + N) % N;
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], plane_bytes);
+            __syncwarp();
+            for (int item = lane; item < NF * 2 * (ty + 2); item += 32) {
+                const int f = item / (2 * (ty + 2));
+                const int rem = item - f * 2 * (ty + 2);
+                const int a = rem / (ty + 2);
+                const int r = rem - a * (ty + 2);
+                const int yg = (y_tile - 1 + r + N) % N;
+                const T *src = static_cast<const T *>(a == 0 ? fp.phi_in[f] : fp.pi_in[f]) +
+                               ((size_t)zg * NN + (size_t)yg * N);
+                copy_row<T>(arr(s, f, a) + r * rowe, src, x_tile - W, rowe, N, &full[s]);
+            }
+            issued = k + 1;
         }
-    };
-
-    bool ok = true;
-    if (active) {
-        ok = mbar_wait_bounded(&bars[0], 0u, sc);
-        centre(0, zm, pn);
-        ok = ok && mbar_wait_bounded(&bars[1 % S], (1 / S) & 1u, sc);
-        centre(1, cu, pc);
-    }
-    if (!ok) s_failed = 1;
-
-    int issued = (S < K) ? S : K;
-    for (int z = z0; z < z1; ++z) {
-        const int kz = z - z0 + 1;
-        __syncthreads();  // every thread is done with plane kz-1's stage
-        if (s_failed) break;
-        if (tid < 32 && issued < K && issued == kz - 1 + S) {
-            issue(issued);
-        }
-        issued = (issued < K && issued == kz - 1 + S) ? issued + 1 : issued;
-        if (active) {
-            const int s1 = (kz + 1) % S;
-            if (!mbar_wait_bounded(&bars[s1], ((kz + 1) / S) & 1u, sc)) s_failed = 1;
-            centre(kz + 1, zp, pn);
-            const int s0 = kz % S;
-            T ym[NF][W], yp[NF][W], xlv[NF], xrv[NF];
+    } else {
+        const int lane = tid & 31;
+        const int tx = tid % txt, tyi = tid / txt;
+        const int x0 = x_tile + tx * W;
+        const int y = y_tile + tyi;
+        const bool active = (tyi < ty) && (x0 < N) && (y < N);
+        const Coefs<T, NF> k(m, c, sc);
+        const int ctr = (tyi + 1) * rowe + (tx + 1) * W;
+        T zm[NF][W], cu[NF][W], zp[NF][W], pc[NF][W], pn[NF][W];
+        T acc[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) acc[i] = (T)0;
+        auto centre = [&](int kk, T (&ph)[NF][W], T (&pp)[NF][W]) {
+            const int s = kk % S;
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                const T *ph = arr(s0, f, 0), *pp = arr(s0, f, 1);
-                T a[W], b[W];
-                load_vec_s(ph + ctr - rowe, a);
-                load_vec_s(pp + ctr - rowe, b);
+                T a[W];
+                load_vec_s(arr(s, f, 0) + ctr, a);
+                load_vec_s(arr(s, f, 1) + ctr, pp[f]);
 #pragma unroll
-                for (int j = 0; j < W; ++j) ym[f][j] = fma_t(k.drift, b[j], a[j]);
-                load_vec_s(ph + ctr + rowe, a);
-                load_vec_s(pp + ctr + rowe, b);
-#pragma unroll
-                for (int j = 0; j < W; ++j) yp[f][j] = fma_t(k.drift, b[j], a[j]);
-                xlv[f] = fma_t(k.drift, pp[ctr - 1], ph[ctr - 1]);
-                xrv[f] = fma_t(k.drift, pp[ctr + W], ph[ctr + W]);
+                for (int j = 0; j < W; ++j) ph[f][j] = fma_t(k.drift, pp[f][j], a[j]);
             }
-            T pnew[NF][W];
-            site_update<T, NF, W>(k, cu, zm, zp, ym, yp, xlv, xrv, pc, pnew, acc);
-            if (!MEASURE) {
-                const size_t off = (size_t)z * NN + (size_t)y * N + x0;
+        };
+        auto release = [&](int kk) {
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[kk % S]))
+                                        : "memory");
+        };
+        bool ok = true;
+        if (active) {
+            ok = mbar_wait_bounded(&full[0], 0u, sc);
+            centre(0, zm, pn);
+            ok = ok && mbar_wait_bounded(&full[1 % S], (1 / S) & 1u, sc);
+            centre(1, cu, pc);
+        }
+        if (!ok) s_failed = 1;
+        release(0);
+        for (int z = z0; z < z1 && !s_failed; ++z) {
+            const int kz = z - z0 + 1;
+            if (active) {
+                if (!mbar_wait_bounded(&full[(kz + 1) % S], ((kz + 1) / S) & 1u, sc)) s_failed = 1;
+                centre(kz + 1, zp, pn);
+                const int s0 = kz % S;
+                T ym[NF][W], yp[NF][W], xlv[NF], xrv[NF];
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    store_vec_cs(static_cast<T *>(fp.phi_out[f]) + off, cu[f]);
-                    store_vec_cs(static_cast<T *>(fp.pi_out[f]) + off, pnew[f]);
+                    const T *ph = arr(s0, f, 0), *pp = arr(s0, f, 1);
+                    T a[W], b[W];
+                    load_vec_s(ph + ctr - rowe, a);
+                    load_vec_s(pp + ctr - rowe, b);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) ym[f][j] = fma_t(k.drift, b[j], a[j]);
+                    load_vec_s(ph + ctr + rowe, a);
+                    load_vec_s(pp + ctr + rowe, b);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) yp[f][j] = fma_t(k.drift, b[j], a[j]);
+                    xlv[f] = fma_t(k.drift, pp[ctr - 1], ph[ctr - 1]);
+                    xrv[f] = fma_t(k.drift, pp[ctr + W], ph[ctr + W]);
                 }
+                T pnew[NF][W];
+                site_update<T, NF, W>(k, cu, zm, zp, ym, yp, xlv, xrv, pc, pnew, acc);
+                if (!MEASURE) {
+                    const size_t off = (size_t)z * NN + (size_t)y * N + x0;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        store_vec_cs(static_cast<T *>(fp.phi_out[f]) + off, cu[f]);
+                        store_vec_cs(static_cast<T *>(fp.pi_out[f]) + off, pnew[f]);
+                    }
+                }
+                if (((z - z0) & 15) == 15) {
+#pragma unroll
+                    for (int i = 0; i < NQ; ++i) {
+                        accd[i] += (double)acc[i];
+                        acc[i] = (T)0;
+                    }
+                }
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        zm[f][j] = cu[f][j];
+                        cu[f][j] = zp[f][j];
+                        pc[f][j] = pn[f][j];
+                    }
             }
-            if (((z - z0) & 15) == 15) {
-#pragma unroll
-                for (int i = 0; i < NQ; ++i) {
-                    accd[i] += (double)acc[i];
-                    acc[i] = (T)0;
-                }
-            }
-#pragma unroll
-            for (int f = 0; f < NF; ++f)
-#pragma unroll
-                for (int j = 0; j < W; ++j) {
-                    zm[f][j] = cu[f][j];
-                    cu[f][j] = zp[f][j];
-                    pc[f][j] = pn[f][j];
-                }
+            release(kz);
         }
-    }
 #pragma unroll
-    for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
+        for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
+    }
+    __syncthreads();
     // After a timeout, wait (bounded) for planes still in flight before the
     // CTA's shared memory goes away.
-    __syncthreads();
-    if (s_failed && tid == 0) {
-        for (int kk = 0; kk < issued; ++kk) mbar_wait_bounded(&bars[kk % S], (kk / S) & 1u, sc);
-    }
+    if (s_failed && producer && (tid & 31) == 0)
+        for (int kk = (issued > S ? issued - S : 0); kk < issued; ++kk)
+            mbar_wait_bounded(&full[kk % S], (kk / S) & 1u, sc);
     cta_reduce_finalize<NQ>(accd, m, c, sc, slots);
 }
 
@@ -644,42 +714,79 @@ __global__ void set_background_kernel(Model m, Scalars *sc, double a, double b)
     for (int i = 0; i < kMaxQ; ++i) sc->E[i] = 0.0;
 }
 
-PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, int variant)
+size_t bulk_smem_bytes(int txt, int ty, int W, int nf, int stages, int elem_bytes)
+{
+    return (size_t)stages * nf * 2 * (ty + 2) * (txt * W + 2 * W) * (size_t)elem_bytes;
+}
+
+PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTuning &t)
 {
     const int W = 16 / elem_bytes;
     PassGeom g;
-    int per_row = N / W;  // N % 4 == 0 is required, so W | N
-    // 1-D CTAs of 256 threads (whole warps, as the CTA reduction needs) laid
-    // over a tile of txt x ty threads; leftover threads idle.
+    const int per_row = N / W;  // N % 4 == 0 is required, so W | N
+    g.variant = t.variant;
+    g.cwarps = (t.variant == kVariantBulk) ? (t.cwarps == 4 ? 4 : 8) : 8;
+    // CTAs of whole warps (the CTA reduction needs them) whose compute threads
+    // are laid over a tile of txt x ty threads; leftover threads idle.
+    const int threads = 32 * g.cwarps;
     g.txt = per_row < 32 ? per_row : 32;
-    g.ty = 256 / g.txt;
+    g.ty = threads / g.txt;
     if (g.ty > N) g.ty = N;
     const int gx = (per_row + g.txt - 1) / g.txt;
     const int gy = (N + g.ty - 1) / g.ty;
     // z-chunk: long enough to amortise the two extra planes, short enough
     // for several waves of CTAs over the GPU.
-    const long target = 8L * (sm_count > 0 ? sm_count : 152);
-    int zc = N < 128 ? N : 128;
-    while (zc > 4 && (long)gx * gy * ((N + zc - 1) / zc) < target) zc /= 2;
+    int zc = t.zc > 0 ? t.zc : (N < 128 ? N : 128);
+    if (t.zc <= 0) {
+        const long target = 8L * (sm_count > 0 ? sm_count : 152);
+        while (zc > 4 && (long)gx * gy * ((N + zc - 1) / zc) < target) zc /= 2;
+    }
+    if (zc > N) zc = N;
     g.zc = zc;
     g.grid = dim3(gx, gy, (N + zc - 1) / zc);
     g.nblocks = g.grid.x * g.grid.y * g.grid.z;
-    g.variant = variant;
-    // ring depth: 4 planes (2 in flight) fit two CTAs per SM up to two fields;
-    // three fields use 3 (1 in flight) for the same occupancy.
-    g.stages = nf >= 3 ? 3 : 4;
-    g.smem = variant == kVariantBulk
-                 ? (size_t)g.stages * nf * 2 * (g.ty + 2) * (g.txt * W + 2 * W) * (size_t)elem_bytes
-                 : 0;
+    g.stages = 0;
+    g.smem = 0;
+    g.prefetch = 0;
+    if (g.variant == kVariantLdg) {
+        const int D = t.prefetch >= 0 ? t.prefetch : 3;
+        g.prefetch = (D == 0 || D == 2 || D == 4) ? D : 3;
+        g.smem = (size_t)g.prefetch * nf * 2 * 256 * 16;
+    }
+    if (g.variant == kVariantBulk) {
+        // ring depth: as deep as fits two CTAs per SM (<= 113 KB each), at
+        // least 3 (two planes read + one in flight), at most kMaxStages.
+        int S = t.stages > 0 ? t.stages : 8;
+        if (S > 8) S = 8;
+        while (S > 3 && bulk_smem_bytes(g.txt, g.ty, W, nf, S, elem_bytes) > (t.stages > 0 ? 227u : 113u) * 1024u) --S;
+        if (S < 3) S = 3;
+        g.stages = S;
+        g.smem = bulk_smem_bytes(g.txt, g.ty, W, nf, S, elem_bytes);
+    }
     return g;
 }
 
-template <typename T, int NF, bool MEASURE, int S>
+template <typename T, int NF, bool MEASURE>
 static cudaError_t launch_bulk(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
                                double *slots, cudaStream_t s)
 {
     static size_t configured = 0;  // dynamic shared memory the attribute allows so far
-    auto kern = fused_pass_bulk<T, NF, MEASURE, S>;
+    auto kern = fused_pass_bulk<T, NF, MEASURE>;
+    if (g.smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+        if (e != cudaSuccess) return e;
+        configured = g.smem;
+    }
+    kern<<<g.grid, 32 * (g.cwarps + 1), g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, g.stages, sc, slots);
+    return cudaGetLastError();
+}
+
+template <typename T, int NF, bool MEASURE, int D>
+static cudaError_t launch_ldg(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
+                              double *slots, cudaStream_t s)
+{
+    static size_t configured = 0;
+    auto kern = fused_pass_ldg<T, NF, MEASURE, D>;
     if (g.smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
         if (e != cudaSuccess) return e;
@@ -693,18 +800,19 @@ template <typename T, int NF>
 static cudaError_t launch_t(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
                             double *slots, bool measure_only, cudaStream_t s)
 {
-    if (g.variant == kVariantBulk) {
-        if (g.stages == 3)
-            return measure_only ? launch_bulk<T, NF, true, 3>(m, fp, c, g, sc, slots, s)
-                                : launch_bulk<T, NF, false, 3>(m, fp, c, g, sc, slots, s);
-        return measure_only ? launch_bulk<T, NF, true, 4>(m, fp, c, g, sc, slots, s)
-                            : launch_bulk<T, NF, false, 4>(m, fp, c, g, sc, slots, s);
+    if (g.variant == kVariantBulk)
+        return measure_only ? launch_bulk<T, NF, true>(m, fp, c, g, sc, slots, s)
+                            : launch_bulk<T, NF, false>(m, fp, c, g, sc, slots, s);
+    switch (g.prefetch) {
+    case 0: return measure_only ? launch_ldg<T, NF, true, 0>(m, fp, c, g, sc, slots, s)
+                                : launch_ldg<T, NF, false, 0>(m, fp, c, g, sc, slots, s);
+    case 2: return measure_only ? launch_ldg<T, NF, true, 2>(m, fp, c, g, sc, slots, s)
+                                : launch_ldg<T, NF, false, 2>(m, fp, c, g, sc, slots, s);
+    case 4: return measure_only ? launch_ldg<T, NF, true, 4>(m, fp, c, g, sc, slots, s)
+                                : launch_ldg<T, NF, false, 4>(m, fp, c, g, sc, slots, s);
+    default: return measure_only ? launch_ldg<T, NF, true, 3>(m, fp, c, g, sc, slots, s)
+                                 : launch_ldg<T, NF, false, 3>(m, fp, c, g, sc, slots, s);
     }
-    if (measure_only)
-        fused_pass_ldg<T, NF, true><<<g.grid, 256, 0, s>>>(m, fp, c, g.txt, g.ty, g.zc, sc, slots);
-    else
-        fused_pass_ldg<T, NF, false><<<g.grid, 256, 0, s>>>(m, fp, c, g.txt, g.ty, g.zc, sc, slots);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,
