@@ -43,12 +43,17 @@ METRIC = "site-updates/s per field"
 PASSES = {"leapfrog": 1, "verlet": 1, "yoshida4": 3}[WL.integrator]
 BYTES_PER_SITE_FIELD_PASS = 4 * (4 if WL.dtype == "f32" else 8)  # read phi, pi; write phi, pi
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_pass_1024cubed_2f_f32.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_2607_24908_gb300", "csrc", "tl_pass.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2607_24908_gb300", "csrc", n)
+               for n in ("tl_pass_impl.cuh", "tl_pass.cu", "tl_pass_f32.cu")]
 
 
 def kernel_hash() -> str:
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """sha256 of the fused-pass sources (kernel, geometry, FP32 instantiation)."""
+    h = hashlib.sha256()
+    for p in KERNEL_SRCS:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def measured_traffic():

@@ -1,0 +1,745 @@
+// Fused lattice pass: deferred drift + 7-point Laplacian + dV/dphi + kick +
+// K/G/V reductions + (last CTA) FP64 scale-factor update, in one kernel.
+//
+// The paper's step (Sec. 4) is a kick pi+ = pi + dt (Lap phi - dV/dphi) and a
+// drift phi+ = phi + dt pi+, each its own bandwidth-bound sweep.  Here the
+// drift of step n is deferred into the pass of step n+1: a pass reads the
+// stored (phi_s, pi_s), forms phi = phi_s + drift pi_s for each site and its
+// six neighbours (one fma, bitwise the same wherever it is recomputed),
+// evaluates F = a^(1+alpha) Lap phi - a^(3+alpha) dV/dphi, and writes phi and
+// pi_s + kdt F to the other ping-pong buffer.  With expansion the drift
+// coefficient depends on the scale factor after the b-kick, which needs the
+// energies of this same pass; the last CTA to finish computes it and leaves
+// it in device memory for the next pass, so the host never waits.
+//
+// Layout and traffic: each thread owns W = 16/sizeof(T) consecutive x-sites
+// (one 128-bit word per array) of one y-row and marches a chunk of z-planes,
+// keeping phi at z-1, z, z+1 in registers.  Two variants feed it: plain
+// per-thread loads through L1/L2 (fused_pass_ldg), or a ring of z-planes of the
+// CTA's tile staged in shared memory by bulk asynchronous copies
+// (fused_pass_bulk).  Either way HBM sees each array read once and written
+// once per pass: 4 sizeof(T) bytes per site per field.
+#pragma once
+#include <math.h>
+
+#include "tl_internal.cuh"
+
+namespace tl {
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+    static constexpr int W = 4;
+    typedef float4 type;
+};
+template <>
+struct Vec<double> {
+    static constexpr int W = 2;
+    typedef double2 type;
+};
+
+__device__ __forceinline__ void load_vec(const float *p, float (&o)[4])
+{
+    float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void load_vec(const double *p, double (&o)[2])
+{
+    double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+    o[0] = t.x; o[1] = t.y;
+}
+__device__ __forceinline__ void store_vec(float *p, const float (&v)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store_vec(double *p, const double (&v)[2])
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+__device__ __forceinline__ void load_vec_s(const float *p, float (&o)[4])
+{
+    float4 t = *reinterpret_cast<const float4 *>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void load_vec_s(const double *p, double (&o)[2])
+{
+    double2 t = *reinterpret_cast<const double2 *>(p);
+    o[0] = t.x; o[1] = t.y;
+}
+// streaming (evict-first) stores: the outputs are read again only by the next pass
+__device__ __forceinline__ void store_vec_cs(float *p, const float (&v)[4])
+{
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+__device__ __forceinline__ void store_vec_cs(double *p, const double (&v)[2])
+{
+    __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+}
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Scale-factor update and next-pass coefficients (one thread of the last CTA).
+// tot: raw lattice sums  [sum pi_int_f^2, sum |grad+ phi_f|^2 dx^2, sum V].
+static __device__ void finalize(const Model &m, const PassCoef &c, Scalars *sc, const double *tot)
+{
+    const int nf = m.nf;
+    const double n3 = (double)m.N * (double)m.N * (double)m.N;
+    const double a = sc->a;
+    double E[kMaxQ];
+    double K = 0.0, G = 0.0;
+    bool finite = true;
+    for (int f = 0; f < nf; ++f) {
+        E[f] = 0.5 * sc->wk * (tot[f] / n3);
+        E[nf + f] = 0.5 * sc->wg * m.inv_dx2 * (tot[nf + f] / n3);
+        K += E[f];
+        G += E[nf + f];
+    }
+    const double V = tot[2 * nf] / n3;
+    E[2 * nf] = V;
+    for (int i = 0; i < 2 * nf + 1; ++i) {
+        finite = finite && isfinite(E[i]);
+        if (c.integer_time) sc->E[i] = E[i];
+    }
+    if (!finite && sc->status == TL_OK) sc->status = TL_EUNSTABLE;
+    sc->time += sc->pending_dt;
+    if (m.expanding) {
+        const double al = m.alpha;
+        const double rho = K + G + V;
+        double b = sc->b, b_eval;
+        if (c.set_b_from_constraint) {
+            b = pow(a, 1.0 + al) * sqrt(m.mu2 * rho / 3.0);
+            b_eval = b;
+        } else {
+            const double fb = pow(a, 2.0 * al + 1.0) * (m.mu2 / 3.0) * ((al - 2.0) * K + al * G + (al + 1.0) * V);
+            b_eval = b + c.hb_dt * fb;
+            b = b + c.edt * fb;
+        }
+        if (c.integer_time) {
+            const double H2 = (b_eval / a) * (b_eval / a);
+            sc->hubble = fabs(H2 - pow(a, 2.0 * al) * m.mu2 * rho / 3.0) / H2;
+        }
+        const double an = a + c.dnext_dt * b;
+        sc->drift = c.dnext_dt * pow(0.5 * (a + an), al - 3.0);
+        sc->a = an;
+        sc->b = b;
+        sc->wl = pow(an, 1.0 + al);
+        sc->wv = pow(an, 3.0 + al);
+        sc->wk = pow(an, -6.0);
+        sc->wg = pow(an, -2.0);
+    } else {
+        sc->drift = c.dnext_dt;
+        sc->hubble = 0.0;
+    }
+    sc->pending_dt = c.dnext_dt;
+}
+
+// ---- pieces shared by both pass variants ------------------------------------
+
+// Per-pass constants in the storage precision.
+template <typename T, int NF>
+struct Coefs {
+    T drift, wlx, wv, kdt, hdt, lam, q;
+    T m2[NF];
+    __device__ Coefs(const Model &m, const PassCoef &c, const Scalars *sc)
+    {
+        drift = (T)sc->drift;
+        wlx = (T)(sc->wl * m.inv_dx2);
+        wv = (T)sc->wv;
+        kdt = (T)c.kdt;
+        hdt = (T)c.hdt;
+        lam = (T)m.lambda;
+        q = (T)m.q;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) m2[f] = (T)m.m2[f];
+    }
+};
+
+// Update W consecutive sites of one row of plane z, all fields: Laplacian from
+// the six neighbours (differences first, so FP32 keeps the small gradients
+// exact), dV/dphi, the kick, and the K/G/V sums at the evaluation time.
+// cu/zm/zp: phi at z, z-1, z+1; ym/yp: rows y-1, y+1; xl/xr: the sites left of
+// element 0 and right of element W-1; pc: stored pi at z.
+template <typename T, int NF, int W>
+__device__ __forceinline__ void site_update(const Coefs<T, NF> &k, const T (&cu)[NF][W], const T (&zm)[NF][W],
+                                            const T (&zp)[NF][W], const T (&ym)[NF][W], const T (&yp)[NF][W],
+                                            const T (&xl)[NF], const T (&xr)[NF], const T (&pc)[NF][W],
+                                            T (&pnew)[NF][W], T (&acc)[2 * NF + 1])
+{
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        T v[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) v[f] = cu[f][j];
+        T others = (T)0;
+#pragma unroll
+        for (int f = 1; f < NF; ++f) others += v[f] * v[f];
+        const T v02 = v[0] * v[0];
+        T dv[NF];
+        dv[0] = k.m2[0] * v[0] + k.lam * v02 * v[0] + k.q * v[0] * others;
+        T Vs = (T)0.5 * k.m2[0] * v02 + (T)0.25 * k.lam * v02 * v02 + (T)0.5 * k.q * v02 * others;
+#pragma unroll
+        for (int f = 1; f < NF; ++f) {
+            dv[f] = k.m2[f] * v[f] + k.q * v02 * v[f];
+            Vs += (T)0.5 * k.m2[f] * v[f] * v[f];
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const T cc = v[f];
+            const T left = (j == 0) ? xl[f] : cu[f][j - 1];
+            const T right = (j == W - 1) ? xr[f] : cu[f][j + 1];
+            const T dxm = left - cc, dxp = right - cc;
+            const T dym = ym[f][j] - cc, dyp = yp[f][j] - cc;
+            const T dzm = zm[f][j] - cc, dzp = zp[f][j] - cc;
+            const T lap = ((dxm + dxp) + (dym + dyp)) + (dzm + dzp);
+            const T F = k.wlx * lap - k.wv * dv[f];
+            const T pint = fma_t(k.hdt, F, pc[f][j]);
+            pnew[f][j] = fma_t(k.kdt, F, pc[f][j]);
+            acc[f] += pint * pint;
+            acc[NF + f] += dxp * dxp + dyp * dyp + dzp * dzp;
+        }
+        acc[2 * NF] += Vs;
+    }
+}
+
+// CTA sum in a fixed order (warp trees, then warps in index order) into this
+// CTA's slot; the last CTA to arrive sums all slots in index order and runs
+// finalize().  Deterministic for a given launch geometry.
+template <int NQ>
+__device__ __forceinline__ void cta_reduce_finalize(const double (&accd)[NQ], const Model &m, const PassCoef &c,
+                                                    Scalars *sc, double *slots)
+{
+    __shared__ double red[16][NQ];
+    __shared__ bool last;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        double v = warp_sum(accd[i]);
+        if (lane == 0) red[warp][i] = v;
+    }
+    __syncthreads();
+    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    if (tid < NQ) {
+        double s = 0.0;
+        for (int w = 0; w < nwarps; ++w) s += red[w][tid];
+        slots[(size_t)bid * NQ + tid] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = (atomicAdd(&sc->ticket, 1u) == nblocks - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double part[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) part[i] = 0.0;
+    for (unsigned b = tid; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) part[i] += __ldcg(slots + (size_t)b * NQ + i);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        double v = warp_sum(part[i]);
+        if (lane == 0) red[warp][i] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double tot[kMaxQ];
+        for (int i = 0; i < NQ; ++i) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += red[w][i];
+            tot[i] = s;
+        }
+        finalize(m, c, sc, tot);
+        sc->ticket = 0u;
+        __threadfence();
+    }
+}
+
+// ---- variant 1: register streaming with a per-thread prefetch ring -------------
+// Each thread owns its 128-bit words.  The HBM stream (the stored phi and pi
+// of its own sites, plane after plane) is prefetched D planes ahead with
+// cp.async into a private shared-memory ring (no CTA barrier: a thread only
+// waits for its own copies); the neighbour rows and edge sites of plane z are
+// other threads' words of the same plane and come from L1/L2 with ld.global.
+// D = 0 loads the next plane directly, without the ring.
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int Npending>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(Npending) : "memory"); }
+
+template <typename T, int NF, bool MEASURE, int D, int MINB>
+__global__ void __launch_bounds__(256, MINB) fused_pass_ldg(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
+                                                      Scalars *sc, double *slots)
+{
+    constexpr int W = Vec<T>::W;
+    constexpr int NQ = 2 * NF + 1;
+    extern __shared__ __align__(16) unsigned char ring_raw[];
+    const int N = m.N;
+    const int tid = threadIdx.x;
+    const int tx = tid % txt, tyi = tid / txt;
+    const int x0 = (blockIdx.x * txt + tx) * W;
+    const int y = blockIdx.y * ty + tyi;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(z0 + zc, N);
+    const bool active = (tyi < ty) && (x0 < N) && (y < N);
+    // ring slot (plane d, field f, array a) of this thread
+    auto slot = [&](int d, int f, int a) -> T * {
+        return reinterpret_cast<T *>(ring_raw) + ((size_t)((d * NF + f) * 2 + a) * blockDim.x + tid) * W;
+    };
+
+    double accd[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) accd[i] = 0.0;
+
+    if (active) {
+        const Coefs<T, NF> k(m, c, sc);
+        const T *phs[NF], *pis[NF];
+        T *pho[NF], *pio[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            phs[f] = static_cast<const T *>(fp.phi_in[f]);
+            pis[f] = static_cast<const T *>(fp.pi_in[f]);
+            pho[f] = static_cast<T *>(fp.phi_out[f]);
+            pio[f] = static_cast<T *>(fp.pi_out[f]);
+        }
+        const size_t NN = (size_t)N * (size_t)N;
+        const int xl = (x0 == 0) ? N - 1 : x0 - 1;
+        const int xr = (x0 + W == N) ? 0 : x0 + W;
+        const size_t row = (size_t)y * N;
+        const size_t rowm = (size_t)((y == 0) ? N - 1 : y - 1) * N;
+        const size_t rowp = (size_t)((y + 1 == N) ? 0 : y + 1) * N;
+        auto cur_vec = [&](int f, size_t off, T (&o)[W]) {
+            T a[W], b[W];
+            load_vec(phs[f] + off, a);
+            load_vec(pis[f] + off, b);
+#pragma unroll
+            for (int j = 0; j < W; ++j) o[j] = fma_t(k.drift, b[j], a[j]);
+        };
+        auto cur_one = [&](int f, size_t off) -> T {
+            return fma_t(k.drift, __ldg(pis[f] + off), __ldg(phs[f] + off));
+        };
+        auto plane_off = [&](int zz) -> size_t { return (size_t)(zz >= N ? zz - N : zz) * NN + row + x0; };
+        // prefetch this thread's words of plane zz (<= z1) into ring slot d
+        auto prefetch = [&](int zz, int d) {
+            if (zz <= z1) {
+                const size_t off = plane_off(zz);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    cp_async16(slot(d, f, 0), phs[f] + off);
+                    cp_async16(slot(d, f, 1), pis[f] + off);
+                }
+            }
+            cp_async_commit();
+        };
+
+        T zm[NF][W], cu[NF][W], zp[NF][W], pc[NF][W];
+        {
+            const size_t pm = (size_t)((z0 == 0) ? N - 1 : z0 - 1) * NN;
+            const size_t p0 = (size_t)z0 * NN;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                cur_vec(f, pm + row + x0, zm[f]);
+                T a[W];
+                load_vec(phs[f] + p0 + row + x0, a);
+                load_vec(pis[f] + p0 + row + x0, pc[f]);
+#pragma unroll
+                for (int j = 0; j < W; ++j) cu[f][j] = fma_t(k.drift, pc[f][j], a[j]);
+            }
+        }
+        if (D > 0) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) prefetch(z0 + 1 + d, d);
+        }
+        T acc[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) acc[i] = (T)0;
+
+        int d = 0;  // ring slot holding plane z+1
+        for (int z = z0; z < z1; ++z) {
+            const size_t pz = (size_t)z * NN;
+            T pnext[NF][W];
+            if (D > 0) {
+                cp_async_wait<(D > 0 ? D - 1 : 0)>();
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    T a[W];
+                    load_vec_s(slot(d, f, 0), a);
+                    load_vec_s(slot(d, f, 1), pnext[f]);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) zp[f][j] = fma_t(k.drift, pnext[f][j], a[j]);
+                }
+                prefetch(z + 1 + D, d);
+                d = (d + 1 == D) ? 0 : d + 1;
+            } else {
+                const size_t pn = plane_off(z + 1);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    T a[W];
+                    load_vec(phs[f] + pn, a);
+                    load_vec(pis[f] + pn, pnext[f]);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) zp[f][j] = fma_t(k.drift, pnext[f][j], a[j]);
+                }
+            }
+            T ym[NF][W], yp[NF][W], xlv[NF], xrv[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                cur_vec(f, pz + rowm + x0, ym[f]);
+                cur_vec(f, pz + rowp + x0, yp[f]);
+                xlv[f] = cur_one(f, pz + row + xl);
+                xrv[f] = cur_one(f, pz + row + xr);
+            }
+            T pnew[NF][W];
+            site_update<T, NF, W>(k, cu, zm, zp, ym, yp, xlv, xrv, pc, pnew, acc);
+            if (!MEASURE) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    store_vec_cs(pho[f] + pz + row + x0, cu[f]);
+                    store_vec_cs(pio[f] + pz + row + x0, pnew[f]);
+                }
+            }
+            if (((z - z0) & 15) == 15) {
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) {
+                    accd[i] += (double)acc[i];
+                    acc[i] = (T)0;
+                }
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+#pragma unroll
+                for (int j = 0; j < W; ++j) {
+                    zm[f][j] = cu[f][j];
+                    cu[f][j] = zp[f][j];
+                    pc[f][j] = pnext[f][j];
+                }
+        }
+        if (D > 0) cp_async_wait<0>();
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
+    }
+    cta_reduce_finalize<NQ>(accd, m, c, sc, slots);
+}
+
+// ---- variant 2: bulk-copy staging ------------------------------------------------
+// The CTA keeps a ring of S z-planes of its tile plus a one-site halo (raw
+// phi_s and pi_s of every field) in shared memory.  Warp 0 fills the ring with
+// cp.async.bulk row copies (the Tensor Memory Accelerator's bulk path; rows
+// that cross the periodic boundary are split in two), each plane signalling
+// one mbarrier; S-2 planes are in flight while the CTA computes plane z from
+// planes z (halo) and z+1 (centre).  Registers hold only phi at z-1, z, z+1
+// and pi at z, z+1 for the thread's own sites.
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for a plane with a time limit (about one second); on expiry record
+// TL_ETIMEOUT in the lattice status and return false.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, Scalars *sc)
+{
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 256; ++i)
+            if (mbar_test(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            atomicCAS(&sc->status, TL_OK, TL_ETIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Copy elements [xs, xs+len) of a periodic row (indices mod N) to dst, in at
+// most ceil(len/N)+1 contiguous bulk copies.  xs, len and N are multiples of
+// W, so every copy is 16-byte aligned and a multiple of 16 bytes.
+template <typename T>
+__device__ __forceinline__ void copy_row(T *dst, const T *row, int xs, int len, int N, uint64_t *bar)
+{
+    int xg = xs % N;
+    if (xg < 0) xg += N;
+    int off = 0;
+    while (off < len) {
+        const int n = min(len - off, N - xg);
+        bulk_load(dst + off, row + xg, (uint32_t)(n * sizeof(T)), bar);
+        off += n;
+        xg = 0;
+    }
+}
+
+// Warp-specialised: warps 0..CW-1 compute, warp CW produces.  The producer
+// runs up to S planes ahead: before refilling a stage it waits on that
+// stage's "empty" mbarrier, which each consumer warp arrives on once it is done
+// with the plane; consumers wait on the stage's "full" mbarrier (completed by
+// the bulk copies' byte count).  No CTA-wide barrier inside the z loop.
+constexpr int kMaxStages = 8;
+
+template <typename T, int NF, bool MEASURE>
+__global__ void __launch_bounds__(288, 2) fused_pass_bulk(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
+                                                          int S, Scalars *sc, double *slots)
+{
+    constexpr int W = Vec<T>::W;
+    constexpr int NQ = 2 * NF + 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+    __shared__ volatile int s_failed;
+    T *stage_base = reinterpret_cast<T *>(smem_raw);
+
+    const int N = m.N;
+    const int tid = threadIdx.x;
+    const int CW = (blockDim.x >> 5) - 1;  // consumer warps
+    const bool producer = (tid >> 5) == CW;
+    const int x_tile = blockIdx.x * txt * W, y_tile = blockIdx.y * ty;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(z0 + zc, N);
+    const int K = (z1 - z0) + 2;  // planes z0-1 .. z1
+    const int rowe = txt * W + 2 * W;
+    const int plane = (ty + 2) * rowe;
+    const uint32_t plane_bytes = (uint32_t)(NF * 2 * plane * sizeof(T));
+    const size_t NN = (size_t)N * (size_t)N;
+    auto arr = [&](int s, int f, int a) -> T * { return stage_base + (size_t)((s * NF + f) * 2 + a) * plane; };
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CW);
+        }
+        s_failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    double accd[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) accd[i] = 0.0;
+    int issued = 0;
+
+    if (producer) {
+        const int lane = tid & 31;
+        for (int k = 0; k < K; ++k) {
+            const int s = k % S;
+            if (k >= S && !mbar_wait_bounded(&empty[s], ((k / S) - 1) & 1u, sc)) {
+                s_failed = 1;
+                break;
+            }
+            if (s_failed) break;
+            const int zg = (z0 - 1 + k + N) % N;
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], plane_bytes);
+            __syncwarp();
+            for (int item = lane; item < NF * 2 * (ty + 2); item += 32) {
+                const int f = item / (2 * (ty + 2));
+                const int rem = item - f * 2 * (ty + 2);
+                const int a = rem / (ty + 2);
+                const int r = rem - a * (ty + 2);
+                const int yg = (y_tile - 1 + r + N) % N;
+                const T *src = static_cast<const T *>(a == 0 ? fp.phi_in[f] : fp.pi_in[f]) +
+                               ((size_t)zg * NN + (size_t)yg * N);
+                copy_row<T>(arr(s, f, a) + r * rowe, src, x_tile - W, rowe, N, &full[s]);
+            }
+            issued = k + 1;
+        }
+    } else {
+        const int lane = tid & 31;
+        const int tx = tid % txt, tyi = tid / txt;
+        const int x0 = x_tile + tx * W;
+        const int y = y_tile + tyi;
+        const bool active = (tyi < ty) && (x0 < N) && (y < N);
+        const Coefs<T, NF> k(m, c, sc);
+        const int ctr = (tyi + 1) * rowe + (tx + 1) * W;
+        T zm[NF][W], cu[NF][W], zp[NF][W], pc[NF][W], pn[NF][W];
+        T acc[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) acc[i] = (T)0;
+        auto centre = [&](int kk, T (&ph)[NF][W], T (&pp)[NF][W]) {
+            const int s = kk % S;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                T a[W];
+                load_vec_s(arr(s, f, 0) + ctr, a);
+                load_vec_s(arr(s, f, 1) + ctr, pp[f]);
+#pragma unroll
+                for (int j = 0; j < W; ++j) ph[f][j] = fma_t(k.drift, pp[f][j], a[j]);
+            }
+        };
+        auto release = [&](int kk) {
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[kk % S]))
+                                        : "memory");
+        };
+        bool ok = true;
+        if (active) {
+            ok = mbar_wait_bounded(&full[0], 0u, sc);
+            centre(0, zm, pn);
+            ok = ok && mbar_wait_bounded(&full[1 % S], (1 / S) & 1u, sc);
+            centre(1, cu, pc);
+        }
+        if (!ok) s_failed = 1;
+        release(0);
+        for (int z = z0; z < z1 && !s_failed; ++z) {
+            const int kz = z - z0 + 1;
+            if (active) {
+                if (!mbar_wait_bounded(&full[(kz + 1) % S], ((kz + 1) / S) & 1u, sc)) s_failed = 1;
+                centre(kz + 1, zp, pn);
+                const int s0 = kz % S;
+                T ym[NF][W], yp[NF][W], xlv[NF], xrv[NF];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const T *ph = arr(s0, f, 0), *pp = arr(s0, f, 1);
+                    T a[W], b[W];
+                    load_vec_s(ph + ctr - rowe, a);
+                    load_vec_s(pp + ctr - rowe, b);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) ym[f][j] = fma_t(k.drift, b[j], a[j]);
+                    load_vec_s(ph + ctr + rowe, a);
+                    load_vec_s(pp + ctr + rowe, b);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) yp[f][j] = fma_t(k.drift, b[j], a[j]);
+                    xlv[f] = fma_t(k.drift, pp[ctr - 1], ph[ctr - 1]);
+                    xrv[f] = fma_t(k.drift, pp[ctr + W], ph[ctr + W]);
+                }
+                T pnew[NF][W];
+                site_update<T, NF, W>(k, cu, zm, zp, ym, yp, xlv, xrv, pc, pnew, acc);
+                if (!MEASURE) {
+                    const size_t off = (size_t)z * NN + (size_t)y * N + x0;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        store_vec_cs(static_cast<T *>(fp.phi_out[f]) + off, cu[f]);
+                        store_vec_cs(static_cast<T *>(fp.pi_out[f]) + off, pnew[f]);
+                    }
+                }
+                if (((z - z0) & 15) == 15) {
+#pragma unroll
+                    for (int i = 0; i < NQ; ++i) {
+                        accd[i] += (double)acc[i];
+                        acc[i] = (T)0;
+                    }
+                }
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        zm[f][j] = cu[f][j];
+                        cu[f][j] = zp[f][j];
+                        pc[f][j] = pn[f][j];
+                    }
+            }
+            release(kz);
+        }
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
+    }
+    __syncthreads();
+    // After a timeout, wait (bounded) for planes still in flight before the
+    // CTA's shared memory goes away.
+    if (s_failed && producer && (tid & 31) == 0)
+        for (int kk = (issued > S ? issued - S : 0); kk < issued; ++kk)
+            mbar_wait_bounded(&full[kk % S], (kk / S) & 1u, sc);
+    cta_reduce_finalize<NQ>(accd, m, c, sc, slots);
+}
+
+template <typename T, int NF, bool MEASURE>
+static cudaError_t launch_bulk(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
+                               double *slots, cudaStream_t s)
+{
+    static size_t configured = 0;  // dynamic shared memory the attribute allows so far
+    auto kern = fused_pass_bulk<T, NF, MEASURE>;
+    if (g.smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+        if (e != cudaSuccess) return e;
+        configured = g.smem;
+    }
+    kern<<<g.grid, 32 * (g.cwarps + 1), g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, g.stages, sc, slots);
+    return cudaGetLastError();
+}
+
+template <typename T, int NF, bool MEASURE, int D, int MINB>
+static cudaError_t launch_ldg(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
+                              double *slots, cudaStream_t s)
+{
+    static size_t configured = 0;
+    auto kern = fused_pass_ldg<T, NF, MEASURE, D, MINB>;
+    if (g.smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+        if (e != cudaSuccess) return e;
+        configured = g.smem;
+    }
+    kern<<<g.grid, 256, g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, sc, slots);
+    return cudaGetLastError();
+}
+
+template <typename T, int NF>
+static cudaError_t launch_t(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
+                            double *slots, bool measure_only, cudaStream_t s)
+{
+    if (g.variant == kVariantBulk)
+        return measure_only ? launch_bulk<T, NF, true>(m, fp, c, g, sc, slots, s)
+                            : launch_bulk<T, NF, false>(m, fp, c, g, sc, slots, s);
+    const bool three = g.minblocks == 3;
+    if (g.prefetch == 0) {
+        if (three)
+            return measure_only ? launch_ldg<T, NF, true, 0, 3>(m, fp, c, g, sc, slots, s)
+                                : launch_ldg<T, NF, false, 0, 3>(m, fp, c, g, sc, slots, s);
+        return measure_only ? launch_ldg<T, NF, true, 0, 2>(m, fp, c, g, sc, slots, s)
+                            : launch_ldg<T, NF, false, 0, 2>(m, fp, c, g, sc, slots, s);
+    }
+    if (three)
+        return measure_only ? launch_ldg<T, NF, true, 3, 3>(m, fp, c, g, sc, slots, s)
+                            : launch_ldg<T, NF, false, 3, 3>(m, fp, c, g, sc, slots, s);
+    return measure_only ? launch_ldg<T, NF, true, 3, 2>(m, fp, c, g, sc, slots, s)
+                        : launch_ldg<T, NF, false, 3, 2>(m, fp, c, g, sc, slots, s);
+}
+
+}  // namespace tl
