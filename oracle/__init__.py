@@ -17,7 +17,7 @@ Contents
 Paper passages followed: the phi^4 kick/drift leapfrog and 7-point stencil
 (Sec. 4, Benchmarks); Gaussian random fields from counter-based Philox
 (Sec. 2, Interface); Fourier-space views for state preparation and
-measurement (Sec. 2 and Sec. 3, Fourier Transformations).  The expanding
+measurement (Sec. 2 and Sec. 3.5, Fourier Transformations).  The expanding
 background, alpha time variable, Yoshida-4 and spectrum conventions are not
 printed in the paper; the readings used are stated in the C file's header and
 in the functions below.
