@@ -197,6 +197,39 @@ int tl_energies_noalloc(int N, double kIR, int n_fields, tl_dtype dtype, const t
                         const tl_expansion *expansion, double a, const void *const *phi, const void *const *pi,
                         void *cuda_stream, double *out);
 
+/* ---- batched ensembles and launch tuning (beyond the paper's single
+ * lattice: many independent small lattices advanced together) ---- */
+
+typedef struct tl_batch tl_batch; /* opaque */
+
+/* Group n existing lattices (same dtype; any N, n_fields, potential,
+ * background) into a batch that tl_batch_step advances together.  The
+ * lattices stay owned by the caller and cannot be destroyed or autotuned
+ * while the batch exists; their own calls (tl_energies, tl_get_state,
+ * tl_spectrum ...) keep working between batch steps.  cuda_stream: the
+ * stream the batch runs on.  Errors: TL_EINVAL, TL_ENOMEM, TL_ECUDA. */
+int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_stream);
+
+/* Advance every lattice of the batch by n steps of size dt, as tl_step
+ * would, with one persistent launch per pass and per field count (each
+ * launch walks all lattices' CTA tiles), the whole pass sequence captured
+ * once as a CUDA graph per (n, dt, integrator) and replayed.  Each lattice
+ * keeps its own launch geometry and reduction order, so its results are
+ * bitwise those of tl_step on it alone.  Enqueues only. */
+int tl_batch_step(tl_batch *batch, int n, double dt, tl_integrator integrator);
+
+void tl_batch_destroy(tl_batch *batch);
+
+/* Time candidate launch geometries of the fused pass on this lattice (the
+ * z-planes per CTA of the register-streaming kernel, from 4 to the whole
+ * lattice) with passes whose kick and drift coefficients are zero, which
+ * rewrite the state unchanged, and keep the fastest.  Results are cached per
+ * (N, n_fields, dtype, SM count) for the process and, if the environment
+ * variable TL_TUNE_FILE names a file, appended there and reused by later
+ * processes.  best_ms_per_pass (may be NULL) receives the winner's time.
+ * Synchronises the lattice stream.  Errors: TL_ESTATE (in a batch), TL_ECUDA. */
+int tl_autotune(tl_lattice *lat, double *best_ms_per_pass);
+
 /* Message for the last error on this thread ("" if none). */
 const char *tl_last_error(void);
 

@@ -7,11 +7,14 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
 #include "tl_fourier.cuh"
 #include "tl_internal.cuh"
+#include "tl_lattice.cuh"
 
 using tl::FieldPtrs;
 using tl::Model;
@@ -61,37 +64,60 @@ tl::PassTuning tl::default_tuning()
     return t;
 }
 
+// Pass list of n steps from a synchronised state (phi_n, pi_n, a_n, b_n):
+// substep sizes s_1..s_M (M = n P) in units of dt; pass 0 half-kicks with
+// s_1, pass j (0 < j < M) closes substep j and opens j+1 (merged kicks
+// (s_j + s_{j+1})/2), pass M closes substep M with a half kick.  Each pass
+// evaluates at the boundary after its deferred drift; hdt/hb_dt bring pi and
+// b to that boundary for the energies and the Hubble residual.
+bool tl::pass_schedule(int n, double dt, int integrator, std::vector<PassCoef> &out)
+{
+    double w[3];
+    int P;
+    if (integrator == TL_LEAPFROG || integrator == TL_VERLET) {
+        w[0] = 1.0;
+        P = 1;
+    } else if (integrator == TL_YOSHIDA4) {
+        const double cr = cbrt(2.0);
+        w[0] = w[2] = 1.0 / (2.0 - cr);
+        w[1] = -cr / (2.0 - cr);
+        P = 3;
+    } else {
+        return false;
+    }
+    const long M = (long)n * P;
+    out.clear();
+    out.reserve(M + 1);
+    for (long j = 0; j <= M; ++j) {
+        const double s_prev = j > 0 ? w[(j - 1) % P] : 0.0;
+        const double s_next = j < M ? w[j % P] : 0.0;
+        PassCoef c{};
+        c.kdt = 0.5 * (s_prev + s_next) * dt;
+        c.hdt = 0.5 * s_prev * dt;
+        c.edt = 0.5 * (s_prev + s_next) * dt;
+        c.hb_dt = 0.5 * s_prev * dt;
+        c.dnext_dt = s_next * dt;
+        c.integer_time = (j % P == 0) ? 1 : 0;
+        out.push_back(c);
+    }
+    return true;
+}
+
+int tl::fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
 int tl::set_error(int code, const char *msg, const char *detail)
 {
     snprintf(g_err, sizeof g_err, "%s%s", msg, detail);
     return code;
 }
 
-struct tl_lattice {
-    int N = 0, nf = 0;
-    double kIR = 0.0, dx = 0.0;
-    tl_dtype dtype = TL_F32;
-    size_t esz = 0;
-    tl_expansion ex{};
-    tl_potential pot{};
-    bool has_pot = false;
-    unsigned state_mask = 0;  // bit 2 f + which: that array was set
-    bool has_state = false;
-    cudaStream_t stream = nullptr;
-    bool own = false;
-    void *base = nullptr;           // owned field memory
-    void *buf[2][2][TL_MAX_FIELDS]; // [parity][phi, pi][field]
-    int cur = 0;
-    Scalars *d_sc = nullptr;
-    double *d_slots = nullptr;
-    PassGeom geom{};
-    Model model{};
-    int sm_count = 0;
-    int64_t step = 0;
-    bool energies_valid = false;
-    cufftHandle plan_c2r = 0, plan_r2c = 0;
-    bool have_c2r = false, have_r2c = false;
-};
 
 namespace {
 
@@ -153,10 +179,12 @@ int finish_create(tl_lattice *L, int N, double kIR, int nf, tl_dtype dtype, cons
     int dev = 0;
     TL_CK(cudaGetDevice(&dev));
     TL_CK(cudaDeviceGetAttribute(&L->sm_count, cudaDevAttrMultiProcessorCount, dev));
-    L->geom = tl::pass_geometry(N, (int)L->esz, L->sm_count, nf, tl::default_tuning());
+    L->tuning = tl::default_tuning();
+    L->geom = tl::pass_geometry(N, (int)L->esz, L->sm_count, nf, L->tuning);
     TL_CK(cudaMalloc(&L->d_sc, sizeof(Scalars)));
     TL_CK(cudaMemset(L->d_sc, 0, sizeof(Scalars)));
     TL_CK(cudaMalloc(&L->d_slots, sizeof(double) * tl::kMaxQ * L->geom.nblocks));
+    L->slots_cap = L->geom.nblocks;
     refresh_model(L);
     TL_CK(tl::launch_set_background(L->model, L->d_sc, L->ex.a0, 0.0, L->stream));
     return TL_OK;
@@ -202,7 +230,31 @@ int check_field(const tl_lattice *L, int field, int which)
     return TL_OK;
 }
 
+// cuFFT plans shared by all lattices of a size (planning costs milliseconds
+// and a workspace per plan); a plan is bound to the caller's stream for each
+// execution under this mutex.
+std::mutex g_plan_mu;
+std::map<std::pair<int, int>, cufftHandle> g_plans;  // (N, cufftType) -> plan
+
+int shared_plan(int N, cufftType type, cufftHandle *out)
+{
+    auto key = std::make_pair(N, (int)type);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+        *out = it->second;
+        return TL_OK;
+    }
+    cufftHandle h;
+    cufftResult r = cufftPlan3d(&h, N, N, N, type);
+    if (r != CUFFT_SUCCESS) return fail(TL_ECUDA, "cufftPlan3d(%d) failed (%d)", N, (int)r);
+    g_plans[key] = h;
+    *out = h;
+    return TL_OK;
+}
+
 }  // namespace
+
+int tl::lattice_launch(tl_lattice *L, const PassCoef &c, bool measure_only) { return launch(L, c, measure_only); }
 
 extern "C" {
 
@@ -292,10 +344,8 @@ int tl_lattice_create_with_buffers(tl_lattice **out, int N, double kIR, int n_fi
 
 void tl_lattice_destroy(tl_lattice *L)
 {
-    if (!L) return;
+    if (!L || L->batch_refs > 0) return;  // still held by a tl_batch: destroy the batch first
     if (L->stream || true) cudaStreamSynchronize(L->stream);
-    if (L->have_c2r) cufftDestroy(L->plan_c2r);
-    if (L->have_r2c) cufftDestroy(L->plan_r2c);
     if (L->own && L->base) cudaFree(L->base);
     if (L->d_sc) cudaFree(L->d_sc);
     if (L->d_slots) cudaFree(L->d_slots);
@@ -320,25 +370,10 @@ int tl_set_potential(tl_lattice *L, const tl_potential *pot)
 
 namespace {
 
-// Pass list of n steps from a synchronised state (phi_n, pi_n, a_n, b_n):
-// substep sizes s_1..s_M (M = n P) in units of dt; pass 0 half-kicks with
-// s_1, pass j (0 < j < M) closes substep j and opens j+1 (merged kicks
-// (s_j + s_{j+1})/2), pass M closes substep M with a half kick.  Each pass
-// evaluates at the boundary after its deferred drift; hdt/hb bring pi and b
-// to that boundary for the energies and the Hubble residual.
-int run_steps(tl_lattice *L, int n, double dt, const double *w, int P)
+// Launch a pass list on the lattice's stream.
+int run_passes(tl_lattice *L, const std::vector<PassCoef> &passes)
 {
-    const long M = (long)n * P;
-    for (long j = 0; j <= M; ++j) {
-        const double s_prev = j > 0 ? w[(j - 1) % P] : 0.0;
-        const double s_next = j < M ? w[j % P] : 0.0;
-        PassCoef c{};
-        c.kdt = 0.5 * (s_prev + s_next) * dt;
-        c.hdt = 0.5 * s_prev * dt;
-        c.edt = 0.5 * (s_prev + s_next) * dt;
-        c.hb_dt = 0.5 * s_prev * dt;
-        c.dnext_dt = s_next * dt;
-        c.integer_time = (j % P == 0) ? 1 : 0;
+    for (const PassCoef &c : passes) {
         int rc = launch(L, c, false);
         if (rc) return rc;
     }
@@ -358,17 +393,9 @@ int tl_step(tl_lattice *L, int n, double dt, tl_integrator integrator)
     if (!L->has_pot) return fail(TL_ESTATE, "tl_set_potential has not been called");
     if (!L->has_state) return fail(TL_ESTATE, "no state: call tl_init_fluctuations or tl_set_state for every array");
     if (n == 0) return TL_OK;
-    static const double w_vv[1] = {1.0};
-    const double cr = cbrt(2.0);
-    const double w1 = 1.0 / (2.0 - cr), w0 = -cr / (2.0 - cr);
-    const double w_y4[3] = {w1, w0, w1};
-    int rc;
-    switch (integrator) {
-    case TL_LEAPFROG:
-    case TL_VERLET: rc = run_steps(L, n, dt, w_vv, 1); break;
-    case TL_YOSHIDA4: rc = run_steps(L, n, dt, w_y4, 3); break;
-    default: return fail(TL_EINVAL, "unknown integrator %d", (int)integrator);
-    }
+    std::vector<PassCoef> passes;
+    if (!tl::pass_schedule(n, dt, (int)integrator, passes)) return fail(TL_EINVAL, "unknown integrator %d", (int)integrator);
+    int rc = run_passes(L, passes);
     if (rc) return rc;
     L->step += n;
     L->energies_valid = true;
@@ -473,11 +500,13 @@ int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
     const int N = L->N;
     const size_t n3 = n3_of(N);
     const size_t nh = (size_t)N * N * (N / 2 + 1);
-    if (!L->have_c2r) {
-        TL_CKFFT(cufftPlan3d(&L->plan_c2r, N, N, N, CUFFT_Z2D));
-        L->have_c2r = true;
+    std::lock_guard<std::mutex> plan_lock(g_plan_mu);
+    cufftHandle plan;
+    {
+        int prc = shared_plan(N, CUFFT_Z2D, &plan);
+        if (prc) return prc;
     }
-    TL_CKFFT(cufftSetStream(L->plan_c2r, L->stream));
+    TL_CKFFT(cufftSetStream(plan, L->stream));
     double2 *modes = nullptr;
     double *real = nullptr;
     TL_CK(cudaMallocAsync((void **)&modes, nh * sizeof(double2), L->stream));
@@ -499,7 +528,7 @@ int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
                                                        seed, which == 0 ? (uint64_t)f : (uint64_t)(8 + f),
                                                        L->sm_count, L->stream);
                 if (ce != cudaSuccess) { rc = fail(TL_ECUDA, "fill_modes: %s", cudaGetErrorString(ce)); break; }
-                cufftResult fr = cufftExecZ2D(L->plan_c2r, reinterpret_cast<cufftDoubleComplex *>(modes), real);
+                cufftResult fr = cufftExecZ2D(plan, reinterpret_cast<cufftDoubleComplex *>(modes), real);
                 if (fr != CUFFT_SUCCESS) { rc = fail(TL_ECUDA, "cufftExecZ2D failed (%d)", (int)fr); break; }
                 ce = tl::launch_assemble((int)L->dtype, dst, real, n3, base, which == 0 ? 1.0 : pscale,
                                          L->sm_count, L->stream);
@@ -533,11 +562,13 @@ int tl_spectrum(tl_lattice *L, int field, int which, int nbins, double *k, doubl
     if (nbins < nb) return fail(TL_EINVAL, "nbins must be >= %d", nb);
     const size_t n3 = n3_of(N);
     const size_t nh = (size_t)N * N * (N / 2 + 1);
-    if (!L->have_r2c) {
-        TL_CKFFT(cufftPlan3d(&L->plan_r2c, N, N, N, CUFFT_D2Z));
-        L->have_r2c = true;
+    std::lock_guard<std::mutex> plan_lock(g_plan_mu);
+    cufftHandle plan;
+    {
+        int prc = shared_plan(N, CUFFT_D2Z, &plan);
+        if (prc) return prc;
     }
-    TL_CKFFT(cufftSetStream(L->plan_r2c, L->stream));
+    TL_CKFFT(cufftSetStream(plan, L->stream));
     double2 *modes = nullptr;
     double *real = nullptr, *acc = nullptr;
     TL_CK(cudaMallocAsync((void **)&modes, nh * sizeof(double2), L->stream));
@@ -545,7 +576,7 @@ int tl_spectrum(tl_lattice *L, int field, int which, int nbins, double *k, doubl
     TL_CK(cudaMallocAsync((void **)&acc, (size_t)nb * 3 * sizeof(double), L->stream));
     TL_CK(cudaMemsetAsync(acc, 0, (size_t)nb * 3 * sizeof(double), L->stream));
     TL_CK(tl::launch_widen((int)L->dtype, real, L->buf[L->cur][which][field], n3, L->sm_count, L->stream));
-    cufftResult fr = cufftExecD2Z(L->plan_r2c, real, reinterpret_cast<cufftDoubleComplex *>(modes));
+    cufftResult fr = cufftExecD2Z(plan, real, reinterpret_cast<cufftDoubleComplex *>(modes));
     if (fr != CUFFT_SUCCESS) return fail(TL_ECUDA, "cufftExecD2Z failed (%d)", (int)fr);
     TL_CK(tl::launch_bin(modes, N, nb, acc, acc + nb, reinterpret_cast<unsigned long long *>(acc + 2 * nb),
                          L->sm_count, L->stream));

@@ -94,6 +94,22 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
 // TL_BULK_WARPS, TL_BULK_STAGES, TL_PASS_ZC), else the built-in defaults.
 PassTuning default_tuning();
 
+// One lattice of a batched (grouped) launch: its model, fields for this pass,
+// scalars, reduction slots and its own launch geometry.
+struct BatchJob {
+    Model m;
+    FieldPtrs fp;
+    Scalars *sc;
+    double *slots;
+    int txt, ty, zc, gx, gy;
+    unsigned nblocks;
+};
+
+// Enqueue one grouped pass over every job (all with n_fields == nf) as a
+// persistent launch of `grid` CTAs walking the (job, tile) items.
+cudaError_t launch_group(int dtype, int nf, const BatchJob *jobs, const unsigned *first_item, int njobs,
+                         unsigned total, const PassCoef &c, int grid, cudaStream_t s);
+
 // Enqueue one fused pass (measure_only: energies of the stored state, no writes).
 cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,
                         Scalars *sc, double *slots, bool measure_only, cudaStream_t s);

@@ -1,0 +1,45 @@
+// The lattice object behind the opaque tl_lattice handle (host side).
+#pragma once
+
+#include <cufft.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "tl_internal.cuh"
+
+struct tl_lattice {
+    int N = 0, nf = 0;
+    double kIR = 0.0, dx = 0.0;
+    tl_dtype dtype = TL_F32;
+    size_t esz = 0;
+    tl_expansion ex{};
+    tl_potential pot{};
+    bool has_pot = false;
+    unsigned state_mask = 0;  // bit 2 f + which: that array was set
+    bool has_state = false;
+    cudaStream_t stream = nullptr;
+    bool own = false;
+    void *base = nullptr;           // owned field memory
+    void *buf[2][2][TL_MAX_FIELDS]; // [parity][phi, pi][field]
+    int cur = 0;
+    tl::Scalars *d_sc = nullptr;
+    double *d_slots = nullptr;
+    unsigned slots_cap = 0;       // CTA slots d_slots holds
+    tl::PassTuning tuning{};      // launch parameters in use
+    tl::PassGeom geom{};
+    tl::Model model{};
+    int sm_count = 0;
+    int64_t step = 0;
+    bool energies_valid = false;
+    int batch_refs = 0;  // tl_batch objects that hold this lattice
+};
+
+namespace tl {
+// Launch one fused pass of a lattice on its stream and flip its buffers.
+int lattice_launch(tl_lattice *L, const PassCoef &c, bool measure_only);
+// Record an error message for tl_last_error(); returns code.
+int fail(int code, const char *fmt, ...);
+// Coefficients of the n P + 1 passes of n steps (false: unknown integrator).
+bool pass_schedule(int n, double dt, int integrator, std::vector<PassCoef> &out);
+}  // namespace tl

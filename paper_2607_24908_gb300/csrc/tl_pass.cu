@@ -98,6 +98,18 @@ cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const Pa
                            : launch_pass_f64(m, fp, c, g, sc, slots, measure_only, s);
 }
 
+cudaError_t launch_group_f32(int nf, const BatchJob *jobs, const unsigned *first_item, int njobs, unsigned total,
+                             const PassCoef &c, int grid, cudaStream_t s);
+cudaError_t launch_group_f64(int nf, const BatchJob *jobs, const unsigned *first_item, int njobs, unsigned total,
+                             const PassCoef &c, int grid, cudaStream_t s);
+
+cudaError_t launch_group(int dtype, int nf, const BatchJob *jobs, const unsigned *first_item, int njobs,
+                         unsigned total, const PassCoef &c, int grid, cudaStream_t s)
+{
+    return dtype == TL_F32 ? launch_group_f32(nf, jobs, first_item, njobs, total, c, grid, s)
+                           : launch_group_f64(nf, jobs, first_item, njobs, total, c, grid, s);
+}
+
 cudaError_t launch_set_background(const Model &m, Scalars *sc, double a, double b, cudaStream_t s)
 {
     set_background_kernel<<<1, 32, 0, s>>>(m, sc, a, b);

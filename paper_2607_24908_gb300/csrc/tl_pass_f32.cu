@@ -15,4 +15,16 @@ cudaError_t launch_pass_f32(const Model &m, const FieldPtrs &fp, const PassCoef 
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_group_f32(int nf, const BatchJob *jobs, const unsigned *first_item, int njobs, unsigned total,
+                              const PassCoef &c, int grid, cudaStream_t s)
+{
+    switch (nf) {
+    case 1: fused_pass_group<float, 1><<<grid, 256, 0, s>>>(jobs, first_item, njobs, total, c); break;
+    case 2: fused_pass_group<float, 2><<<grid, 256, 0, s>>>(jobs, first_item, njobs, total, c); break;
+    case 3: fused_pass_group<float, 3><<<grid, 256, 0, s>>>(jobs, first_item, njobs, total, c); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace tl

@@ -214,7 +214,7 @@ __device__ __forceinline__ void site_update(const Coefs<T, NF> &k, const T (&cu)
 // finalize().  Deterministic for a given launch geometry.
 template <int NQ>
 __device__ __forceinline__ void cta_reduce_finalize(const double (&accd)[NQ], const Model &m, const PassCoef &c,
-                                                    Scalars *sc, double *slots)
+                                                    Scalars *sc, double *slots, unsigned bid, unsigned nblocks)
 {
     __shared__ double red[16][NQ];
     __shared__ bool last;
@@ -227,8 +227,6 @@ __device__ __forceinline__ void cta_reduce_finalize(const double (&accd)[NQ], co
         if (lane == 0) red[warp][i] = v;
     }
     __syncthreads();
-    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
-    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (tid < NQ) {
         double s = 0.0;
         for (int w = 0; w < nwarps; ++w) s += red[w][tid];
@@ -238,33 +236,37 @@ __device__ __forceinline__ void cta_reduce_finalize(const double (&accd)[NQ], co
     __syncthreads();
     if (tid == 0) last = (atomicAdd(&sc->ticket, 1u) == nblocks - 1);
     __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double part[NQ];
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) part[i] = 0.0;
-    for (unsigned b = tid; b < nblocks; b += blockDim.x)
-#pragma unroll
-        for (int i = 0; i < NQ; ++i) part[i] += __ldcg(slots + (size_t)b * NQ + i);
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) {
-        double v = warp_sum(part[i]);
-        if (lane == 0) red[warp][i] = v;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double tot[kMaxQ];
-        for (int i = 0; i < NQ; ++i) {
-            double s = 0.0;
-            for (int w = 0; w < nwarps; ++w) s += red[w][i];
-            tot[i] = s;
-        }
-        finalize(m, c, sc, tot);
-        sc->ticket = 0u;
+    if (last) {
         __threadfence();
+        double part[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) part[i] = 0.0;
+        for (unsigned b = tid; b < nblocks; b += blockDim.x)
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) part[i] += __ldcg(slots + (size_t)b * NQ + i);
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            double v = warp_sum(part[i]);
+            if (lane == 0) red[warp][i] = v;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double tot[kMaxQ];
+            for (int i = 0; i < NQ; ++i) {
+                double s = 0.0;
+                for (int w = 0; w < nwarps; ++w) s += red[w][i];
+                tot[i] = s;
+            }
+            finalize(m, c, sc, tot);
+            sc->ticket = 0u;
+            __threadfence();
+        }
     }
+    __syncthreads();  // red[] and last may be reused by the next tile of a persistent CTA
 }
+
+__device__ __forceinline__ unsigned grid_bid() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
+__device__ __forceinline__ unsigned grid_nblocks() { return gridDim.x * gridDim.y * gridDim.z; }
 
 // ---- variant 1: register streaming with a per-thread prefetch ring -------------
 // Each thread owns its 128-bit words.  The HBM stream (the stored phi and pi
@@ -284,19 +286,21 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int Npending>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(Npending) : "memory"); }
 
-template <typename T, int NF, bool MEASURE, int D, int MINB>
-__global__ void __launch_bounds__(256, MINB) fused_pass_ldg(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
-                                                      Scalars *sc, double *slots)
+// One CTA tile (bx, by, bz) of the register-streaming pass; bid/nblocks
+// index the tile among the lattice's tiles for the reduction.
+template <typename T, int NF, bool MEASURE, int D>
+__device__ __forceinline__ void ldg_tile(const Model &m, const FieldPtrs &fp, const PassCoef &c, int txt, int ty,
+                                         int zc, int bx, int by, int bz, unsigned bid, unsigned nblocks, Scalars *sc,
+                                         double *slots, unsigned char *ring_raw)
 {
     constexpr int W = Vec<T>::W;
     constexpr int NQ = 2 * NF + 1;
-    extern __shared__ __align__(16) unsigned char ring_raw[];
     const int N = m.N;
     const int tid = threadIdx.x;
     const int tx = tid % txt, tyi = tid / txt;
-    const int x0 = (blockIdx.x * txt + tx) * W;
-    const int y = blockIdx.y * ty + tyi;
-    const int z0 = blockIdx.z * zc;
+    const int x0 = (bx * txt + tx) * W;
+    const int y = by * ty + tyi;
+    const int z0 = bz * zc;
     const int z1 = min(z0 + zc, N);
     const bool active = (tyi < ty) && (x0 < N) && (y < N);
     // ring slot (plane d, field f, array a) of this thread
@@ -435,7 +439,42 @@ __global__ void __launch_bounds__(256, MINB) fused_pass_ldg(Model m, FieldPtrs f
 #pragma unroll
         for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
     }
-    cta_reduce_finalize<NQ>(accd, m, c, sc, slots);
+    cta_reduce_finalize<NQ>(accd, m, c, sc, slots, bid, nblocks);
+}
+
+template <typename T, int NF, bool MEASURE, int D, int MINB>
+__global__ void __launch_bounds__(256, MINB) fused_pass_ldg(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
+                                                            Scalars *sc, double *slots)
+{
+    extern __shared__ __align__(16) unsigned char ring_raw[];
+    ldg_tile<T, NF, MEASURE, D>(m, fp, c, txt, ty, zc, blockIdx.x, blockIdx.y, blockIdx.z, grid_bid(), grid_nblocks(),
+                                sc, slots, ring_raw);
+}
+
+// ---- batched form: many lattices in one persistent launch ------------------------
+// Each job is one lattice with its own model, fields, scalars, reduction slots
+// and launch geometry (the geometry it would use alone, so its sums and thus
+// its results are bitwise the same alone and in a batch).  The CTAs of the
+// launch walk the flattened list of (job, tile) items.
+
+template <typename T, int NF>
+__global__ void __launch_bounds__(256, 2) fused_pass_group(const BatchJob *jobs, const unsigned *first_item, int njobs,
+                                                           unsigned total, PassCoef c)
+{
+    for (unsigned item = blockIdx.x; item < total; item += gridDim.x) {
+        int lo = 0, hi = njobs - 1;  // last job whose first item <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(first_item + mid) <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchJob &j = jobs[lo];
+        const unsigned local = item - __ldg(first_item + lo);
+        const int bx = (int)(local % (unsigned)j.gx);
+        const int by = (int)((local / (unsigned)j.gx) % (unsigned)j.gy);
+        const int bz = (int)(local / ((unsigned)j.gx * (unsigned)j.gy));
+        ldg_tile<T, NF, false, 0>(j.m, j.fp, c, j.txt, j.ty, j.zc, bx, by, bz, local, j.nblocks, j.sc, j.slots, nullptr);
+    }
 }
 
 // ---- variant 2: bulk-copy staging ------------------------------------------------
@@ -687,7 +726,7 @@ __global__ void __launch_bounds__(288, 2) fused_pass_bulk(Model m, FieldPtrs fp,
     if (s_failed && producer && (tid & 31) == 0)
         for (int kk = (issued > S ? issued - S : 0); kk < issued; ++kk)
             mbar_wait_bounded(&full[kk % S], (kk / S) & 1u, sc);
-    cta_reduce_finalize<NQ>(accd, m, c, sc, slots);
+    cta_reduce_finalize<NQ>(accd, m, c, sc, slots, grid_bid(), grid_nblocks());
 }
 
 template <typename T, int NF, bool MEASURE>

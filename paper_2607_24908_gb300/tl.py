@@ -84,6 +84,11 @@ _SIGS = {
                                            ctypes.c_double, ctypes.POINTER(ctypes.c_void_p),
                                            ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
                                            ctypes.POINTER(ctypes.c_double)]),
+    "tl_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                       ctypes.c_void_p]),
+    "tl_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
+    "tl_batch_destroy": (None, [ctypes.c_void_p]),
+    "tl_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tl_last_error": (ctypes.c_char_p, []),
 }
 
@@ -215,6 +220,55 @@ def tl_energies_noalloc(N: int, kIR: float, n_fields: int, dtype: int, lam: floa
     return out
 
 
+def tl_batch_create(handles: Sequence, cuda_stream: int = 0) -> ctypes.c_void_p:
+    b = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    _check(lib().tl_batch_create(ctypes.byref(b), arr, len(handles), ctypes.c_void_p(cuda_stream)))
+    return b
+
+
+def tl_batch_step(b, n: int, dt: float, integrator: int):
+    _check(lib().tl_batch_step(b, n, dt, integrator))
+
+
+def tl_batch_destroy(b):
+    lib().tl_batch_destroy(b)
+
+
+def tl_autotune(h) -> float:
+    ms = ctypes.c_double()
+    _check(lib().tl_autotune(h, ctypes.byref(ms)))
+    return ms.value
+
+
+class Batch:
+    """Several lattices advanced together (see tl_batch_step)."""
+
+    def __init__(self, lattices: Sequence["Lattice"], stream: int = 0):
+        self.lattices = list(lattices)
+        self.b = tl_batch_create([l.h for l in self.lattices], stream)
+
+    def step(self, n: int, dt: float, integrator="verlet"):
+        tl_batch_step(self.b, n, dt, INTEGRATORS[integrator] if isinstance(integrator, str) else integrator)
+
+    def close(self):
+        if getattr(self, "b", None):
+            tl_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 # --- convenience wrapper --------------------------------------------------------
 
 @dataclass
@@ -240,6 +294,7 @@ class Lattice:
                  alpha: float = 0.0, fstar_over_mp: float = 1.0, a0: float = 1.0, stream: int = 0):
         self.N, self.nf, self.kIR = N, n_fields, kIR
         self.dtype = dtype
+        self.expanding, self.alpha = bool(expanding), alpha
         self.np_dtype = np.float32 if dtype == "f32" else np.float64
         ex = tl_expansion(int(bool(expanding)), alpha, fstar_over_mp, a0)
         self.h = tl_lattice_create(N, kIR, n_fields, DTYPES[dtype], ex, stream)
@@ -298,3 +353,7 @@ class Lattice:
 
     def device_ptr(self, field: int, which: int) -> int:
         return tl_state_device_ptr(self.h, field, which)
+
+    def autotune(self) -> float:
+        """Pick the fastest launch geometry for this lattice shape; returns ms per pass."""
+        return tl_autotune(self.h)

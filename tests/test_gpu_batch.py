@@ -1,0 +1,116 @@
+"""Batched ensembles (tl_batch_*) and the autotuner on the GPU.
+
+A batch advances lattices of uneven N, 1-2 fields, different couplings,
+backgrounds and seeds with one persistent launch per pass (per field count)
+replayed as a CUDA graph; each lattice keeps its own launch geometry, so the
+results must be bitwise those of tl_step on the lattice alone."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2607_24908_gb300 import tl as T
+from paper_2607_24908_gb300.workloads import white_noise_state
+
+pytestmark = pytest.mark.gpu
+
+JOBS = [  # N, fields, q, expanding, dtype seed
+    (32, 1, 0.0, True, 11), (48, 2, 10.0, True, 12), (24, 2, 100.0, False, 13),
+    (40, 1, 0.0, False, 14), (64, 2, 100.0, True, 15), (16, 1, 0.0, True, 16),
+]
+
+
+def make(N, nf, q, expanding, dtype):
+    lat = T.Lattice(N, 0.5, nf, dtype, expanding, 1.0, 1.0, 1.0)
+    lat.set_potential(1.0, q, (0.0, 0.1, 0.0))
+    return lat
+
+
+def fill(lat, N, nf, seed, dtype):
+    npd = np.float32 if dtype == "f32" else np.float64
+    phi, pi = white_noise_state(N, nf, seed=seed, phi0=(1.0, 0.0), sigma_phi=1e-3, sigma_pi=1e-3)
+    lat.set_state(phi.astype(npd), pi.astype(npd), 1.0, 0.0, b_from_constraint=lat.expanding)
+    return phi.astype(npd), pi.astype(npd)
+
+
+@pytest.mark.parametrize("dtype,integ,steps", [("f32", "verlet", 40), ("f64", "yoshida4", 10)])
+def test_batch_is_bitwise_the_single_lattice_path(dtype, integ, steps):
+    alone, batched = [], []
+    for N, nf, q, ex, seed in JOBS:
+        a = make(N, nf, q, ex, dtype)
+        fill(a, N, nf, seed, dtype)
+        a.step(steps, 0.01, integ)
+        alone.append((*a.get_all(), a.energies()))
+        a.close()
+    lats = [make(N, nf, q, ex, dtype) for N, nf, q, ex, _ in JOBS]
+    for lat, (N, nf, q, ex, seed) in zip(lats, JOBS):
+        fill(lat, N, nf, seed, dtype)
+    with T.Batch(lats) as b:
+        b.step(steps // 2, 0.01, integ)
+        b.step(steps - steps // 2, 0.01, integ)  # second call reuses the captured graph when n repeats
+    # the reference ran one call of `steps`; rerun alone with the same split for bitwise comparison
+    alone2 = []
+    for N, nf, q, ex, seed in JOBS:
+        a = make(N, nf, q, ex, dtype)
+        fill(a, N, nf, seed, dtype)
+        a.step(steps // 2, 0.01, integ)
+        a.step(steps - steps // 2, 0.01, integ)
+        alone2.append((*a.get_all(), a.energies()))
+        a.close()
+    for lat, ref, ref1 in zip(lats, alone2, alone):
+        phi, pi = lat.get_all()
+        E = lat.energies()
+        assert np.array_equal(phi, ref[0]) and np.array_equal(pi, ref[1])
+        assert np.array_equal(E.vector(), ref[2].vector()) and E.a == ref[2].a and E.b == ref[2].b
+        assert E.step == steps
+        # one call vs two calls differ only by rounding of the resynchronisation
+        assert np.max(np.abs(phi.astype(np.float64) - ref1[0])) <= 1e-5 * np.max(np.abs(ref1[0]))
+    for lat in lats:
+        lat.close()
+
+
+def test_batch_against_oracle_fp64():
+    dt, steps = 0.01, 20
+    lats, inputs = [], []
+    for N, nf, q, ex, seed in JOBS[:4]:
+        lat = make(N, nf, q, ex, "f64")
+        inputs.append(fill(lat, N, nf, seed, "f64"))
+        lats.append(lat)
+    with T.Batch(lats) as b:
+        b.step(steps, dt, "verlet")
+    for lat, (phi0, pi0), (N, nf, q, ex, seed) in zip(lats, inputs, JOBS[:4]):
+        p = o.Params(N=N, nf=nf, kIR=0.5, expanding=ex, alpha=1.0, lam=1.0, q=q, m2=(0.0, 0.1, 0.0))
+        b0 = math.sqrt(float(np.sum(o.energies(p, phi0, pi0, 1.0))) / 3.0) if ex else 0.0
+        ophi, opi, oa, ob = o.run(p, phi0, pi0, 1.0, b0, dt, steps, o.VERLET)
+        phi, pi = lat.get_all()
+        assert np.max(np.abs(phi - ophi)) / np.max(np.abs(ophi)) < 1e-12
+        assert np.max(np.abs(pi - opi)) / np.max(np.abs(opi)) < 1e-12
+        if ex:
+            E = lat.energies()
+            assert abs(E.a - oa) / oa < 1e-12 and abs(E.b - ob) / ob < 1e-12
+        lat.close()
+
+
+def test_autotune_keeps_state_and_parity(tmp_path, monkeypatch):
+    monkeypatch.setenv("TL_TUNE_FILE", str(tmp_path / "tune.txt"))
+    N, nf = 64, 2
+    p = o.Params(N=N, nf=nf, kIR=0.5, expanding=True, alpha=1.0, lam=1.0, q=100.0)
+    phi0, pi0 = white_noise_state(N, nf, seed=3, phi0=(1.0, 0.0), sigma_phi=1e-3, sigma_pi=1e-3)
+    lat = make(N, nf, 100.0, True, "f64")
+    lat.set_potential(1.0, 100.0, (0.0, 0.0, 0.0))
+    lat.set_state(phi0, pi0, 1.0, 0.0, True)
+    E0 = lat.energies()
+    ms = lat.autotune()
+    assert ms > 0
+    phi, pi = lat.get_all()
+    assert np.array_equal(phi, phi0) and np.array_equal(pi, pi0)  # identity passes
+    E1 = lat.energies()
+    assert E1.a == E0.a and E1.b == E0.b
+    lat.step(10, 0.005, "yoshida4")
+    b0 = math.sqrt(float(np.sum(o.energies(p, phi0, pi0, 1.0))) / 3.0)
+    ophi, opi, oa, ob = o.run(p, phi0, pi0, 1.0, b0, 0.005, 10, o.YOSHIDA4)
+    phi, pi = lat.get_all()
+    assert np.max(np.abs(phi - ophi)) / np.max(np.abs(ophi)) < 1e-12
+    lat.close()
+    assert (tmp_path / "tune.txt").read_text().strip()
