@@ -402,6 +402,56 @@ def run_ensemble(args):
     return 0
 
 
+# ---------------------------------------------------------------------------------
+# Serving: continuous batching vs a plain sequential loop
+# ---------------------------------------------------------------------------------
+
+def run_serve(args):
+    import torch
+    from paper_2607_24908_gb300 import serve as S
+    torch.cuda.set_device(0)
+    s32, s64 = torch.cuda.Stream(), torch.cuda.Stream()
+    streams = {"f32": s32.cuda_stream, "f64": s64.cuda_stream}
+    budget = int(150e9)
+    n = args.jobs
+    base = S.poisson_jobs(n, seed=12345, rate=0.0)
+    # warm-up: one small job of each precision (kernels, FFT plans)
+    warm = [S.JobSpec(-1, 64, 2, 100.0, 100, "f32", 1), S.JobSpec(-2, 64, 2, 100.0, 100, "f64", 2)]
+    S.run_alone(warm)
+    # mean sequential service time from the first jobs, arrivals at t = 0
+    probe = [S.JobSpec(**{**j.__dict__, "arrival": 0.0}) for j in base[:4]]
+    _, t_probe = S.run_alone(probe)
+    mean_service = t_probe / len(probe)
+    rate = 0.8 / mean_service
+    jobs = S.poisson_jobs(n, seed=12345, rate=rate)
+
+    def stats(res, span):
+        lat = np.array([r.latency for r in res])
+        return {"jobs_per_s": len(res) / span, "p50_s": float(np.percentile(lat, 50)),
+                "p99_s": float(np.percentile(lat, 99)), "makespan_s": span}
+
+    served, span_srv = S.serve(jobs, budget, streams=streams)
+    alone, span_seq = S.run_alone(jobs)
+    same = all(np.array_equal(a.energies, b.energies) for a, b in
+               zip(sorted(served, key=lambda r: r.job_id), sorted(alone, key=lambda r: r.job_id)))
+    # saturation: every job present at t = 0
+    sat = [S.JobSpec(**{**j.__dict__, "arrival": 0.0}) for j in jobs]
+    served0, span0 = S.serve(sat, budget, streams=streams)
+    alone0, span0_seq = S.run_alone(sat)
+    line = {"metric": "served jobs/s", "value": len(sat) / span0, "unit": "jobs/s", "higher_is_better": True,
+            "mode": "serve", "n_gpus": 1,
+            "config": {"workload": f"{n} Poisson jobs: N in {{64,128,256,384}}, 1-3 fields, q in {{1,100}}, "
+                                   "500-5000 Verlet steps (dt 0.01), FP32 or FP64, expanding alpha=1, kIR=0.1",
+                       "budget_bytes": budget, "chunk_steps": 100, "arrival_rate_per_s": rate,
+                       "mean_sequential_service_s": mean_service},
+            "poisson_load_0.8": {"served": stats(served, span_srv), "sequential": stats(alone, span_seq)},
+            "saturation": {"served": stats(served0, span0), "sequential": stats(alone0, span0_seq),
+                           "speedup_jobs_per_s": span0_seq / span0},
+            "results_bitwise_equal_served_vs_alone": bool(same)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,9 +461,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--N", type=int, default=0, help="lattice size (default: the workload's 1024; for profiling)")
-    ap.add_argument("--mode", default="step", choices=["step", "ensemble"],
-                    help="step: the 1024^3 fused step (default); ensemble: batched small lattices vs a plain loop")
-    ap.add_argument("--jobs", type=int, default=96)
+    ap.add_argument("--mode", default="step", choices=["step", "ensemble", "serve"],
+                    help="step: the 1024^3 fused step (default); ensemble: batched small lattices vs a plain loop; "
+                         "serve: continuous batching of Poisson-arriving jobs vs a sequential loop")
+    ap.add_argument("--jobs", type=int, default=0, help="jobs for --mode ensemble (96) / serve (24)")
     ap.add_argument("--ens-steps", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -422,7 +473,11 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "ensemble":
+        args.jobs = args.jobs or 96
         return run_ensemble(args)
+    if args.mode == "serve":
+        args.jobs = args.jobs or 24
+        return run_serve(args)
     return run_ours(args)
 
 

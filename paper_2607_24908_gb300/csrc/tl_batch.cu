@@ -90,8 +90,8 @@ int upload_jobs(tl_batch *B)
                                   cudaMemcpyHostToDevice, B->stream));
         }
     }
-    // the host vector is reused next call: make sure the copies have read it
-    TB_CK(cudaStreamSynchronize(B->stream));
+    // h_jobs is pageable memory: each cudaMemcpyAsync has staged it before
+    // returning, so the vector can be refilled at once without a sync.
     return TL_OK;
 }
 

@@ -4,6 +4,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -50,3 +51,25 @@ def test_create_without_gpu_fails_cleanly():
     with pytest.raises(tl.TLError) as e:
         tl.Lattice(30, 0.5, 1, "f64")
     assert e.value.code == tl.EINVAL
+
+
+def test_serving_job_generator_and_budget_arithmetic():
+    """Host-side pieces of the server that need no GPU."""
+    from paper_2607_24908_gb300 import serve as S
+    jobs = S.poisson_jobs(50, seed=12345, rate=10.0)
+    assert len(jobs) == 50
+    arr = [j.arrival for j in jobs]
+    assert arr == sorted(arr) and arr[0] > 0
+    for j in jobs:
+        assert j.N in (64, 128, 256, 384) and 1 <= j.n_fields <= 3 and j.q in (1.0, 100.0)
+        assert 500 <= j.steps <= 5000 and j.steps % 100 == 0 and j.dtype in ("f32", "f64")
+        esz = 4 if j.dtype == "f32" else 8
+        assert j.state_bytes() == 4 * j.n_fields * j.N ** 3 * esz
+        assert j.budget_bytes() > j.state_bytes()
+    # mean inter-arrival ~ 1/rate
+    gaps = np.diff([0.0] + arr)
+    assert 0.05 < gaps.mean() < 0.2
+    srv = S.Server(budget_bytes=jobs[0].budget_bytes())
+    assert srv.fits(jobs[0])
+    srv.used = 1
+    assert not srv.fits(jobs[0])
