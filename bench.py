@@ -410,8 +410,6 @@ def run_serve(args):
     import torch
     from paper_2607_24908_gb300 import serve as S
     torch.cuda.set_device(0)
-    s32, s64 = torch.cuda.Stream(), torch.cuda.Stream()
-    streams = {"f32": s32.cuda_stream, "f64": s64.cuda_stream}
     budget = int(150e9)
     n = args.jobs
     base = S.poisson_jobs(n, seed=12345, rate=0.0)
@@ -430,13 +428,13 @@ def run_serve(args):
         return {"jobs_per_s": len(res) / span, "p50_s": float(np.percentile(lat, 50)),
                 "p99_s": float(np.percentile(lat, 99)), "makespan_s": span}
 
-    served, span_srv = S.serve(jobs, budget, streams=streams)
+    served, span_srv = S.serve(jobs, budget)
     alone, span_seq = S.run_alone(jobs)
     same = all(np.array_equal(a.energies, b.energies) for a, b in
                zip(sorted(served, key=lambda r: r.job_id), sorted(alone, key=lambda r: r.job_id)))
     # saturation: every job present at t = 0
     sat = [S.JobSpec(**{**j.__dict__, "arrival": 0.0}) for j in jobs]
-    served0, span0 = S.serve(sat, budget, streams=streams)
+    served0, span0 = S.serve(sat, budget)
     alone0, span0_seq = S.run_alone(sat)
     line = {"metric": "served jobs/s", "value": len(sat) / span0, "unit": "jobs/s", "higher_is_better": True,
             "mode": "serve", "n_gpus": 1,
@@ -476,7 +474,7 @@ def main():
         args.jobs = args.jobs or 96
         return run_ensemble(args)
     if args.mode == "serve":
-        args.jobs = args.jobs or 24
+        args.jobs = args.jobs or 16
         return run_serve(args)
     return run_ours(args)
 

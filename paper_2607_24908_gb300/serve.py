@@ -3,13 +3,15 @@
 Jobs (lattice size, fields, couplings, steps, precision, seed) arrive over
 time.  The server admits a waiting job as soon as its device memory fits in
 the budget beside the jobs already resident, draws its initial state on the
-device, and from then on advances it together with every other resident job:
-each scheduler tick runs ``chunk`` velocity-Verlet steps of all resident jobs
-of one precision as one batched call (``tl_batch_step``: one grouped launch per
-pass, replayed as a CUDA graph), FP32 and FP64 jobs on two streams so their
-work overlaps.  A job that has run all its steps is reaped (final energies and
-spectrum read back, lattice destroyed, memory returned) and the freed budget
-admits the next arrivals at the following tick.
+device, and from then on advances it together with the other resident jobs
+of its lane.  A lane is one precision and one size class with its own CUDA
+stream; whenever a lane is idle the host reaps its finished jobs and starts
+its next ``chunk`` velocity-Verlet steps for all its jobs as one batched call
+(``tl_batch_step``: one grouped launch per pass, replayed as a CUDA graph).
+Lanes run concurrently on the device, so small jobs are not held to the pace
+of large ones.  A reaped job's final energies and spectrum are read back, its
+lattice destroyed and its memory returned, and the freed budget admits the
+next arrivals.
 
 Every job advances in the same ``chunk``-step calls whatever else is resident,
 and keeps the launch geometry it has alone, so its results are bitwise those
@@ -19,8 +21,8 @@ of running it alone (``run_alone``).  Step counts must be multiples of
 from __future__ import annotations
 
 import time
-from dataclasses import dataclass, field
-from typing import Callable, Dict, List, Optional
+from dataclasses import dataclass
+from typing import Callable, List, Optional
 
 import numpy as np
 
@@ -95,91 +97,114 @@ class _Active:
     admitted: float
 
 
+def job_cost(spec: JobSpec) -> float:
+    """Relative device time per step (FP64 runs ALU-bound, ~8x an FP32 site)."""
+    return spec.N ** 3 * spec.n_fields * (8.0 if spec.dtype == "f64" else 1.0)
+
+
+SMALL_COST = 128 ** 3 * 3  # jobs up to this per-step cost share the "small" lanes
+
+
+class _Lane:
+    """Jobs of one precision and size class, advanced together on their own
+    stream; the host starts the lane's next chunk as soon as the last one is
+    done, independently of the other lanes."""
+
+    def __init__(self, dtype: str, stream):
+        self.dtype = dtype
+        self.stream = stream
+        self.jobs: List[_Active] = []
+        self.batch: Optional[T.Batch] = None
+        self.members: tuple = ()
+        self.event = None
+        self.inflight: List[_Active] = []
+
+    def busy(self) -> bool:
+        return self.event is not None and not self.event.query()
+
+
 class Server:
     """Continuous batching over resident lattices (see the module docstring)."""
 
-    def __init__(self, budget_bytes: int, chunk: int = 100, streams: Optional[Dict[str, int]] = None):
+    def __init__(self, budget_bytes: int, chunk: int = 100):
         self.budget = int(budget_bytes)
         self.chunk = int(chunk)
-        self.streams = streams or {"f32": 0, "f64": 0}
-        self.active: List[_Active] = []
+        self.lanes = {}  # (dtype, size class) -> _Lane, created with its stream on first use
         self.used = 0
-        self._batches: Dict[str, T.Batch] = {}
-        self._members: Dict[str, tuple] = {}
-        self.rejected: List[int] = []
+
+    @property
+    def active(self) -> List[_Active]:
+        return [a for lane in self.lanes.values() for a in lane.jobs]
 
     def fits(self, spec: JobSpec) -> bool:
         return self.used + spec.budget_bytes() <= self.budget
 
+    def lane_of(self, spec: JobSpec) -> _Lane:
+        key = (spec.dtype, "small" if job_cost(spec) <= SMALL_COST else "big")
+        if key not in self.lanes:
+            import torch
+            self.lanes[key] = _Lane(spec.dtype, torch.cuda.Stream())
+        return self.lanes[key]
+
     def admit(self, spec: JobSpec, now: float) -> None:
         if spec.steps % self.chunk != 0:
             raise ValueError(f"job {spec.job_id}: steps must be a multiple of {self.chunk}")
-        lat = _new_lattice(spec, self.streams[spec.dtype])
-        self.active.append(_Active(spec, lat, 0, now))
+        lane = self.lane_of(spec)
+        lat = _new_lattice(spec, lane.stream.cuda_stream)
+        lane.jobs.append(_Active(spec, lat, 0, now))
         self.used += spec.budget_bytes()
 
-    def _batch(self, dtype: str) -> Optional[T.Batch]:
-        members = tuple(id(a.lat) for a in self.active if a.spec.dtype == dtype)
-        if not members:
-            self._drop(dtype)
-            return None
-        if self._members.get(dtype) != members:
-            self._drop(dtype)
-            lats = [a.lat for a in self.active if a.spec.dtype == dtype]
-            self._batches[dtype] = T.Batch(lats, self.streams[dtype])
-            self._members[dtype] = members
-        return self._batches[dtype]
-
-    def _drop(self, dtype: str) -> None:
-        b = self._batches.pop(dtype, None)
-        self._members.pop(dtype, None)
-        if b is not None:
-            b.close()
-
-    def tick(self) -> None:
-        """Advance every resident job by one chunk (both precisions, two streams)."""
-        for dtype in ("f32", "f64"):
-            b = self._batch(dtype)
-            if b is not None:
-                b.step(self.chunk, 0.01, "verlet")
-        for a in self.active:
-            a.done_steps += self.chunk
-
-    def reap(self, t0: float) -> List[JobResult]:
-        out, keep = [], []
-        for a in self.active:
-            if a.done_steps >= a.spec.steps:
-                out.append((a, None))
-            else:
-                keep.append(a)
-        if not out:
-            return []
-        # results are read on the lattices' own streams after the batch work
-        for dtype in ("f32", "f64"):
-            if any(a.spec.dtype == dtype for a, _ in out):
-                self._drop(dtype)
-        results = []
-        for a, _ in out:
-            results.append(_result(a.spec, a.lat, a.admitted, t0))
-            a.lat.close()
-            self.used -= a.spec.budget_bytes()
-        self.active = keep
-        return results
+    def service(self, t0: float) -> List[JobResult]:
+        """Reap finished jobs of idle lanes and start their next chunk.  Returns
+        the jobs completed now."""
+        done: List[JobResult] = []
+        for lane in self.lanes.values():
+            if lane.busy():
+                continue
+            lane.event = None
+            for a in lane.inflight:
+                a.done_steps += self.chunk
+            lane.inflight = []
+            finished = [a for a in lane.jobs if a.done_steps >= a.spec.steps]
+            if finished:
+                lane.jobs = [a for a in lane.jobs if a.done_steps < a.spec.steps]
+                if lane.batch is not None:
+                    lane.batch.close()
+                    lane.batch, lane.members = None, ()
+                for a in finished:
+                    done.append(_result(a.spec, a.lat, a.admitted, t0))
+                    a.lat.close()
+                    self.used -= a.spec.budget_bytes()
+            if not lane.jobs:
+                continue
+            members = tuple(id(a.lat) for a in lane.jobs)
+            if members != lane.members:
+                if lane.batch is not None:
+                    lane.batch.close()
+                lane.batch = T.Batch([a.lat for a in lane.jobs], lane.stream.cuda_stream)
+                lane.members = members
+            lane.batch.step(self.chunk, 0.01, "verlet")
+            lane.inflight = list(lane.jobs)
+            import torch
+            lane.event = torch.cuda.Event()
+            lane.event.record(lane.stream)
+        return done
 
     def close(self):
-        for d in list(self._batches):
-            self._drop(d)
-        for a in self.active:
-            a.lat.close()
-        self.active = []
+        for lane in self.lanes.values():
+            if lane.batch is not None:
+                lane.batch.close()
+            for a in lane.jobs:
+                a.lat.close()
+            lane.jobs, lane.batch, lane.members, lane.inflight = [], None, (), []
         self.used = 0
 
 
 def serve(jobs: List[JobSpec], budget_bytes: int, chunk: int = 100,
-          clock: Callable[[], float] = time.perf_counter, streams: Optional[Dict[str, int]] = None):
+          clock: Callable[[], float] = time.perf_counter):
     """Run ``jobs`` (sorted by arrival) through a continuous-batching server in
     real time.  Returns (results in completion order, makespan seconds)."""
-    srv = Server(budget_bytes, chunk, streams)
+    srv = Server(budget_bytes, chunk)
     pending = sorted(jobs, key=lambda j: j.arrival)
     for j in pending:
         if j.budget_bytes() > budget_bytes:
@@ -190,18 +215,18 @@ def serve(jobs: List[JobSpec], budget_bytes: int, chunk: int = 100,
     try:
         while len(results) < len(jobs):
             now = clock() - t0
-            # admit arrivals in order while they fit
             while i < len(pending) and pending[i].arrival <= now and srv.fits(pending[i]):
                 srv.admit(pending[i], now)
                 i += 1
-            if not srv.active:
-                if i < len(pending):  # idle until the next arrival
+            got = srv.service(t0)
+            results.extend(got)
+            if not got:
+                if not srv.active and i < len(pending):
                     wait = pending[i].arrival - (clock() - t0)
                     if wait > 0:
-                        time.sleep(wait)
-                continue
-            srv.tick()
-            results.extend(srv.reap(t0))
+                        time.sleep(min(wait, 0.05))
+                else:
+                    time.sleep(0.0005)
     finally:
         srv.close()
     return results, clock() - t0

@@ -18,8 +18,6 @@ def small_jobs():
 
 
 def test_served_results_equal_alone_and_budget_respected():
-    import torch
-    s32, s64 = torch.cuda.Stream(), torch.cuda.Stream()
     jobs = small_jobs()
     budget = 3 * max(j.budget_bytes() for j in jobs)  # at most ~3 jobs resident: forces queueing
     peak = {"used": 0}
@@ -31,8 +29,7 @@ def test_served_results_equal_alone_and_budget_respected():
         assert self.used <= self.budget
     S.Server.admit = admit
     try:
-        served, t_served = S.serve(jobs, budget, chunk=100,
-                                   streams={"f32": s32.cuda_stream, "f64": s64.cuda_stream})
+        served, t_served = S.serve(jobs, budget, chunk=100)
     finally:
         S.Server.admit = orig_admit
     alone, _ = S.run_alone(jobs, chunk=100)
