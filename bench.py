@@ -450,6 +450,57 @@ def run_serve(args):
     return 0
 
 
+# ---------------------------------------------------------------------------------
+# phi^4 through parametric resonance in an expanding box (256^3, VV, FP64 and FP32)
+# ---------------------------------------------------------------------------------
+
+def run_expanding256(args):
+    import torch
+    from paper_2607_24908_gb300 import tl as T
+    from paper_2607_24908_gb300.workloads import PHI4_EXPANDING_256 as W2
+    torch.cuda.set_device(0)
+    steps = args.ens_steps if args.ens_steps != 1000 else W2.steps
+    every = 100
+    out = {}
+    for dtype in ("f64", "f32"):
+        stream = torch.cuda.Stream()
+        lat = T.Lattice(W2.N, W2.kIR, 1, dtype, True, W2.alpha, W2.fstar_over_mp, 1.0, stream=stream.cuda_stream)
+        lat.set_potential(W2.lam, 0.0, (0.0, 0.0, 0.0))
+        lat.init_fluctuations(W2.seed, A=W2.A, meff2=W2.meff2, phi0=W2.phi0)
+        series = []
+        t_step = 0.0
+        for s0 in range(0, steps, every):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(every, W2.dt, "verlet")
+            e1.record(stream)
+            E = lat.energies()
+            t_step += e0.elapsed_time(e1)
+            k, P, c = lat.spectrum(0, 0)
+            series.append({"step": E.step, "a": E.a, "H_resid": E.hubble_resid, "K": float(E.K[0]),
+                           "G": float(E.G[0]), "V": E.V, "P": P})
+        lat.close()
+        out[dtype] = (series, t_step / (steps + steps // every) )
+    s64, ms64 = out["f64"]
+    s32, ms32 = out["f32"]
+    rows = []
+    for a, b in zip(s64, s32):
+        sel = a["P"] > 1e-6 * a["P"].max()
+        rows.append({"step": a["step"], "a": a["a"], "hubble_resid_f64": a["H_resid"], "hubble_resid_f32": b["H_resid"],
+                     "rho_f64": a["K"] + a["G"] + a["V"],
+                     "f32_vs_f64_energy_rel": max(abs(b[q] - a[q]) / (a["K"] + a["G"] + a["V"]) for q in ("K", "G", "V")),
+                     "f32_vs_f64_spectrum_rel_max": float(np.max(np.abs(b["P"][sel] - a["P"][sel]) / a["P"][sel])),
+                     "P_bins_1_4_16_f64": [float(a["P"][i]) for i in (1, 4, 16)]})
+    sites = W2.N ** 3
+    line = {"mode": "expanding256", "workload": W2.name, "steps": steps,
+            "ms_per_pass": {"f64": ms64, "f32": ms32},
+            "site_updates_per_s": {"f64": sites / (ms64 / 1e3), "f32": sites / (ms32 / 1e3)},
+            "every_100_steps": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -459,7 +510,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--N", type=int, default=0, help="lattice size (default: the workload's 1024; for profiling)")
-    ap.add_argument("--mode", default="step", choices=["step", "ensemble", "serve"],
+    ap.add_argument("--mode", default="step", choices=["step", "ensemble", "serve", "expanding256"],
                     help="step: the 1024^3 fused step (default); ensemble: batched small lattices vs a plain loop; "
                          "serve: continuous batching of Poisson-arriving jobs vs a sequential loop")
     ap.add_argument("--jobs", type=int, default=0, help="jobs for --mode ensemble (96) / serve (24)")
@@ -473,6 +524,8 @@ def main():
     if args.mode == "ensemble":
         args.jobs = args.jobs or 96
         return run_ensemble(args)
+    if args.mode == "expanding256":
+        return run_expanding256(args)
     if args.mode == "serve":
         args.jobs = args.jobs or 16
         return run_serve(args)

@@ -302,3 +302,35 @@ def test_full_size_1024_two_fields_sampled():
     assert np.max(np.abs(E0.vector() - oE0)) / np.sum(oE0) < 1e-5
     for i in range(len(oE0)):  # every component, relative to itself
         assert abs(E0.vector()[i] - oE0[i]) / abs(oE0[i]) < 1e-4, (i, E0.vector()[i], oE0[i])
+
+
+# --- chaotic nonlinear regime: volume averages and spectra within 1% ----------------------
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_chaotic_regime_energies_and_spectra_within_one_percent(dtype):
+    """Strongly nonlinear two-field state (white noise sigma 0.3 on phi = 1,
+    q = 10), 2000 Verlet steps: the dynamics is chaotic (on the oracle alone a
+    1e-7 perturbation of the input grows to ~3e-3 in the fields by then), yet
+    volume averages and shell spectra must stay within 1% (bins with >= 100
+    modes and P_b >= 1e-6 max)."""
+    N, nf, dt, steps = 48, 2, 0.02, 2000
+    p = o.Params(N=N, nf=nf, kIR=0.5, lam=1.0, q=10.0, m2=(0.0, 0.5, 0.0))
+    npd = np.float32 if dtype == "f32" else np.float64
+    phi0, pi0 = white_noise_state(N, nf, seed=99, phi0=(1.0, 0.5), sigma_phi=0.3, sigma_pi=0.3)
+    phi0, pi0 = phi0.astype(npd), pi0.astype(npd)
+    with make(p, dtype) as lat:
+        lat.set_state(phi0, pi0)
+        lat.step(steps, dt, "verlet")
+        E = lat.energies()
+        spec = [lat.spectrum(f, 0) for f in range(nf)]
+    ophi, opi, _, _ = o.run(p, phi0, pi0, 1.0, 0.0, dt, steps, o.VERLET)
+    oE = o.energies(p, ophi, opi)
+    # nonlinear: the potential and gradient energies are of the same order as the kinetic
+    assert min(oE[:2 * nf]) > 1e-3 * max(oE)
+    assert np.max(np.abs(E.vector() - oE) / np.abs(oE)) < 0.01, (E.vector(), oE)
+    for f in range(nf):
+        k, P, c = spec[f]
+        ok, oP, oc = o.spectrum(p, ophi[f])
+        sel = (oc >= 100) & (oP >= 1e-6 * oP.max())
+        assert sel.sum() > 10
+        assert np.max(np.abs(P[sel] - oP[sel]) / oP[sel]) < 0.01
