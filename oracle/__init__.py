@@ -346,3 +346,34 @@ def vv_step_at_sites(p: Params, phi, pi, sites, dt: float):
     F1 = _patch_force(p, ph1)                             # centre
     pi1 = pih[:, :, 1, 1, 1] + 0.5 * dt * F1[:, :, 0, 0, 0]
     return ph1[:, :, 1, 1, 1], pi1
+
+
+# ---- Langevin phi^4 (Sec. 2, Eq. 1) -------------------------------------------------
+
+LANGEVIN_STREAM = 1 << 63  # high bit of the second Philox counter word marks Langevin noise
+
+
+def langevin_noise(N: int, seed: int, step: int) -> np.ndarray:
+    """Unit Gaussian per site for one step: Philox-2x64-10 of counter
+    (site index, 2^63 + step) under key seed, Box-Muller on the two words
+    (u1 in (0, 1], u2 in [0, 1)): xi = sqrt(-2 ln u1) cos(2 pi u2)."""
+    w = philox2x64(np.arange(N ** 3, dtype=np.uint64), LANGEVIN_STREAM + int(step), seed)
+    u1, u2 = _uniforms(w)
+    return (np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)).reshape(N, N, N)
+
+
+def langevin_run(N: int, kIR: float, phi, dt: float, nsteps: int, lam: float, m2: float, noise: float,
+                 seed: int, step0: int = 0) -> np.ndarray:
+    """Euler-Maruyama for d phi/dt = Lap phi - m^2 phi - (lam/2) phi^3 + noise * eta,
+    <eta eta> = delta(t - t') per site:  phi += dt (Lap phi - m^2 phi - lam/2 phi^3)
+    + noise sqrt(dt) xi_n  (the update of the paper's Langevin listing, Sec. 2,
+    where eta is drawn per site and rescaled by 1/sqrt(dt)).  Steps are numbered
+    from step0 for the noise counters."""
+    dx = 2.0 * math.pi / (kIR * N)
+    f = np.array(phi, dtype=np.float64, copy=True).reshape(N, N, N)
+    for n in range(nsteps):
+        lap = sum(np.roll(f, 1, ax) + np.roll(f, -1, ax) - 2.0 * f for ax in range(3)) / dx ** 2
+        drift = lap - m2 * f - 0.5 * lam * f ** 3
+        xi = langevin_noise(N, seed, step0 + n) if noise != 0.0 else 0.0
+        f = f + dt * drift + noise * math.sqrt(dt) * xi
+    return f

@@ -7,6 +7,23 @@
 
 namespace tl {
 
+// x^e with integer exponents by repeated squaring (as the pass's finalize does)
+__device__ double powe_h(double x, double e)
+{
+    const double r = rint(e);
+    if (r == e && fabs(r) <= 16.0) {
+        int n = (int)fabs(r);
+        double acc = 1.0, b = x;
+        while (n) {
+            if (n & 1) acc *= b;
+            b *= b;
+            n >>= 1;
+        }
+        return r < 0.0 ? 1.0 / acc : acc;
+    }
+    return pow(x, e);
+}
+
 __global__ void set_background_kernel(Model m, Scalars *sc, double a, double b)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -14,10 +31,10 @@ __global__ void set_background_kernel(Model m, Scalars *sc, double a, double b)
         const double al = m.alpha;
         sc->a = a;
         sc->b = b;
-        sc->wl = pow(a, 1.0 + al);
-        sc->wv = pow(a, 3.0 + al);
-        sc->wk = pow(a, -6.0);
-        sc->wg = pow(a, -2.0);
+        sc->wl = powe_h(a, 1.0 + al);
+        sc->wv = powe_h(a, 3.0 + al);
+        sc->wk = powe_h(a, -6.0);
+        sc->wg = powe_h(a, -2.0);
     } else {
         sc->a = 1.0;
         sc->b = 0.0;

@@ -86,6 +86,25 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// x^e: integer exponents up to 16 in magnitude by repeated squaring (a few
+// multiplications instead of a pow() on the FP64 unit, which this last-CTA
+// tail would otherwise serialise every pass); other exponents by pow().
+__device__ __forceinline__ double powe(double x, double e)
+{
+    const double r = rint(e);
+    if (r == e && fabs(r) <= 16.0) {
+        int n = (int)fabs(r);
+        double acc = 1.0, b = x;
+        while (n) {
+            if (n & 1) acc *= b;
+            b *= b;
+            n >>= 1;
+        }
+        return r < 0.0 ? 1.0 / acc : acc;
+    }
+    return pow(x, e);
+}
+
 // Scale-factor update and next-pass coefficients (one thread of the last CTA).
 // tot: raw lattice sums  [sum pi_int_f^2, sum |grad+ phi_f|^2 dx^2, sum V].
 static __device__ void finalize(const Model &m, const PassCoef &c, Scalars *sc, const double *tot)
@@ -115,25 +134,25 @@ static __device__ void finalize(const Model &m, const PassCoef &c, Scalars *sc, 
         const double rho = K + G + V;
         double b = sc->b, b_eval;
         if (c.set_b_from_constraint) {
-            b = pow(a, 1.0 + al) * sqrt(m.mu2 * rho / 3.0);
+            b = powe(a, 1.0 + al) * sqrt(m.mu2 * rho / 3.0);
             b_eval = b;
         } else {
-            const double fb = pow(a, 2.0 * al + 1.0) * (m.mu2 / 3.0) * ((al - 2.0) * K + al * G + (al + 1.0) * V);
+            const double fb = powe(a, 2.0 * al + 1.0) * (m.mu2 / 3.0) * ((al - 2.0) * K + al * G + (al + 1.0) * V);
             b_eval = b + c.hb_dt * fb;
             b = b + c.edt * fb;
         }
         if (c.integer_time) {
             const double H2 = (b_eval / a) * (b_eval / a);
-            sc->hubble = fabs(H2 - pow(a, 2.0 * al) * m.mu2 * rho / 3.0) / H2;
+            sc->hubble = fabs(H2 - powe(a, 2.0 * al) * m.mu2 * rho / 3.0) / H2;
         }
         const double an = a + c.dnext_dt * b;
-        sc->drift = c.dnext_dt * pow(0.5 * (a + an), al - 3.0);
+        sc->drift = c.dnext_dt * powe(0.5 * (a + an), al - 3.0);
         sc->a = an;
         sc->b = b;
-        sc->wl = pow(an, 1.0 + al);
-        sc->wv = pow(an, 3.0 + al);
-        sc->wk = pow(an, -6.0);
-        sc->wg = pow(an, -2.0);
+        sc->wl = powe(an, 1.0 + al);
+        sc->wv = powe(an, 3.0 + al);
+        sc->wk = powe(an, -6.0);
+        sc->wg = powe(an, -2.0);
     } else {
         sc->drift = c.dnext_dt;
         sc->hubble = 0.0;

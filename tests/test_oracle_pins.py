@@ -442,3 +442,68 @@ def test_vv_step_at_sites_matches_full_step():
     f, g, _, _ = o.run(p, phi, pi, 1.0, 0.0, 0.03, 1, o.VERLET)
     assert np.max(np.abs(a - f[:, s[:, 0], s[:, 1], s[:, 2]].T)) < 1e-15
     assert np.max(np.abs(b - g[:, s[:, 0], s[:, 1], s[:, 2]].T)) < 1e-15
+
+
+# --- 15. Langevin (Sec. 2): noise statistics, relaxation, discrete OU spectrum --------------
+
+def test_langevin_noise_is_unit_gaussian_and_independent():
+    xi = o.langevin_noise(32, seed=5, step=0)
+    xj = o.langevin_noise(32, seed=5, step=1)
+    n = xi.size
+    assert abs(xi.mean()) < 4 / math.sqrt(n) and abs(xi.var() - 1.0) < 4 * math.sqrt(2.0 / n)
+    assert abs(np.mean(xi ** 4) - 3.0) < 0.1  # Gaussian kurtosis
+    assert abs(np.corrcoef(xi.ravel(), xj.ravel())[0, 1]) < 5 / math.sqrt(n)
+    assert np.array_equal(xi, o.langevin_noise(32, seed=5, step=0))
+
+
+def test_langevin_deterministic_relaxation_of_a_plane_wave():
+    """noise = 0, lam = 0: a lattice Fourier mode decays as (1 - dt w^2)^n exactly,
+    w^2 = m^2 + sum_i (2/dx sin(k_i dx/2))^2."""
+    N, kIR, dt, m2 = 16, 0.5, 0.02, 0.5
+    p = o.Params(N=N, kIR=kIR)
+    phi0 = plane_wave(N, (1, 2, 3))
+    w2 = lattice_omega2(p, (1, 2, 3), m2)
+    f = o.langevin_run(N, kIR, phi0, dt, 50, 0.0, m2, 0.0, seed=1)
+    assert np.max(np.abs(f - phi0 * (1.0 - dt * w2) ** 50)) < 1e-14
+
+
+def test_langevin_stationary_spectrum_of_the_discrete_ou_process():
+    """lam = 0: each Fourier mode is the AR(1) map x -> (1 - dt w^2) x + sqrt(dt) noise
+    * (DFT of white noise), so its stationary variance is N^3 dt noise^2 /
+    (1 - (1 - dt w^2)^2) for the unnormalised DFT; averaged over modes of
+    similar w the measured power matches to a few percent."""
+    N, kIR, dt, m2, noise = 16, 0.5, 0.05, 1.0, 1.0
+    p = o.Params(N=N, kIR=kIR)
+    f = np.zeros((N, N, N))
+    f = o.langevin_run(N, kIR, f, dt, 200, 0.0, m2, noise, seed=3)  # burn-in (decay time 1/(dt w^2) <= 20)
+    acc = np.zeros((N, N, N))
+    samples = 120
+    for s in range(samples):
+        f = o.langevin_run(N, kIR, f, dt, 5, 0.0, m2, noise, seed=3, step0=200 + 5 * s)
+        acc += np.abs(np.fft.fftn(f)) ** 2
+    acc /= samples
+    n = np.rint(np.fft.fftfreq(N, 1.0 / N))
+    nz, ny, nx = np.meshgrid(n, n, n, indexing="ij")
+    w2 = m2 + sum((2.0 / p.dx * np.sin(np.pi * c / N)) ** 2 for c in (nx, ny, nz))
+    r = 1.0 - dt * w2
+    expect = N ** 3 * dt * noise ** 2 / (1.0 - r * r)
+    ratio = acc / expect
+    # group modes into 8 bins of w^2; each bin averages many (correlated-in-time) samples
+    edges = np.quantile(w2, np.linspace(0, 1, 9))
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = (w2 >= lo) & (w2 <= hi)
+        assert abs(ratio[sel].mean() - 1.0) < 0.08, (lo, hi, ratio[sel].mean())
+
+
+def test_langevin_nonlinear_term_closed_form_first_order():
+    """No noise, m = 0, homogeneous field: d phi/dt = -(lam/2) phi^3 has
+    phi(t) = phi0 / sqrt(1 + lam phi0^2 t); Euler-Maruyama converges at order 1
+    (error halves with dt), which fixes the lam/2 coefficient."""
+    N, lam, phi0, T = 4, 1.0, 1.5, 1.0
+    exact = phi0 / math.sqrt(1.0 + lam * phi0 ** 2 * T)
+    errs = []
+    for dt in (0.01, 0.005):
+        f = o.langevin_run(N, 0.5, np.full((N, N, N), phi0), dt, int(round(T / dt)), lam, 0.0, 0.0, seed=1)
+        errs.append(abs(f[0, 0, 0] - exact))
+    assert errs[1] < 5e-3
+    assert 1.8 < errs[0] / errs[1] < 2.2, errs
