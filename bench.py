@@ -501,6 +501,40 @@ def run_expanding256(args):
     return 0
 
 
+# ---------------------------------------------------------------------------------
+# Langevin phi^4 (the paper's interface example) throughput
+# ---------------------------------------------------------------------------------
+
+def run_langevin(args):
+    import torch
+    from paper_2607_24908_gb300 import tl as T
+    torch.cuda.set_device(0)
+    N = args.N or 512
+    peak, peak_kind = peaks()
+    out = {}
+    for dtype in ("f32", "f64"):
+        stream = torch.cuda.Stream()
+        lat = T.Lattice(N, 0.5, 1, dtype, stream=stream.cuda_stream)
+        npd = np.float32 if dtype == "f32" else np.float64
+        lat.set_state(np.full((1, N, N, N), 0.5, npd), np.zeros((1, N, N, N), npd))
+        lat.langevin(args.warmup, 0.01, 1.0, 0.5, 1.0, 7)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.langevin(args.steps, 0.01, 1.0, 0.5, 1.0, 7)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        esz = 4 if dtype == "f32" else 8
+        out[dtype] = {"ms_per_step": ms, "site_updates_per_s": N ** 3 / (ms / 1e3),
+                      "hbm_gbs": 2 * esz * N ** 3 / (ms / 1e3) / 1e9,
+                      "frac_of_hbm": 2 * esz * N ** 3 / (ms / 1e3) / 1e9 / peak}
+        lat.close()
+    print(json.dumps({"mode": "langevin", "N": N, "steps": args.steps, "peak_gbs": peak, "peak_source": peak_kind,
+                      "results": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -510,7 +544,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--N", type=int, default=0, help="lattice size (default: the workload's 1024; for profiling)")
-    ap.add_argument("--mode", default="step", choices=["step", "ensemble", "serve", "expanding256"],
+    ap.add_argument("--mode", default="step", choices=["step", "ensemble", "serve", "expanding256", "langevin"],
                     help="step: the 1024^3 fused step (default); ensemble: batched small lattices vs a plain loop; "
                          "serve: continuous batching of Poisson-arriving jobs vs a sequential loop")
     ap.add_argument("--jobs", type=int, default=0, help="jobs for --mode ensemble (96) / serve (24)")
@@ -524,6 +558,8 @@ def main():
     if args.mode == "ensemble":
         args.jobs = args.jobs or 96
         return run_ensemble(args)
+    if args.mode == "langevin":
+        return run_langevin(args)
     if args.mode == "expanding256":
         return run_expanding256(args)
     if args.mode == "serve":

@@ -197,6 +197,24 @@ int tl_energies_noalloc(int N, double kIR, int n_fields, tl_dtype dtype, const t
                         const tl_expansion *expansion, double a, const void *const *phi, const void *const *pi,
                         void *cuda_stream, double *out);
 
+/* ---- Langevin evolution (Sec. 2, Eq. 1: the paper's interface example) ---- */
+
+typedef struct {
+    double lambda; /* the drift is Lap phi - m2 phi - (lambda/2) phi^3 */
+    double m2;
+    double noise;  /* amplitude of eta: <eta eta> = noise^2 delta(t-t') per site */
+} tl_langevin_params;
+
+/* n Euler-Maruyama steps of phi_0:  phi <- phi + dt (Lap phi - m2 phi -
+ * lambda/2 phi^3) + noise sqrt(dt) xi, xi a unit Gaussian per site and step:
+ * Philox-2x64-10 of counter (site index [z][y][x], 2^63 + step) under key
+ * seed, Box-Muller on the two words (u1 = (w0 >> 11 + 1) 2^-53,
+ * u2 = (w1 >> 11) 2^-53, xi = sqrt(-2 ln u1) cos(2 pi u2)).  Steps are counted
+ * from the last tl_set_state / tl_init_fluctuations.  Only phi_0 evolves (the
+ * momenta are untouched); the energies are re-measured on demand.  Enqueues
+ * only.  Errors: TL_EINVAL, TL_ESTATE (phi_0 not set, or in a batch), TL_ECUDA. */
+int tl_langevin_step(tl_lattice *lat, int n, double dt, const tl_langevin_params *p, uint64_t seed);
+
 /* ---- batched ensembles and launch tuning (beyond the paper's single
  * lattice: many independent small lattices advanced together) ---- */
 

@@ -457,6 +457,7 @@ int tl_set_state(tl_lattice *L, int field, int which, const void *host, size_t b
     L->state_mask |= 1u << (2 * field + which);
     L->has_state = L->state_mask == (1u << (2 * L->nf)) - 1u;
     L->step = 0;
+    L->langevin_steps = 0;
     L->energies_valid = false;
     return TL_OK;
 }
@@ -545,6 +546,7 @@ int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
     L->state_mask = (1u << (2 * L->nf)) - 1u;
     L->has_state = true;
     L->step = 0;
+    L->langevin_steps = 0;
     TL_CK(tl::launch_set_background(L->model, L->d_sc, L->ex.a0, 0.0, L->stream));
     rc = measure(L, expanding);
     if (rc) return rc;

@@ -1,0 +1,165 @@
+// Langevin evolution of a scalar phi^4 field (the paper's interface example,
+// Sec. 2, Eq. 1): Euler-Maruyama steps
+//     phi <- phi + dt (Lap phi - m^2 phi - (lambda/2) phi^3) + noise sqrt(dt) xi,
+// with xi a unit Gaussian per site and step (the paper's field-valued random
+// number generator rescaled by 1/sqrt(dt)), drawn from Philox-2x64-10 of the
+// counter (site index, 2^63 + step) under key seed and turned into a Gaussian
+// by Box-Muller on the two output words.
+//
+// One kernel per step, marching z-planes like the fused pass: phi at z-1, z,
+// z+1 in registers, the y-neighbour rows and edge sites through L1/L2; HBM
+// sees one read and one write of phi per site.  The field ping-pongs between
+// the lattice's two phi_0 buffers; momenta are not used.
+#include <math.h>
+#include <stdint.h>
+
+#include "tl_internal.cuh"
+#include "tl_lattice.cuh"
+
+namespace {
+
+// Philox-2x64 with 10 rounds (Salmon et al., SC'11), as in the initial-state draw.
+__device__ __forceinline__ void philox2x64_10(uint64_t c0, uint64_t c1, uint64_t key, uint64_t &o0, uint64_t &o1)
+{
+    const uint64_t M = 0xD2B74407B1CE6E93ULL;
+    const uint64_t Wk = 0x9E3779B97F4A7C15ULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t hi = __umul64hi(M, c0);
+        const uint64_t lo = M * c0;
+        c0 = hi ^ key ^ c1;
+        c1 = lo;
+        key += Wk;
+    }
+    o0 = c0;
+    o1 = c1;
+}
+
+template <typename T>
+__device__ __forceinline__ T gauss(uint64_t site, uint64_t ctr1, uint64_t seed);
+
+template <>
+__device__ __forceinline__ double gauss<double>(uint64_t site, uint64_t ctr1, uint64_t seed)
+{
+    uint64_t w0, w1;
+    philox2x64_10(site, ctr1, seed, w0, w1);
+    const double two53 = 9007199254740992.0;
+    const double u1 = ((double)(w0 >> 11) + 1.0) / two53;
+    const double u2 = (double)(w1 >> 11) / two53;
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+template <>
+__device__ __forceinline__ float gauss<float>(uint64_t site, uint64_t ctr1, uint64_t seed)
+{
+    uint64_t w0, w1;
+    philox2x64_10(site, ctr1, seed, w0, w1);
+    // same uniforms, Box-Muller in FP32 (the field is stored in FP32)
+    const float u1 = (float)(((double)(w0 >> 11) + 1.0) * (1.0 / 9007199254740992.0));
+    const float u2 = (float)((double)(w1 >> 11) * (1.0 / 9007199254740992.0));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    return sqrtf(-2.0f * logf(u1)) * c;
+}
+
+template <typename T>
+struct V16;
+template <>
+struct V16<float> {
+    static constexpr int W = 4;
+};
+template <>
+struct V16<double> {
+    static constexpr int W = 2;
+};
+
+template <typename T>
+__device__ __forceinline__ void ld(const T *p, T (&o)[V16<T>::W])
+{
+#pragma unroll
+    for (int j = 0; j < V16<T>::W; ++j) o[j] = __ldg(p + j);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) langevin_pass(const T *__restrict__ in, T *__restrict__ out, int N, int txt,
+                                                     int ty, int zc, T inv_dx2, T dt, T m2, T half_lam, T amp,
+                                                     uint64_t seed, uint64_t ctr1)
+{
+    constexpr int W = V16<T>::W;
+    const int tx = threadIdx.x % txt, tyi = threadIdx.x / txt;
+    const int x0 = (blockIdx.x * txt + tx) * W;
+    const int y = blockIdx.y * ty + tyi;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(z0 + zc, N);
+    if (!(tyi < ty && x0 < N && y < N)) return;
+    const size_t NN = (size_t)N * N;
+    const size_t row = (size_t)y * N, rowm = (size_t)(y == 0 ? N - 1 : y - 1) * N,
+                 rowp = (size_t)(y + 1 == N ? 0 : y + 1) * N;
+    const int xl = x0 == 0 ? N - 1 : x0 - 1, xr = x0 + W == N ? 0 : x0 + W;
+    T zm[W], cu[W], zp[W];
+    ld(in + (size_t)(z0 == 0 ? N - 1 : z0 - 1) * NN + row + x0, zm);
+    ld(in + (size_t)z0 * NN + row + x0, cu);
+    for (int z = z0; z < z1; ++z) {
+        const size_t pz = (size_t)z * NN;
+        T ym[W], yp[W];
+        ld(in + (size_t)(z + 1 == N ? 0 : z + 1) * NN + row + x0, zp);
+        ld(in + pz + rowm + x0, ym);
+        ld(in + pz + rowp + x0, yp);
+        const T a = __ldg(in + pz + row + xl), b = __ldg(in + pz + row + xr);
+        T o[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const T c = cu[j];
+            const T left = j == 0 ? a : cu[j - 1];
+            const T right = j == W - 1 ? b : cu[j + 1];
+            const T lap = (((left - c) + (right - c)) + ((ym[j] - c) + (yp[j] - c))) + ((zm[j] - c) + (zp[j] - c));
+            const T drift = lap * inv_dx2 - m2 * c - half_lam * c * c * c;
+            const T xi = gauss<T>(pz + row + x0 + j, ctr1, seed);
+            o[j] = (c + dt * drift) + amp * xi;
+        }
+#pragma unroll
+        for (int j = 0; j < W; ++j) out[pz + row + x0 + j] = o[j];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            zm[j] = cu[j];
+            cu[j] = zp[j];
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int tl_langevin_step(tl_lattice *L, int n, double dt, const tl_langevin_params *p, uint64_t seed)
+{
+    tl::set_error(TL_OK, "", "");
+    if (!L || !p) return tl::fail(TL_EINVAL, "NULL argument");
+    if (n < 0 || !(dt > 0.0) || !isfinite(dt)) return tl::fail(TL_EINVAL, "n >= 0 and a positive finite dt needed");
+    if (!isfinite(p->lambda) || !isfinite(p->m2) || !isfinite(p->noise)) return tl::fail(TL_EINVAL, "non-finite parameter");
+    if (!(L->state_mask & 1u)) return tl::fail(TL_ESTATE, "phi_0 has not been set");
+    if (L->batch_refs > 0) return tl::fail(TL_ESTATE, "lattice is part of a batch");
+    tl::PassTuning t{tl::kVariantLdg, 8, 0, 0, 0, 2};
+    const tl::PassGeom g = tl::pass_geometry(L->N, (int)L->esz, L->sm_count, 1, t);
+    const double inv_dx2 = 1.0 / (L->dx * L->dx);
+    const double amp = p->noise * sqrt(dt);
+    for (int s = 0; s < n; ++s) {
+        void *in = L->buf[L->cur][0][0];
+        void *out = L->buf[L->cur ^ 1][0][0];
+        const uint64_t ctr1 = (1ull << 63) + (uint64_t)(L->langevin_steps + s);
+        if (L->dtype == TL_F32)
+            langevin_pass<float><<<g.grid, 256, 0, L->stream>>>(
+                static_cast<const float *>(in), static_cast<float *>(out), L->N, g.txt, g.ty, g.zc, (float)inv_dx2,
+                (float)dt, (float)p->m2, (float)(0.5 * p->lambda), (float)amp, seed, ctr1);
+        else
+            langevin_pass<double><<<g.grid, 256, 0, L->stream>>>(
+                static_cast<const double *>(in), static_cast<double *>(out), L->N, g.txt, g.ty, g.zc, inv_dx2, dt,
+                p->m2, 0.5 * p->lambda, amp, seed, ctr1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return tl::fail(TL_ECUDA, "langevin_pass: %s", cudaGetErrorString(e));
+        // phi_0 ping-pongs; the momenta stay where they are
+        L->buf[L->cur][0][0] = out;
+        L->buf[L->cur ^ 1][0][0] = in;
+    }
+    L->langevin_steps += n;
+    L->energies_valid = false;
+    return TL_OK;
+}

@@ -31,6 +31,7 @@ struct tl_lattice {
     tl::Model model{};
     int sm_count = 0;
     int64_t step = 0;
+    int64_t langevin_steps = 0;  // Langevin steps since the last state reset (noise counters)
     bool energies_valid = false;
     int batch_refs = 0;  // tl_batch objects that hold this lattice
 };

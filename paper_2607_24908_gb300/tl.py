@@ -48,6 +48,10 @@ class tl_init_spec(ctypes.Structure):
                 ("fluct_pi", ctypes.c_int)]
 
 
+class tl_langevin_params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("m2", ctypes.c_double), ("noise", ctypes.c_double)]
+
+
 class tl_energies_t(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("time", ctypes.c_double), ("a", ctypes.c_double),
                 ("b", ctypes.c_double), ("K", ctypes.c_double * MAX_FIELDS),
@@ -89,6 +93,8 @@ _SIGS = {
     "tl_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
     "tl_batch_destroy": (None, [ctypes.c_void_p]),
     "tl_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "tl_langevin_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                        ctypes.POINTER(tl_langevin_params), ctypes.c_uint64]),
     "tl_last_error": (ctypes.c_char_p, []),
 }
 
@@ -218,6 +224,11 @@ def tl_energies_noalloc(N: int, kIR: float, n_fields: int, dtype: int, lam: floa
                                      ctypes.byref(expansion) if expansion is not None else None, a, ph, pp,
                                      ctypes.c_void_p(cuda_stream), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def tl_langevin_step(h, n: int, dt: float, lam: float, m2: float, noise: float, seed: int):
+    p = tl_langevin_params(lam, m2, noise)
+    _check(lib().tl_langevin_step(h, n, dt, ctypes.byref(p), ctypes.c_uint64(seed)))
 
 
 def tl_batch_create(handles: Sequence, cuda_stream: int = 0) -> ctypes.c_void_p:
@@ -353,6 +364,10 @@ class Lattice:
 
     def device_ptr(self, field: int, which: int) -> int:
         return tl_state_device_ptr(self.h, field, which)
+
+    def langevin(self, n: int, dt: float, lam: float, m2: float = 0.0, noise: float = 1.0, seed: int = 0):
+        """n Euler-Maruyama Langevin steps of phi_0 (see tl_langevin_step)."""
+        tl_langevin_step(self.h, n, dt, lam, m2, noise, seed)
 
     def autotune(self) -> float:
         """Pick the fastest launch geometry for this lattice shape; returns ms per pass."""
