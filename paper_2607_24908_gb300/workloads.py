@@ -47,6 +47,24 @@ def sample_sites(N: int, count: int, seed: int) -> np.ndarray:
     return np.stack([z, y, x], axis=1)
 
 
+def random_su2_links(N: int, seed: int, amp: float) -> np.ndarray:
+    """Random SU(2) links as unit quaternions, component-major [3, 4, N, N, N]
+    (direction, component, z, y, x): q = (1, amp xi1, amp xi2, amp xi3) with xi
+    standard normal, divided by its norm."""
+    rng = np.random.default_rng(seed)
+    q = np.empty((3, 4, N, N, N))
+    q[:, 0] = 1.0
+    q[:, 1:] = amp * rng.standard_normal((3, 3, N, N, N))
+    return q / np.sqrt(np.sum(q * q, axis=1, keepdims=True))
+
+
+def random_su2_gauge(N: int, seed: int) -> np.ndarray:
+    """A random SU(2) element per site as a unit quaternion [4, N, N, N]."""
+    rng = np.random.default_rng(seed)
+    q = rng.standard_normal((4, N, N, N))
+    return q / np.sqrt(np.sum(q * q, axis=0, keepdims=True))
+
+
 @dataclass(frozen=True)
 class Workload:
     """One named synthetic workload (sizes and model parameters only)."""
