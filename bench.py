@@ -535,6 +535,41 @@ def run_langevin(args):
     return 0
 
 
+# ---------------------------------------------------------------------------------
+# SU(2) Yang-Mills leapfrog (the paper's benchmark workload), ns per site per step
+# ---------------------------------------------------------------------------------
+
+def run_su2(args):
+    import torch
+    from paper_2607_24908_gb300 import tl as T
+    torch.cuda.set_device(0)
+    N = args.N or 576
+    peak, peak_kind = peaks()
+    out = {}
+    for dtype in ("f64", "f32"):
+        stream = torch.cuda.Stream()
+        lat = T.SU2(N, dtype, stream=stream.cuda_stream)
+        lat.init_random(7, 0.8)
+        lat.step(args.warmup, 0.02)
+        m0 = lat.measure()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(args.steps, 0.02)
+        e1.record(stream)
+        m1 = lat.measure()
+        ms = e0.elapsed_time(e1) / args.steps
+        esz = 4 if dtype == "f32" else 8
+        alg = 42 * esz * N ** 3  # read 12 link + 9 field values, write 9 + 12, per site
+        out[dtype] = {"ms_per_step": ms, "ns_per_site_step": ms * 1e6 / N ** 3,
+                      "achieved_gbs": alg / (ms / 1e3) / 1e9, "frac_of_hbm": alg / (ms / 1e3) / 1e9 / peak,
+                      "energy_drift_rel": abs(m1[0] + m1[1] - m0[0] - m0[1]) / (m0[0] + m0[1]),
+                      "gauss_max": m1[2]}
+        lat.close()
+    print(json.dumps({"mode": "su2", "N": N, "steps": args.steps, "dt": 0.02, "peak_gbs": peak,
+                      "peak_source": peak_kind, "results": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -544,7 +579,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--N", type=int, default=0, help="lattice size (default: the workload's 1024; for profiling)")
-    ap.add_argument("--mode", default="step", choices=["step", "ensemble", "serve", "expanding256", "langevin"],
+    ap.add_argument("--mode", default="step", choices=["step", "ensemble", "serve", "expanding256", "langevin", "su2"],
                     help="step: the 1024^3 fused step (default); ensemble: batched small lattices vs a plain loop; "
                          "serve: continuous batching of Poisson-arriving jobs vs a sequential loop")
     ap.add_argument("--jobs", type=int, default=0, help="jobs for --mode ensemble (96) / serve (24)")
@@ -558,6 +593,8 @@ def main():
     if args.mode == "ensemble":
         args.jobs = args.jobs or 96
         return run_ensemble(args)
+    if args.mode == "su2":
+        return run_su2(args)
     if args.mode == "langevin":
         return run_langevin(args)
     if args.mode == "expanding256":

@@ -215,6 +215,38 @@ typedef struct {
  * only.  Errors: TL_EINVAL, TL_ESTATE (phi_0 not set, or in a batch), TL_ECUDA. */
 int tl_langevin_step(tl_lattice *lat, int n, double dt, const tl_langevin_params *p, uint64_t seed);
 
+/* ---- SU(2) Yang-Mills in temporal gauge (Sec. 4 benchmark workload) ----
+ * Links U_i(x) in SU(2) as unit quaternions (u0, u1, u2, u3) meaning
+ * u0 + i (u1 s1 + u2 s2 + u3 s3); electric fields E_i(x) = i e_i.s as 3-vectors.
+ * Host/device layout, component-major: U[i][c][z][y][x] (3 x 4 arrays of N^3)
+ * and E[i][c][z][y][x] (3 x 3 arrays), elements of dtype.  Lattice units
+ * (dx = 1).  One step is the paper's leapfrog: kick
+ * e_i(x) <- e_i(x) - 2 dt sum_{j != i} Im[U_i(x) S_ij(x)] with the staples
+ * S_ij(x) = U_j(x+i) U_i(x+j)^+ U_j(x)^+ + U_j(x+i-j)^+ U_i(x-j)^+ U_j(x-j)
+ * (the paper's E+ = E - dt sum_j (P_ij - P_ij^+)), then drift
+ * U_i(x) <- exp(dt E_i(x)) U_i(x) (closed-form exponential map), fused in one
+ * pass per step.  FP32 links are renormalised to unit length after each drift. */
+
+typedef struct tl_su2 tl_su2; /* opaque */
+
+/* Allocate the links (two copies), the fields and measurement scratch:
+ * 33 N^3 elements.  4 <= N <= 1290.  Errors: TL_EINVAL, TL_ENOMEM, TL_ECUDA. */
+int tl_su2_create(tl_su2 **out, int N, tl_dtype dtype, void *cuda_stream);
+void tl_su2_destroy(tl_su2 *lat);
+/* Copy the whole state from / to host memory (layout above); synchronises. */
+int tl_su2_set_state(tl_su2 *lat, const void *U, const void *E);
+int tl_su2_get_state(tl_su2 *lat, void *U, void *E);
+/* Random links q/|q|, q = (1, amp g1, amp g2, amp g3), g standard normal from
+ * Philox-2x64-10 (counter (3 site + i, 2^62 + h), key seed, Box-Muller), and
+ * E = 0 (so Gauss's law holds exactly).  Enqueues only. */
+int tl_su2_init_random(tl_su2 *lat, uint64_t seed, double amp);
+/* n leapfrog steps of size dt (kick then drift).  Enqueues only. */
+int tl_su2_step(tl_su2 *lat, int n, double dt);
+/* out4 = {<sum_i |e_i|^2/2>, <sum_{i<j} 2 (1 - Re P_ij)>, max_x |G(x)|,
+ * sqrt(<|G|^2>)} with G(x) = sum_i [E_i(x) - U_i(x-i)^+ E_i(x-i) U_i(x-i)]
+ * (Gauss's law), averages over sites; fixed-order FP64 sums.  Synchronises. */
+int tl_su2_measure(tl_su2 *lat, double *out4);
+
 /* ---- batched ensembles and launch tuning (beyond the paper's single
  * lattice: many independent small lattices advanced together) ---- */
 

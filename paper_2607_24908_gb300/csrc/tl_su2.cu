@@ -1,0 +1,407 @@
+// Classical SU(2) Yang-Mills in temporal gauge: the paper's benchmark
+// workload (Sec. 4), each step a kick of the electric fields by the plaquette
+// staples and a drift of the links by the closed-form SU(2) exponential map.
+//
+// Links are unit quaternions U = u0 + i u.s, electric fields su(2) vectors
+// E = i e.s, both stored component-major (U: [direction][component][site],
+// 12 arrays; E: 9 arrays) so that consecutive threads read consecutive sites.
+// One fused pass per step: e_i(x) <- e_i(x) - 2 dt sum_{j != i} Im[U_i S_ij]
+// with the old links, then U_i(x) <- exp(dt E_i(x)) U_i(x) written to the
+// other link buffer (ping-pong), so the neighbours' staples always see the old
+// links.  HBM per site and step: read 12 link + 9 field values, write 9 + 12.
+// A separate measurement kernel reduces the electric and plaquette energies
+// and the Gauss-law violation in a fixed order (per-CTA slots, one summing CTA).
+#include <math.h>
+#include <stdint.h>
+
+#include <new>
+
+#include "tl_internal.cuh"
+#include "tl_lattice.cuh"
+
+namespace {
+
+template <typename T>
+struct Q {
+    T w, x, y, z;
+};
+
+template <typename T>
+__device__ __forceinline__ Q<T> qmul(const Q<T> &a, const Q<T> &b)
+{
+    // (a0 + i a.s)(b0 + i b.s) = a0 b0 - a.b + i (a0 b + b0 a - a x b).s
+    Q<T> r;
+    r.w = a.w * b.w - (a.x * b.x + a.y * b.y + a.z * b.z);
+    r.x = a.w * b.x + b.w * a.x - (a.y * b.z - a.z * b.y);
+    r.y = a.w * b.y + b.w * a.y - (a.z * b.x - a.x * b.z);
+    r.z = a.w * b.z + b.w * a.z - (a.x * b.y - a.y * b.x);
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ Q<T> qadj(const Q<T> &a)
+{
+    return Q<T>{a.w, -a.x, -a.y, -a.z};
+}
+template <typename T>
+__device__ __forceinline__ Q<T> qadd(const Q<T> &a, const Q<T> &b)
+{
+    return Q<T>{a.w + b.w, a.x + b.x, a.y + b.y, a.z + b.z};
+}
+
+__device__ __forceinline__ size_t sidx(int N, int x, int y, int z)
+{
+    x = x < 0 ? x + N : (x >= N ? x - N : x);
+    y = y < 0 ? y + N : (y >= N ? y - N : y);
+    z = z < 0 ? z + N : (z >= N ? z - N : z);
+    return ((size_t)z * N + y) * N + x;
+}
+
+template <typename T>
+__device__ __forceinline__ Q<T> ldU(const T *U, size_t n3, int i, size_t s)
+{
+    const T *b = U + (size_t)(4 * i) * n3 + s;
+    return Q<T>{__ldg(b), __ldg(b + n3), __ldg(b + 2 * n3), __ldg(b + 3 * n3)};
+}
+
+template <typename T>
+__device__ __forceinline__ void sincos_t(T a, T *s, T *c);
+template <>
+__device__ __forceinline__ void sincos_t<float>(float a, float *s, float *c) { sincosf(a, s, c); }
+template <>
+__device__ __forceinline__ void sincos_t<double>(double a, double *s, double *c) { sincos(a, s, c); }
+
+// One leapfrog step for the site owned by this thread (all three links).
+template <typename T>
+__global__ void __launch_bounds__(256) su2_pass(const T *__restrict__ U, T *__restrict__ Uout, T *__restrict__ E,
+                                                int N, T dt)
+{
+    const size_t n3 = (size_t)N * N * N;
+    const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (s >= n3) return;
+    const int x = (int)(s % N), y = (int)((s / N) % N), z = (int)(s / ((size_t)N * N));
+    const int d[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    Q<T> Ux[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Ux[i] = ldU(U, n3, i, s);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Q<T> S{0, 0, 0, 0};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j == i) continue;
+            const size_t xpi = sidx(N, x + d[i][0], y + d[i][1], z + d[i][2]);
+            const size_t xpj = sidx(N, x + d[j][0], y + d[j][1], z + d[j][2]);
+            const size_t xmj = sidx(N, x - d[j][0], y - d[j][1], z - d[j][2]);
+            const size_t xpimj = sidx(N, x + d[i][0] - d[j][0], y + d[i][1] - d[j][1], z + d[i][2] - d[j][2]);
+            // forward staple U_j(x+i) U_i(x+j)^+ U_j(x)^+
+            const Q<T> f = qmul(qmul(ldU(U, n3, j, xpi), qadj(ldU(U, n3, i, xpj))), qadj(Ux[j]));
+            // backward staple U_j(x+i-j)^+ U_i(x-j)^+ U_j(x-j)
+            const Q<T> Ujm = ldU(U, n3, j, xmj);
+            const Q<T> b = qmul(qmul(qadj(ldU(U, n3, j, xpimj)), qadj(ldU(U, n3, i, xmj))), Ujm);
+            S = qadd(S, qadd(f, b));
+        }
+        const Q<T> P = qmul(Ux[i], S);
+        T *e = E + (size_t)(3 * i) * n3 + s;
+        const T e1 = e[0] - (T)2 * dt * P.x;
+        const T e2 = e[n3] - (T)2 * dt * P.y;
+        const T e3 = e[2 * n3] - (T)2 * dt * P.z;
+        e[0] = e1;
+        e[n3] = e2;
+        e[2 * n3] = e3;
+        // drift: exp(i dt e.s) = cos(dt|e|) + i sin(dt|e|) e/|e|
+        const T nrm = sqrt(e1 * e1 + e2 * e2 + e3 * e3);
+        T sn, cs;
+        sincos_t<T>(dt * nrm, &sn, &cs);
+        const T f = nrm > (T)0 ? sn / nrm : dt;
+        Q<T> u = qmul(Q<T>{cs, f * e1, f * e2, f * e3}, Ux[i]);
+        if (sizeof(T) == 4) {  // FP32 storage: keep the link on the unit sphere
+            const T r = rsqrt(u.w * u.w + u.x * u.x + u.y * u.y + u.z * u.z);
+            u = Q<T>{u.w * r, u.x * r, u.y * r, u.z * r};
+        }
+        T *o = Uout + (size_t)(4 * i) * n3 + s;
+        o[0] = u.w;
+        o[n3] = u.x;
+        o[2 * n3] = u.y;
+        o[3 * n3] = u.z;
+    }
+}
+
+// Per-CTA partial sums of |e|^2/2, 2(1 - Re P_ij) and |G|^2, and the CTA's
+// max |G|, into slots[4 * cta + q].
+template <typename T>
+__global__ void __launch_bounds__(256) su2_measure(const T *__restrict__ U, const T *__restrict__ E, int N,
+                                                   double *slots)
+{
+    const size_t n3 = (size_t)N * N * N;
+    double el = 0.0, mag = 0.0, g2 = 0.0, gmax = 0.0;
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n3; s += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(s % N), y = (int)((s / N) % N), z = (int)(s / ((size_t)N * N));
+        const int d[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        double G[3] = {0, 0, 0};
+        for (int i = 0; i < 3; ++i) {
+            const T *e = E + (size_t)(3 * i) * n3;
+            const double a = e[s], b = e[s + n3], c = e[s + 2 * n3];
+            el += 0.5 * (a * a + b * b + c * c);
+            // Gauss: E_i(x) - U_i(x-i)^+ E_i(x-i) U_i(x-i)
+            const size_t xm = sidx(N, x - d[i][0], y - d[i][1], z - d[i][2]);
+            const Q<double> Um{(double)U[(4 * i) * n3 + xm], (double)U[(4 * i + 1) * n3 + xm],
+                               (double)U[(4 * i + 2) * n3 + xm], (double)U[(4 * i + 3) * n3 + xm]};
+            const Q<double> Em{0.0, (double)e[xm], (double)e[xm + n3], (double)e[xm + 2 * n3]};
+            const Q<double> t = qmul(qmul(qadj(Um), Em), Um);
+            G[0] += a - t.x;
+            G[1] += b - t.y;
+            G[2] += c - t.z;
+            for (int j = i + 1; j < 3; ++j) {
+                const size_t xpi = sidx(N, x + d[i][0], y + d[i][1], z + d[i][2]);
+                const size_t xpj = sidx(N, x + d[j][0], y + d[j][1], z + d[j][2]);
+                auto ld = [&](int k, size_t site) {
+                    return Q<double>{(double)U[(4 * k) * n3 + site], (double)U[(4 * k + 1) * n3 + site],
+                                     (double)U[(4 * k + 2) * n3 + site], (double)U[(4 * k + 3) * n3 + site]};
+                };
+                const Q<double> P = qmul(qmul(qmul(ld(i, s), ld(j, xpi)), qadj(ld(i, xpj))), qadj(ld(j, s)));
+                mag += 2.0 * (1.0 - P.w);
+            }
+        }
+        const double gg = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+        g2 += gg;
+        gmax = fmax(gmax, sqrt(gg));
+    }
+    __shared__ double red[8][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double v[4] = {el, mag, g2, gmax};
+    for (int q = 0; q < 4; ++q) {
+        double w = v[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double u = __shfl_xor_sync(0xffffffffu, w, o);
+            w = q == 3 ? fmax(w, u) : w + u;
+        }
+        if (lane == 0) red[warp][q] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double w = red[0][threadIdx.x];
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+            w = threadIdx.x == 3 ? fmax(w, red[k][threadIdx.x]) : w + red[k][threadIdx.x];
+        slots[4 * blockIdx.x + threadIdx.x] = w;
+    }
+}
+
+__global__ void su2_sum_slots(const double *slots, int nblocks, double inv_n3, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double el = 0, mag = 0, g2 = 0, gmax = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        el += slots[4 * b];
+        mag += slots[4 * b + 1];
+        g2 += slots[4 * b + 2];
+        gmax = fmax(gmax, slots[4 * b + 3]);
+    }
+    out[0] = el * inv_n3;
+    out[1] = mag * inv_n3;
+    out[2] = gmax;
+    out[3] = sqrt(g2 * inv_n3);
+}
+
+// Philox-2x64-10 (Salmon et al., SC'11), for random initial links.
+__device__ __forceinline__ void philox(uint64_t c0, uint64_t c1, uint64_t key, uint64_t &o0, uint64_t &o1)
+{
+    const uint64_t M = 0xD2B74407B1CE6E93ULL, Wk = 0x9E3779B97F4A7C15ULL;
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t hi = __umul64hi(M, c0), lo = M * c0;
+        c0 = hi ^ key ^ c1;
+        c1 = lo;
+        key += Wk;
+    }
+    o0 = c0;
+    o1 = c1;
+}
+
+template <typename T>
+__global__ void su2_init(T *U, T *E, int N, uint64_t seed, double amp)
+{
+    const size_t n3 = (size_t)N * N * N;
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n3; s += (size_t)gridDim.x * blockDim.x) {
+        for (int i = 0; i < 3; ++i) {
+            double g[4];
+            for (int h = 0; h < 2; ++h) {
+                uint64_t w0, w1;
+                philox(3 * s + i, (1ull << 62) + h, seed, w0, w1);
+                const double u1 = ((double)(w0 >> 11) + 1.0) / 9007199254740992.0;
+                const double u2 = (double)(w1 >> 11) / 9007199254740992.0;
+                const double r = sqrt(-2.0 * log(u1));
+                double sn, cs;
+                sincospi(2.0 * u2, &sn, &cs);
+                g[2 * h] = r * cs;
+                g[2 * h + 1] = r * sn;
+            }
+            const double q1 = amp * g[0], q2 = amp * g[1], q3 = amp * g[2];
+            const double inv = 1.0 / sqrt(1.0 + q1 * q1 + q2 * q2 + q3 * q3);
+            U[(4 * i) * n3 + s] = (T)inv;
+            U[(4 * i + 1) * n3 + s] = (T)(q1 * inv);
+            U[(4 * i + 2) * n3 + s] = (T)(q2 * inv);
+            U[(4 * i + 3) * n3 + s] = (T)(q3 * inv);
+            for (int c = 0; c < 3; ++c) E[(3 * i + c) * n3 + s] = (T)0;
+        }
+    }
+}
+
+}  // namespace
+
+struct tl_su2 {
+    int N = 0;
+    tl_dtype dtype = TL_F64;
+    size_t esz = 8;
+    cudaStream_t stream = nullptr;
+    void *U[2] = {nullptr, nullptr};
+    void *E = nullptr;
+    int cur = 0;
+    double *slots = nullptr;
+    double *out = nullptr;
+    int mblocks = 0;
+    int sm_count = 0;
+    bool has_state = false;
+};
+
+#define SU_CK(call)                                                                                         \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess)                                                                              \
+            return tl::fail(e_ == cudaErrorMemoryAllocation ? TL_ENOMEM : TL_ECUDA, "%s: %s", #call,        \
+                            cudaGetErrorString(e_));                                                        \
+    } while (0)
+
+extern "C" {
+
+void tl_su2_destroy(tl_su2 *Y)
+{
+    if (!Y) return;
+    cudaStreamSynchronize(Y->stream);
+    cudaFree(Y->U[0]);
+    cudaFree(Y->U[1]);
+    cudaFree(Y->E);
+    cudaFree(Y->slots);
+    cudaFree(Y->out);
+    delete Y;
+}
+
+int tl_su2_create(tl_su2 **out, int N, tl_dtype dtype, void *cuda_stream)
+{
+    tl::set_error(TL_OK, "", "");
+    if (!out) return tl::fail(TL_EINVAL, "NULL out");
+    *out = nullptr;
+    if (N < 4 || N > 1290) return tl::fail(TL_EINVAL, "N must be in [4, 1290]");
+    if (dtype != TL_F32 && dtype != TL_F64) return tl::fail(TL_EINVAL, "unknown dtype");
+    tl_su2 *Y = new (std::nothrow) tl_su2();
+    if (!Y) return tl::fail(TL_ENOMEM, "host allocation failed");
+    Y->N = N;
+    Y->dtype = dtype;
+    Y->esz = dtype == TL_F32 ? 4 : 8;
+    Y->stream = static_cast<cudaStream_t>(cuda_stream);
+    const size_t n3 = (size_t)N * N * N;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete Y;
+        return tl::fail(TL_ECUDA, "cudaMemGetInfo failed (no CUDA device?)");
+    }
+    if (33 * n3 * Y->esz + (64u << 20) > free_b) {
+        delete Y;
+        return tl::fail(TL_ENOMEM, "SU(2) lattice needs %zu bytes", 33 * n3 * Y->esz);
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&Y->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    Y->mblocks = 4 * (Y->sm_count > 0 ? Y->sm_count : 152);
+    cudaError_t e = cudaMalloc(&Y->U[0], 12 * n3 * Y->esz);
+    if (e == cudaSuccess) e = cudaMalloc(&Y->U[1], 12 * n3 * Y->esz);
+    if (e == cudaSuccess) e = cudaMalloc(&Y->E, 9 * n3 * Y->esz);
+    if (e == cudaSuccess) e = cudaMalloc(&Y->slots, sizeof(double) * 4 * Y->mblocks);
+    if (e == cudaSuccess) e = cudaMalloc(&Y->out, sizeof(double) * 4);
+    if (e != cudaSuccess) {
+        tl_su2_destroy(Y);
+        return tl::fail(TL_ENOMEM, "SU(2) allocation: %s", cudaGetErrorString(e));
+    }
+    *out = Y;
+    return TL_OK;
+}
+
+int tl_su2_set_state(tl_su2 *Y, const void *U, const void *E)
+{
+    tl::set_error(TL_OK, "", "");
+    if (!Y || !U || !E) return tl::fail(TL_EINVAL, "NULL argument");
+    const size_t n3 = (size_t)Y->N * Y->N * Y->N;
+    SU_CK(cudaMemcpyAsync(Y->U[Y->cur], U, 12 * n3 * Y->esz, cudaMemcpyHostToDevice, Y->stream));
+    SU_CK(cudaMemcpyAsync(Y->E, E, 9 * n3 * Y->esz, cudaMemcpyHostToDevice, Y->stream));
+    SU_CK(cudaStreamSynchronize(Y->stream));
+    Y->has_state = true;
+    return TL_OK;
+}
+
+int tl_su2_get_state(tl_su2 *Y, void *U, void *E)
+{
+    tl::set_error(TL_OK, "", "");
+    if (!Y || (!U && !E)) return tl::fail(TL_EINVAL, "NULL argument");
+    const size_t n3 = (size_t)Y->N * Y->N * Y->N;
+    if (U) SU_CK(cudaMemcpyAsync(U, Y->U[Y->cur], 12 * n3 * Y->esz, cudaMemcpyDeviceToHost, Y->stream));
+    if (E) SU_CK(cudaMemcpyAsync(E, Y->E, 9 * n3 * Y->esz, cudaMemcpyDeviceToHost, Y->stream));
+    SU_CK(cudaStreamSynchronize(Y->stream));
+    return TL_OK;
+}
+
+int tl_su2_init_random(tl_su2 *Y, uint64_t seed, double amp)
+{
+    tl::set_error(TL_OK, "", "");
+    if (!Y || !(amp >= 0.0)) return tl::fail(TL_EINVAL, "bad argument");
+    if (Y->dtype == TL_F32)
+        su2_init<float><<<Y->mblocks, 256, 0, Y->stream>>>(static_cast<float *>(Y->U[Y->cur]),
+                                                           static_cast<float *>(Y->E), Y->N, seed, amp);
+    else
+        su2_init<double><<<Y->mblocks, 256, 0, Y->stream>>>(static_cast<double *>(Y->U[Y->cur]),
+                                                            static_cast<double *>(Y->E), Y->N, seed, amp);
+    SU_CK(cudaGetLastError());
+    Y->has_state = true;
+    return TL_OK;
+}
+
+int tl_su2_step(tl_su2 *Y, int n, double dt)
+{
+    tl::set_error(TL_OK, "", "");
+    if (!Y) return tl::fail(TL_EINVAL, "NULL lattice");
+    if (n < 0 || !isfinite(dt) || dt == 0.0) return tl::fail(TL_EINVAL, "n >= 0 and a finite nonzero dt needed");
+    if (!Y->has_state) return tl::fail(TL_ESTATE, "no state");
+    const size_t n3 = (size_t)Y->N * Y->N * Y->N;
+    const unsigned grid = (unsigned)((n3 + 255) / 256);
+    for (int k = 0; k < n; ++k) {
+        if (Y->dtype == TL_F32)
+            su2_pass<float><<<grid, 256, 0, Y->stream>>>(static_cast<const float *>(Y->U[Y->cur]),
+                                                         static_cast<float *>(Y->U[Y->cur ^ 1]),
+                                                         static_cast<float *>(Y->E), Y->N, (float)dt);
+        else
+            su2_pass<double><<<grid, 256, 0, Y->stream>>>(static_cast<const double *>(Y->U[Y->cur]),
+                                                          static_cast<double *>(Y->U[Y->cur ^ 1]),
+                                                          static_cast<double *>(Y->E), Y->N, dt);
+        SU_CK(cudaGetLastError());
+        Y->cur ^= 1;
+    }
+    return TL_OK;
+}
+
+int tl_su2_measure(tl_su2 *Y, double *out4)
+{
+    tl::set_error(TL_OK, "", "");
+    if (!Y || !out4) return tl::fail(TL_EINVAL, "NULL argument");
+    const size_t n3 = (size_t)Y->N * Y->N * Y->N;
+    if (Y->dtype == TL_F32)
+        su2_measure<float><<<Y->mblocks, 256, 0, Y->stream>>>(static_cast<const float *>(Y->U[Y->cur]),
+                                                              static_cast<const float *>(Y->E), Y->N, Y->slots);
+    else
+        su2_measure<double><<<Y->mblocks, 256, 0, Y->stream>>>(static_cast<const double *>(Y->U[Y->cur]),
+                                                               static_cast<const double *>(Y->E), Y->N, Y->slots);
+    SU_CK(cudaGetLastError());
+    su2_sum_slots<<<1, 32, 0, Y->stream>>>(Y->slots, Y->mblocks, 1.0 / (double)n3, Y->out);
+    SU_CK(cudaGetLastError());
+    SU_CK(cudaMemcpyAsync(out4, Y->out, 4 * sizeof(double), cudaMemcpyDeviceToHost, Y->stream));
+    SU_CK(cudaStreamSynchronize(Y->stream));
+    return TL_OK;
+}
+
+}  // extern "C"

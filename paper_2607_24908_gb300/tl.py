@@ -95,6 +95,13 @@ _SIGS = {
     "tl_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tl_langevin_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                         ctypes.POINTER(tl_langevin_params), ctypes.c_uint64]),
+    "tl_su2_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "tl_su2_destroy": (None, [ctypes.c_void_p]),
+    "tl_su2_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tl_su2_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tl_su2_init_random": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double]),
+    "tl_su2_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    "tl_su2_measure": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tl_last_error": (ctypes.c_char_p, []),
 }
 
@@ -229,6 +236,58 @@ def tl_energies_noalloc(N: int, kIR: float, n_fields: int, dtype: int, lam: floa
 def tl_langevin_step(h, n: int, dt: float, lam: float, m2: float, noise: float, seed: int):
     p = tl_langevin_params(lam, m2, noise)
     _check(lib().tl_langevin_step(h, n, dt, ctypes.byref(p), ctypes.c_uint64(seed)))
+
+
+class SU2:
+    """SU(2) Yang-Mills lattice in temporal gauge (see tl_su2_* in tl.h);
+    states as numpy arrays U[3, 4, N, N, N], E[3, 3, N, N, N]."""
+
+    def __init__(self, N: int, dtype: str = "f64", stream: int = 0):
+        self.N, self.dtype = N, dtype
+        self.np_dtype = np.float32 if dtype == "f32" else np.float64
+        self.h = ctypes.c_void_p()
+        _check(lib().tl_su2_create(ctypes.byref(self.h), N, DTYPES[dtype], ctypes.c_void_p(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tl_su2_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_state(self, U: np.ndarray, E: np.ndarray):
+        U = np.ascontiguousarray(U, dtype=self.np_dtype)
+        E = np.ascontiguousarray(E, dtype=self.np_dtype)
+        assert U.shape == (3, 4) + (self.N,) * 3 and E.shape == (3, 3) + (self.N,) * 3
+        _check(lib().tl_su2_set_state(self.h, ctypes.c_void_p(U.ctypes.data), ctypes.c_void_p(E.ctypes.data)))
+
+    def get_state(self):
+        U = np.empty((3, 4) + (self.N,) * 3, self.np_dtype)
+        E = np.empty((3, 3) + (self.N,) * 3, self.np_dtype)
+        _check(lib().tl_su2_get_state(self.h, ctypes.c_void_p(U.ctypes.data), ctypes.c_void_p(E.ctypes.data)))
+        return U, E
+
+    def init_random(self, seed: int, amp: float):
+        _check(lib().tl_su2_init_random(self.h, ctypes.c_uint64(seed), amp))
+
+    def step(self, n: int, dt: float):
+        _check(lib().tl_su2_step(self.h, n, dt))
+
+    def measure(self) -> np.ndarray:
+        """[electric, magnetic (plaquette) energy per site, max |Gauss|, rms |Gauss|]."""
+        out = np.zeros(4)
+        _check(lib().tl_su2_measure(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
 
 
 def tl_batch_create(handles: Sequence, cuda_stream: int = 0) -> ctypes.c_void_p:
