@@ -34,20 +34,28 @@ def test_su2_leapfrog_matches_oracle(dtype, N, tol):
 
 
 def test_su2_gauss_law_and_energy_on_device():
-    N, dt = 16, 0.02
-    with T.SU2(N, "f64") as lat:
-        lat.init_random(seed=5, amp=0.8)
-        U0, E0 = lat.get_state()
-        assert np.max(np.abs(E0)) == 0.0
-        assert np.max(np.abs(np.sum(U0 * U0, axis=1) - 1.0)) < 1e-14
-        m0 = lat.measure()
-        assert m0[2] == 0.0 and m0[0] == 0.0 and m0[1] > 0.1
-        H0 = m0[0] + m0[1]
-        devs = []
-        for _ in range(10):
-            lat.step(20, dt)
-            m = lat.measure()
-            devs.append(abs(m[0] + m[1] - H0) / H0)
-            assert m[2] < 1e-11  # Gauss's law is preserved by both updates
-        assert m[0] > 0.01 * m[1]  # energy moved into the electric field
-        assert max(devs) < 5e-3  # leapfrog energy error is O(dt) with half-step E, bounded
+    """From random links and E = 0, Gauss's law stays at rounding level; the
+    energy measured with the leapfrog's half-step E deviates at O(dt), so the
+    largest deviation over a fixed time halves with dt."""
+    N, T_end = 16, 2.0
+    worst = []
+    for dt in (0.02, 0.01):
+        with T.SU2(N, "f64") as lat:
+            lat.init_random(seed=5, amp=0.8)
+            U0, E0 = lat.get_state()
+            assert np.max(np.abs(E0)) == 0.0
+            assert np.max(np.abs(np.sum(U0 * U0, axis=1) - 1.0)) < 1e-14
+            m0 = lat.measure()
+            assert m0[2] == 0.0 and m0[0] == 0.0 and m0[1] > 0.1
+            H0 = m0[0] + m0[1]
+            devs = []
+            chunk = int(round(0.2 / dt))
+            for _ in range(int(round(T_end / 0.2))):
+                lat.step(chunk, dt)
+                m = lat.measure()
+                devs.append(abs(m[0] + m[1] - H0) / H0)
+                assert m[2] < 1e-11  # Gauss's law is preserved by both updates
+            assert m[0] > 0.01 * m[1]  # energy moved into the electric field
+            worst.append(max(devs))
+    assert worst[1] < 0.02
+    assert 1.6 < worst[0] / worst[1] < 2.5, worst
