@@ -53,11 +53,12 @@ int fail(int code, const char *fmt, ...)
 
 tl::PassTuning tl::default_tuning()
 {
-    tl::PassTuning t{tl::kVariantLdg, 8, 0, 0, 0, 2};
+    tl::PassTuning t{tl::kVariantLdg, 8, 0, 0, 0, 256, 0};
     const char *v = getenv("TL_PASS_VARIANT");
     if (v && strcmp(v, "bulk") == 0) t.variant = tl::kVariantBulk;
     if ((v = getenv("TL_PREFETCH"))) t.prefetch = atoi(v);
-    if ((v = getenv("TL_LDG_MINB"))) t.minblocks = atoi(v);
+    if ((v = getenv("TL_LDG_THREADS"))) t.threads = atoi(v);
+    if ((v = getenv("TL_LDG_TXT"))) t.txt = atoi(v);
     if ((v = getenv("TL_BULK_WARPS"))) t.cwarps = atoi(v);
     if ((v = getenv("TL_BULK_STAGES"))) t.stages = atoi(v);
     if ((v = getenv("TL_PASS_ZC"))) t.zc = atoi(v);

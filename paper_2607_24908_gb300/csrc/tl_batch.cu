@@ -142,6 +142,9 @@ int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_s
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
         if (!lats[i]) return tl::fail(TL_EINVAL, "lattice %d is NULL", i);
+        if (lats[i]->geom.variant != tl::kVariantLdg || lats[i]->geom.threads != 256)
+            return tl::fail(TL_EINVAL, "lattice %d uses a launch shape the batched kernel does not run "
+                                       "(it needs the register-streaming pass with 256-thread CTAs)", i);
         if (lats[i]->dtype != lats[0]->dtype) return tl::fail(TL_EINVAL, "all lattices of a batch share one dtype");
         for (int k = 0; k < i; ++k)
             if (lats[k] == lats[i]) return tl::fail(TL_EINVAL, "lattice %d appears twice", i);
@@ -263,10 +266,10 @@ void load_tune_file()
     if (!path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    int N, nf, dt, sms, var, zc, pf, mb;
+    int N, nf, dt, sms, var, zc, pf, th, txt;
     double ms;
-    while (fscanf(f, "%d %d %d %d %d %d %d %d %lf", &N, &nf, &dt, &sms, &var, &zc, &pf, &mb, &ms) == 9) {
-        tl::PassTuning t{var, 8, 0, zc, pf, mb};
+    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %lf", &N, &nf, &dt, &sms, &var, &zc, &pf, &th, &txt, &ms) == 10) {
+        tl::PassTuning t{var, 8, 0, zc, pf, th, txt};
         g_tune[TuneKey(N, nf, dt, sms)] = TuneVal{t, ms};
     }
     fclose(f);
@@ -278,8 +281,8 @@ void save_tune_entry(const TuneKey &k, const TuneVal &v)
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
-            v.t.variant, v.t.zc, v.t.prefetch, v.t.minblocks, v.ms);
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %.6f\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+            v.t.variant, v.t.zc, v.t.prefetch, v.t.threads, v.t.txt, v.ms);
     fclose(f);
 }
 
@@ -316,11 +319,14 @@ extern "C" int tl_autotune(tl_lattice *L, double *best_ms_per_pass)
             return set_geometry(L, it->second.t);
         }
     }
-    // candidates: the register-streaming pass with z-chunks from 4 planes to the
-    // whole lattice, plus the automatic choice
+    // candidates: the register-streaming pass with 256-thread CTAs (the shape
+    // the batched launch runs), tile rows of 32, 16 or 8 threads, and z-chunks
+    // from 4 planes to the whole lattice, plus the automatic choice
     std::vector<tl::PassTuning> cands;
-    cands.push_back(tl::PassTuning{tl::kVariantLdg, 8, 0, 0, 0, 2});
-    for (int zc = 4; zc <= L->N && zc <= 256; zc *= 2) cands.push_back(tl::PassTuning{tl::kVariantLdg, 8, 0, zc, 0, 2});
+    cands.push_back(tl::PassTuning{tl::kVariantLdg, 8, 0, 0, 0, 256, 0});
+    for (int txt : {32, 16, 8})
+        for (int zc = 4; zc <= L->N && zc <= 256; zc *= 2)
+            cands.push_back(tl::PassTuning{tl::kVariantLdg, 8, 0, zc, 0, 256, txt});
     const tl::PassTuning saved = L->tuning;
     cudaEvent_t e0, e1;
     TB_CK(cudaEventCreate(&e0));

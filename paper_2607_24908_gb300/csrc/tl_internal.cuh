@@ -70,7 +70,8 @@ struct PassTuning {
     int stages;   // bulk: shared-memory ring depth in z-planes (3..8)
     int zc;       // z-planes per CTA
     int prefetch; // ldg: planes prefetched per thread with cp.async (0 or 3)
-    int minblocks; // ldg: CTAs per SM the register budget must allow (2 or 3)
+    int threads;  // ldg: threads per CTA, 256 (default) or 512
+    int txt;      // ldg: threads along x per tile row, 32 (default), 16 or 8
 };
 
 // Launch geometry of the fused pass.
@@ -84,13 +85,13 @@ struct PassGeom {
     int cwarps;    // compute warps per CTA
     int stages;    // shared-memory ring depth (bulk variant)
     int prefetch;  // per-thread prefetch depth (ldg variant)
-    int minblocks; // CTAs per SM the ldg kernel's registers allow
+    int threads;   // threads per CTA (ldg variant)
     size_t smem;   // dynamic shared memory per CTA
 };
 
 PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTuning &t);
 
-// Tuning from the environment (TL_PASS_VARIANT=ldg|bulk, TL_PREFETCH, TL_LDG_MINB,
+// Tuning from the environment (TL_PASS_VARIANT=ldg|bulk, TL_PREFETCH, TL_LDG_THREADS, TL_LDG_TXT,
 // TL_BULK_WARPS, TL_BULK_STAGES, TL_PASS_ZC), else the built-in defaults.
 PassTuning default_tuning();
 

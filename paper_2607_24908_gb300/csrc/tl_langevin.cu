@@ -137,7 +137,7 @@ extern "C" int tl_langevin_step(tl_lattice *L, int n, double dt, const tl_langev
     if (!isfinite(p->lambda) || !isfinite(p->m2) || !isfinite(p->noise)) return tl::fail(TL_EINVAL, "non-finite parameter");
     if (!(L->state_mask & 1u)) return tl::fail(TL_ESTATE, "phi_0 has not been set");
     if (L->batch_refs > 0) return tl::fail(TL_ESTATE, "lattice is part of a batch");
-    tl::PassTuning t{tl::kVariantLdg, 8, 0, 0, 0, 2};
+    tl::PassTuning t{tl::kVariantLdg, 8, 0, 0, 0, 256, 0};
     const tl::PassGeom g = tl::pass_geometry(L->N, (int)L->esz, L->sm_count, 1, t);
     const double inv_dx2 = 1.0 / (L->dx * L->dx);
     const double amp = p->noise * sqrt(dt);

@@ -63,8 +63,10 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
     g.cwarps = (t.variant == kVariantBulk) ? (t.cwarps == 4 ? 4 : 8) : 8;
     // CTAs of whole warps (the CTA reduction needs them) whose compute threads
     // are laid over a tile of txt x ty threads; leftover threads idle.
-    const int threads = 32 * g.cwarps;
-    g.txt = per_row < 32 ? per_row : 32;
+    g.threads = (t.variant == kVariantLdg && t.threads == 512) ? 512 : 256;
+    const int threads = t.variant == kVariantBulk ? 32 * g.cwarps : g.threads;
+    const int txt_max = (t.variant == kVariantLdg && (t.txt == 8 || t.txt == 16)) ? t.txt : 32;
+    g.txt = per_row < txt_max ? per_row : txt_max;
     g.ty = threads / g.txt;
     if (g.ty > N) g.ty = N;
     const int gx = (per_row + g.txt - 1) / g.txt;
@@ -83,10 +85,8 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
     g.stages = 0;
     g.smem = 0;
     g.prefetch = 0;
-    g.minblocks = 2;
     if (g.variant == kVariantLdg) {
-        g.prefetch = t.prefetch > 0 ? 3 : 0;
-        g.minblocks = t.minblocks == 3 ? 3 : 2;
+        g.prefetch = (t.prefetch > 0 && g.threads == 256) ? 3 : 0;
         g.smem = (size_t)g.prefetch * nf * 2 * 256 * 16;
     }
     if (g.variant == kVariantBulk) {

@@ -461,8 +461,8 @@ __device__ __forceinline__ void ldg_tile(const Model &m, const FieldPtrs &fp, co
     cta_reduce_finalize<NQ>(accd, m, c, sc, slots, bid, nblocks);
 }
 
-template <typename T, int NF, bool MEASURE, int D, int MINB>
-__global__ void __launch_bounds__(256, MINB) fused_pass_ldg(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
+template <typename T, int NF, bool MEASURE, int D, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) fused_pass_ldg(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
                                                             Scalars *sc, double *slots)
 {
     extern __shared__ __align__(16) unsigned char ring_raw[];
@@ -763,18 +763,18 @@ static cudaError_t launch_bulk(const Model &m, const FieldPtrs &fp, const PassCo
     return cudaGetLastError();
 }
 
-template <typename T, int NF, bool MEASURE, int D, int MINB>
+template <typename T, int NF, bool MEASURE, int D, int NT>
 static cudaError_t launch_ldg(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
                               double *slots, cudaStream_t s)
 {
     static size_t configured = 0;
-    auto kern = fused_pass_ldg<T, NF, MEASURE, D, MINB>;
+    auto kern = fused_pass_ldg<T, NF, MEASURE, D, NT>;
     if (g.smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
         if (e != cudaSuccess) return e;
         configured = g.smem;
     }
-    kern<<<g.grid, 256, g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, sc, slots);
+    kern<<<g.grid, NT, g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, sc, slots);
     return cudaGetLastError();
 }
 
@@ -785,19 +785,16 @@ static cudaError_t launch_t(const Model &m, const FieldPtrs &fp, const PassCoef 
     if (g.variant == kVariantBulk)
         return measure_only ? launch_bulk<T, NF, true>(m, fp, c, g, sc, slots, s)
                             : launch_bulk<T, NF, false>(m, fp, c, g, sc, slots, s);
-    const bool three = g.minblocks == 3;
+    const bool big = g.threads == 512;
     if (g.prefetch == 0) {
-        if (three)
-            return measure_only ? launch_ldg<T, NF, true, 0, 3>(m, fp, c, g, sc, slots, s)
-                                : launch_ldg<T, NF, false, 0, 3>(m, fp, c, g, sc, slots, s);
-        return measure_only ? launch_ldg<T, NF, true, 0, 2>(m, fp, c, g, sc, slots, s)
-                            : launch_ldg<T, NF, false, 0, 2>(m, fp, c, g, sc, slots, s);
+        if (big)
+            return measure_only ? launch_ldg<T, NF, true, 0, 512>(m, fp, c, g, sc, slots, s)
+                                : launch_ldg<T, NF, false, 0, 512>(m, fp, c, g, sc, slots, s);
+        return measure_only ? launch_ldg<T, NF, true, 0, 256>(m, fp, c, g, sc, slots, s)
+                            : launch_ldg<T, NF, false, 0, 256>(m, fp, c, g, sc, slots, s);
     }
-    if (three)
-        return measure_only ? launch_ldg<T, NF, true, 3, 3>(m, fp, c, g, sc, slots, s)
-                            : launch_ldg<T, NF, false, 3, 3>(m, fp, c, g, sc, slots, s);
-    return measure_only ? launch_ldg<T, NF, true, 3, 2>(m, fp, c, g, sc, slots, s)
-                        : launch_ldg<T, NF, false, 3, 2>(m, fp, c, g, sc, slots, s);
+    return measure_only ? launch_ldg<T, NF, true, 3, 256>(m, fp, c, g, sc, slots, s)
+                        : launch_ldg<T, NF, false, 3, 256>(m, fp, c, g, sc, slots, s);
 }
 
 }  // namespace tl
