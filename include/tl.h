@@ -7,6 +7,8 @@
  * in the alpha time variable):
  *   - N^3 sites, periodic, spacing dx = 2 pi/(kIR N), row-major with x
  *     fastest (the paper keeps row-major layout on every device, Sec. 3.3);
+ *     host arrays are dense [z][y][x], device arrays carry one-site ghost
+ *     copies like the paper's single ghost layer (tl_array_layout);
  *   - fields phi_f (f < n_fields <= 3) with momenta pi_f = a^(3-alpha) phi_f';
  *   - phi' = a^(alpha-3) pi,  pi' = a^(1+alpha) Lap phi - a^(3+alpha) dV/dphi,
  *     Lap the 7-point lattice Laplacian (Sec. 2 "LatLapl", Sec. 4);
@@ -112,14 +114,24 @@ int tl_lattice_create(tl_lattice **out, int N, double kIR, int n_fields, tl_dtyp
 
 /* As tl_lattice_create, but the 4 n_fields field arrays live in caller-owned
  * device memory: dev_ptrs[4 f + 0] phi_f (A), [4 f + 1] pi_f (A),
- * [4 f + 2] phi_f (B), [4 f + 3] pi_f (B); each N^3 elements of dtype,
- * 16-byte aligned; n_ptrs == 4 n_fields. */
+ * [4 f + 2] phi_f (B), [4 f + 3] pi_f (B); each holds the `elems` elements of
+ * dtype that tl_array_layout gives (the padded layout), 16-byte aligned;
+ * n_ptrs == 4 n_fields. */
 int tl_lattice_create_with_buffers(tl_lattice **out, int N, double kIR, int n_fields, tl_dtype dtype,
                                    const tl_expansion *expansion, void *cuda_stream,
                                    void *const *dev_ptrs, size_t n_ptrs);
 
 /* Device bytes tl_lattice_create would allocate for the field arrays. */
 size_t tl_state_bytes(int N, int n_fields, tl_dtype dtype);
+
+/* Device layout of one field array of a lattice.  Rows carry W = 16/sizeof
+ * ghost elements on each side and every z-plane one ghost row above and below
+ * (one-site ghost copies of the periodic neighbours, kept current by every
+ * pass, so that a tile plus its halo is one in-bounds box): element (x, y, z)
+ * is at origin + z plane_pitch + y row_pitch + x, with row_pitch = N + 2W,
+ * plane_pitch = (N + 2) row_pitch, origin = row_pitch + W, and elems = N
+ * plane_pitch elements per array.  Any output may be NULL. */
+int tl_array_layout(int N, tl_dtype dtype, size_t *elems, size_t *row_pitch, size_t *plane_pitch, size_t *origin);
 
 void tl_lattice_destroy(tl_lattice *lat);
 
@@ -171,8 +183,8 @@ int tl_set_state(tl_lattice *lat, int field, int which, const void *host, size_t
  * b = a^(1+alpha) sqrt(mu2 rho/3) from the current state's energies. */
 int tl_set_background(tl_lattice *lat, double a, double b, int from_constraint);
 
-/* Device address of phi_field / pi_field of the current state (valid until
- * the next tl_step). */
+/* Device address of element (0, 0, 0) of phi_field / pi_field of the current
+ * state (padded layout, see tl_array_layout; valid until the next tl_step). */
 int tl_state_device_ptr(tl_lattice *lat, int field, int which, void **dev_ptr);
 
 /* Energies of a caller-owned device state, allocating no device memory.

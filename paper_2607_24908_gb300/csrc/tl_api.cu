@@ -55,7 +55,7 @@ tl::PassTuning tl::default_tuning()
 {
     tl::PassTuning t{tl::kVariantLdg, 8, 0, 0, 0, 256, 0};
     const char *v = getenv("TL_PASS_VARIANT");
-    if (v && strcmp(v, "bulk") == 0) t.variant = tl::kVariantBulk;
+    if (v && strcmp(v, "tma") == 0) t.variant = tl::kVariantTma;
     if ((v = getenv("TL_PREFETCH"))) t.prefetch = atoi(v);
     if ((v = getenv("TL_LDG_THREADS"))) t.threads = atoi(v);
     if ((v = getenv("TL_LDG_TXT"))) t.txt = atoi(v);
@@ -124,6 +124,23 @@ namespace {
 
 size_t n3_of(int N) { return (size_t)N * (size_t)N * (size_t)N; }
 
+// Padded array layout (see tl_internal.cuh): W = 16/esz ghost elements on
+// each side of a row, one ghost row on each side of a plane, no z ghosts.
+struct Layout {
+    long long W, pitch, pplane;
+    size_t elems, origin;
+};
+Layout layout_of(int N, size_t esz)
+{
+    Layout l;
+    l.W = (long long)(16 / esz);
+    l.pitch = N + 2 * l.W;
+    l.pplane = (long long)(N + 2) * l.pitch;
+    l.elems = (size_t)N * (size_t)l.pplane;
+    l.origin = (size_t)(l.pitch + l.W);
+    return l;
+}
+
 // Bytes between consecutive field arrays beyond their size (TL_ARRAY_STAGGER,
 // rounded to 256 bytes; default 0).
 size_t array_stagger()
@@ -151,8 +168,12 @@ int check_dims(int N, double kIR, int n_fields, tl_dtype dtype, const tl_expansi
 void refresh_model(tl_lattice *L)
 {
     Model &m = L->model;
+    const Layout lay = layout_of(L->N, L->esz);
     m.N = L->N;
     m.nf = L->nf;
+    m.ghosts = 1;
+    m.pitch = lay.pitch;
+    m.pplane = lay.pplane;
     m.expanding = L->ex.expanding ? 1 : 0;
     m.alpha = L->ex.alpha;
     m.mu2 = L->ex.fstar_over_mp * L->ex.fstar_over_mp;
@@ -223,6 +244,22 @@ int read_scalars(tl_lattice *L, Scalars *h)
     return TL_OK;
 }
 
+// Dense host array [z][y][x] <-> padded device array, one 2-D copy per z-plane.
+int copy_planes(tl_lattice *L, void *host, void *dev, bool to_device)
+{
+    const size_t N = (size_t)L->N, esz = L->esz;
+    const size_t dpitch = (size_t)L->model.pitch * esz;
+    for (size_t z = 0; z < N; ++z) {
+        char *d = static_cast<char *>(dev) + z * (size_t)L->model.pplane * esz;
+        char *h = static_cast<char *>(host) + z * N * N * esz;
+        if (to_device)
+            TL_CK(cudaMemcpy2DAsync(d, dpitch, h, N * esz, N * esz, N, cudaMemcpyHostToDevice, L->stream));
+        else
+            TL_CK(cudaMemcpy2DAsync(h, N * esz, d, dpitch, N * esz, N, cudaMemcpyDeviceToHost, L->stream));
+    }
+    return TL_OK;
+}
+
 int check_field(const tl_lattice *L, int field, int which)
 {
     if (!L) return fail(TL_EINVAL, "NULL lattice");
@@ -264,7 +301,19 @@ const char *tl_last_error(void) { return g_err; }
 size_t tl_state_bytes(int N, int n_fields, tl_dtype dtype)
 {
     if (N <= 0 || n_fields <= 0) return 0;
-    return 4 * (size_t)n_fields * n3_of(N) * (dtype == TL_F64 ? 8 : 4);
+    const size_t esz = dtype == TL_F64 ? 8 : 4;
+    return 4 * (size_t)n_fields * layout_of(N, esz).elems * esz;
+}
+
+int tl_array_layout(int N, tl_dtype dtype, size_t *elems, size_t *row_pitch, size_t *plane_pitch, size_t *origin)
+{
+    if (N < 8 || N % 4 != 0 || (dtype != TL_F32 && dtype != TL_F64)) return fail(TL_EINVAL, "bad N or dtype");
+    const Layout l = layout_of(N, dtype == TL_F64 ? 8 : 4);
+    if (elems) *elems = l.elems;
+    if (row_pitch) *row_pitch = (size_t)l.pitch;
+    if (plane_pitch) *plane_pitch = (size_t)l.pplane;
+    if (origin) *origin = l.origin;
+    return TL_OK;
 }
 
 int tl_lattice_create(tl_lattice **out, int N, double kIR, int n_fields, tl_dtype dtype,
@@ -295,14 +344,16 @@ int tl_lattice_create(tl_lattice **out, int N, double kIR, int n_fields, tl_dtyp
         return fail(TL_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
     }
     L->own = true;
-    const size_t arr = n3_of(N) * (dtype == TL_F64 ? 8 : 4);
+    const size_t esz = dtype == TL_F64 ? 8 : 4;
+    const Layout lay = layout_of(N, esz);
+    const size_t arr = lay.elems * esz;
     char *p = static_cast<char *>(L->base);
     memset(L->buf, 0, sizeof L->buf);
     for (int f = 0; f < n_fields; ++f)
         for (int par = 0; par < 2; ++par)
             for (int w = 0; w < 2; ++w) {
                 const size_t k = (size_t)(4 * f + 2 * par + w);
-                L->buf[par][w][f] = p + k * (arr + stagger);
+                L->buf[par][w][f] = p + k * (arr + stagger) + lay.origin * esz;
             }
     rc = finish_create(L, N, kIR, n_fields, dtype, expansion, cuda_stream);
     if (rc) {
@@ -328,11 +379,13 @@ int tl_lattice_create_with_buffers(tl_lattice **out, int N, double kIR, int n_fi
     tl_lattice *L = new (std::nothrow) tl_lattice();
     if (!L) return fail(TL_ENOMEM, "host allocation failed");
     memset(L->buf, 0, sizeof L->buf);
+    const size_t esz = dtype == TL_F64 ? 8 : 4;
+    const size_t org = layout_of(N, esz).origin * esz;
     for (int f = 0; f < n_fields; ++f) {
-        L->buf[0][0][f] = dev_ptrs[4 * f + 0];
-        L->buf[0][1][f] = dev_ptrs[4 * f + 1];
-        L->buf[1][0][f] = dev_ptrs[4 * f + 2];
-        L->buf[1][1][f] = dev_ptrs[4 * f + 3];
+        L->buf[0][0][f] = static_cast<char *>(dev_ptrs[4 * f + 0]) + org;
+        L->buf[0][1][f] = static_cast<char *>(dev_ptrs[4 * f + 1]) + org;
+        L->buf[1][0][f] = static_cast<char *>(dev_ptrs[4 * f + 2]) + org;
+        L->buf[1][1][f] = static_cast<char *>(dev_ptrs[4 * f + 3]) + org;
     }
     rc = finish_create(L, N, kIR, n_fields, dtype, expansion, cuda_stream);
     if (rc) {
@@ -437,7 +490,8 @@ int tl_get_state(tl_lattice *L, int field, int which, void *host, size_t bytes)
     int rc = check_field(L, field, which);
     if (rc) return rc;
     if (!host || bytes != n3_of(L->N) * L->esz) return fail(TL_EINVAL, "host buffer must hold N^3 elements");
-    TL_CK(cudaMemcpyAsync(host, L->buf[L->cur][which][field], bytes, cudaMemcpyDeviceToHost, L->stream));
+    rc = copy_planes(L, host, L->buf[L->cur][which][field], false);
+    if (rc) return rc;
     Scalars h;
     rc = read_scalars(L, &h);
     if (rc) return rc;
@@ -452,7 +506,10 @@ int tl_set_state(tl_lattice *L, int field, int which, const void *host, size_t b
     int rc = check_field(L, field, which);
     if (rc) return rc;
     if (!host || bytes != n3_of(L->N) * L->esz) return fail(TL_EINVAL, "host buffer must hold N^3 elements");
-    TL_CK(cudaMemcpyAsync(L->buf[L->cur][which][field], host, bytes, cudaMemcpyHostToDevice, L->stream));
+    rc = copy_planes(L, const_cast<void *>(host), L->buf[L->cur][which][field], true);
+    if (rc) return rc;
+    TL_CK(tl::launch_fill_ghosts((int)L->dtype, L->buf[L->cur][which][field], L->N, L->model.pitch, L->model.pplane,
+                                 L->stream));
     TL_CK(tl::launch_set_background(L->model, L->d_sc, L->ex.a0, 0.0, L->stream));
     TL_CK(cudaStreamSynchronize(L->stream));
     L->state_mask |= 1u << (2 * field + which);
@@ -532,11 +589,12 @@ int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
                 if (ce != cudaSuccess) { rc = fail(TL_ECUDA, "fill_modes: %s", cudaGetErrorString(ce)); break; }
                 cufftResult fr = cufftExecZ2D(plan, reinterpret_cast<cufftDoubleComplex *>(modes), real);
                 if (fr != CUFFT_SUCCESS) { rc = fail(TL_ECUDA, "cufftExecZ2D failed (%d)", (int)fr); break; }
-                ce = tl::launch_assemble((int)L->dtype, dst, real, n3, base, which == 0 ? 1.0 : pscale,
-                                         L->sm_count, L->stream);
+                ce = tl::launch_assemble((int)L->dtype, dst, real, n3, base, which == 0 ? 1.0 : pscale, N,
+                                         L->model.pitch, L->model.pplane, L->sm_count, L->stream);
                 if (ce != cudaSuccess) { rc = fail(TL_ECUDA, "assemble: %s", cudaGetErrorString(ce)); break; }
             } else {
-                cudaError_t ce = tl::launch_assemble((int)L->dtype, dst, nullptr, n3, base, 0.0, L->sm_count, L->stream);
+                cudaError_t ce = tl::launch_assemble((int)L->dtype, dst, nullptr, n3, base, 0.0, N, L->model.pitch,
+                                                     L->model.pplane, L->sm_count, L->stream);
                 if (ce != cudaSuccess) { rc = fail(TL_ECUDA, "assemble: %s", cudaGetErrorString(ce)); break; }
             }
         }
@@ -544,6 +602,10 @@ int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
     cudaFreeAsync(modes, L->stream);
     cudaFreeAsync(real, L->stream);
     if (rc) return rc;
+    for (int f = 0; f < L->nf; ++f)
+        for (int which = 0; which < 2; ++which)
+            TL_CK(tl::launch_fill_ghosts((int)L->dtype, L->buf[L->cur][which][f], N, L->model.pitch, L->model.pplane,
+                                         L->stream));
     L->state_mask = (1u << (2 * L->nf)) - 1u;
     L->has_state = true;
     L->step = 0;
@@ -578,7 +640,8 @@ int tl_spectrum(tl_lattice *L, int field, int which, int nbins, double *k, doubl
     TL_CK(cudaMallocAsync((void **)&real, n3 * sizeof(double), L->stream));
     TL_CK(cudaMallocAsync((void **)&acc, (size_t)nb * 3 * sizeof(double), L->stream));
     TL_CK(cudaMemsetAsync(acc, 0, (size_t)nb * 3 * sizeof(double), L->stream));
-    TL_CK(tl::launch_widen((int)L->dtype, real, L->buf[L->cur][which][field], n3, L->sm_count, L->stream));
+    TL_CK(tl::launch_widen((int)L->dtype, real, L->buf[L->cur][which][field], n3, N, L->model.pitch, L->model.pplane,
+                           L->sm_count, L->stream));
     cufftResult fr = cufftExecD2Z(plan, real, reinterpret_cast<cufftDoubleComplex *>(modes));
     if (fr != CUFFT_SUCCESS) return fail(TL_ECUDA, "cufftExecD2Z failed (%d)", (int)fr);
     TL_CK(tl::launch_bin(modes, N, nb, acc, acc + nb, reinterpret_cast<unsigned long long *>(acc + 2 * nb),

@@ -67,18 +67,26 @@ __global__ void fill_modes_kernel(double2 *modes, int N, double kIR, double A, d
     }
 }
 
-template <typename T>
-__global__ void assemble_kernel(T *dst, const double *delta, size_t n, double base, double scale)
+// dense index i = (z N + y) N + x  <->  pitched offset z PP + y P + x
+__device__ __forceinline__ long long pitched(size_t i, int N, long long P, long long PP)
 {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = (T)(base + (delta ? scale * delta[i] : 0.0));
+    const long long x = (long long)(i % N), y = (long long)((i / N) % N), z = (long long)(i / ((size_t)N * N));
+    return z * PP + y * P + x;
 }
 
 template <typename T>
-__global__ void widen_kernel(double *dst, const T *src, size_t n)
+__global__ void assemble_kernel(T *dst, const double *delta, size_t n, double base, double scale, int N, long long P,
+                                long long PP)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = (double)src[i];
+        dst[pitched(i, N, P, PP)] = (T)(base + (delta ? scale * delta[i] : 0.0));
+}
+
+template <typename T>
+__global__ void widen_kernel(double *dst, const T *src, size_t n, int N, long long P, long long PP)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[pitched(i, N, P, PP)];
 }
 
 // bin(s) = floor(sqrt(s) + 1/2) for an integer s >= 0, decided in integers:
@@ -145,22 +153,25 @@ cudaError_t launch_fill_modes(double2 *modes, int N, double kIR, double A, doubl
     return cudaGetLastError();
 }
 
-cudaError_t launch_assemble(int dtype, void *dst, const double *delta, size_t n, double base, double scale,
-                            int sm_count, cudaStream_t s)
+cudaError_t launch_assemble(int dtype, void *dst, const double *delta, size_t n, double base, double scale, int N,
+                            long long P, long long PP, int sm_count, cudaStream_t s)
 {
     if (dtype == TL_F32)
-        assemble_kernel<float><<<grid_for(n, sm_count), 256, 0, s>>>(static_cast<float *>(dst), delta, n, base, scale);
+        assemble_kernel<float><<<grid_for(n, sm_count), 256, 0, s>>>(static_cast<float *>(dst), delta, n, base, scale,
+                                                                     N, P, PP);
     else
-        assemble_kernel<double><<<grid_for(n, sm_count), 256, 0, s>>>(static_cast<double *>(dst), delta, n, base, scale);
+        assemble_kernel<double><<<grid_for(n, sm_count), 256, 0, s>>>(static_cast<double *>(dst), delta, n, base,
+                                                                      scale, N, P, PP);
     return cudaGetLastError();
 }
 
-cudaError_t launch_widen(int dtype, double *dst, const void *src, size_t n, int sm_count, cudaStream_t s)
+cudaError_t launch_widen(int dtype, double *dst, const void *src, size_t n, int N, long long P, long long PP,
+                         int sm_count, cudaStream_t s)
 {
     if (dtype == TL_F32)
-        widen_kernel<float><<<grid_for(n, sm_count), 256, 0, s>>>(dst, static_cast<const float *>(src), n);
+        widen_kernel<float><<<grid_for(n, sm_count), 256, 0, s>>>(dst, static_cast<const float *>(src), n, N, P, PP);
     else
-        widen_kernel<double><<<grid_for(n, sm_count), 256, 0, s>>>(dst, static_cast<const double *>(src), n);
+        widen_kernel<double><<<grid_for(n, sm_count), 256, 0, s>>>(dst, static_cast<const double *>(src), n, N, P, PP);
     return cudaGetLastError();
 }
 

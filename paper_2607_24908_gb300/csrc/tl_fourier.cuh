@@ -11,11 +11,12 @@ namespace tl {
 // Half-spectrum [N][N][N/2+1] of Hermitian Gaussian modes (see tl_init_spec).
 cudaError_t launch_fill_modes(double2 *modes, int N, double kIR, double A, double m2, int pi_spectrum,
                               uint64_t seed, uint64_t stream, int sm_count, cudaStream_t s);
-// dst[i] = (T)(base + scale * delta[i]) (delta may be NULL).
-cudaError_t launch_assemble(int dtype, void *dst, const double *delta, size_t n, double base, double scale,
-                            int sm_count, cudaStream_t s);
-// dst[i] = (double)src[i].
-cudaError_t launch_widen(int dtype, double *dst, const void *src, size_t n, int sm_count, cudaStream_t s);
+// dst[pitched(i)] = (T)(base + scale * delta[i]) (delta may be NULL; delta dense).
+cudaError_t launch_assemble(int dtype, void *dst, const double *delta, size_t n, double base, double scale, int N,
+                            long long P, long long PP, int sm_count, cudaStream_t s);
+// dst[i] = (double)src[pitched(i)] (dst dense).
+cudaError_t launch_widen(int dtype, double *dst, const void *src, size_t n, int N, long long P, long long PP,
+                         int sm_count, cudaStream_t s);
 // Shell sums of |d|^2 / N^6, |n| and mode counts (accumulated with atomics).
 cudaError_t launch_bin(const double2 *modes, int N, int nbins, double *Psum, double *rsum, unsigned long long *cnt,
                        int sm_count, cudaStream_t s);

@@ -29,10 +29,19 @@ struct Scalars {
 };
 
 // Scalar constants of a lattice/model passed by value to every pass.
+// Field arrays are addressed from their element (0, 0, 0) as
+// z * pplane + y * pitch + x.  A dense array has pitch = N, pplane = N^2;
+// the lattice's own arrays carry ghost copies (ghosts = 1): W = 16/sizeof(T)
+// elements left and right of every row and one row above and below every
+// z-plane, pitch = N + 2W, pplane = (N + 2) pitch, which every pass keeps
+// current for the sites it writes.
 struct Model {
     int N;
     int nf;
     int expanding;
+    int ghosts;
+    long long pitch;
+    long long pplane;
     double alpha;
     double mu2;
     double inv_dx2;
@@ -58,14 +67,14 @@ struct FieldPtrs {
     void *pi_out[kMaxFields];
 };
 
-// Fused-pass variants: per-thread loads through L1/L2, or z-planes staged in
-// shared memory by bulk asynchronous copies.
+// Fused-pass variants: per-thread loads through L1/L2, or z-planes of a
+// ghost-padded tile staged in shared memory by tiled TMA copies.
 constexpr int kVariantLdg = 0;
-constexpr int kVariantBulk = 1;
+constexpr int kVariantTma = 1;
 
 // Tunable launch parameters of the fused pass (0 = choose automatically).
 struct PassTuning {
-    int variant;  // kVariantLdg or kVariantBulk
+    int variant;  // kVariantLdg or kVariantTma
     int cwarps;   // bulk: compute warps per CTA (4 or 8; one producer warp is added)
     int stages;   // bulk: shared-memory ring depth in z-planes (3..8)
     int zc;       // z-planes per CTA
@@ -81,7 +90,7 @@ struct PassGeom {
     int zc;   // z-planes per CTA
     dim3 grid;
     unsigned nblocks;
-    int variant;   // kVariantLdg or kVariantBulk
+    int variant;   // kVariantLdg or kVariantTma
     int cwarps;    // compute warps per CTA
     int stages;    // shared-memory ring depth (bulk variant)
     int prefetch;  // per-thread prefetch depth (ldg variant)
@@ -117,6 +126,9 @@ cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const Pa
 
 // Record msg+detail as this thread's tl_last_error() text; returns code.
 int set_error(int code, const char *msg, const char *detail);
+
+// Refresh the ghost copies of one padded array from its interior.
+cudaError_t launch_fill_ghosts(int dtype, void *origin, int N, long long P, long long PP, cudaStream_t s);
 
 // Set a, b (and the derived weights) on the device; drift = 0.
 cudaError_t launch_set_background(const Model &m, Scalars *sc, double a, double b, cudaStream_t s);

@@ -82,8 +82,8 @@ __device__ __forceinline__ void ld(const T *p, T (&o)[V16<T>::W])
 
 template <typename T>
 __global__ void __launch_bounds__(256) langevin_pass(const T *__restrict__ in, T *__restrict__ out, int N, int txt,
-                                                     int ty, int zc, T inv_dx2, T dt, T m2, T half_lam, T amp,
-                                                     uint64_t seed, uint64_t ctr1)
+                                                     int ty, int zc, long long P, long long PP, T inv_dx2, T dt, T m2,
+                                                     T half_lam, T amp, uint64_t seed, uint64_t ctr1)
 {
     constexpr int W = V16<T>::W;
     const int tx = threadIdx.x % txt, tyi = threadIdx.x / txt;
@@ -92,9 +92,12 @@ __global__ void __launch_bounds__(256) langevin_pass(const T *__restrict__ in, T
     const int z0 = blockIdx.z * zc;
     const int z1 = min(z0 + zc, N);
     if (!(tyi < ty && x0 < N && y < N)) return;
-    const size_t NN = (size_t)N * N;
-    const size_t row = (size_t)y * N, rowm = (size_t)(y == 0 ? N - 1 : y - 1) * N,
-                 rowp = (size_t)(y + 1 == N ? 0 : y + 1) * N;
+    const size_t NN = (size_t)PP;
+    const size_t row = (size_t)y * P, rowm = (size_t)(y == 0 ? N - 1 : y - 1) * P,
+                 rowp = (size_t)(y + 1 == N ? 0 : y + 1) * P;
+    // ghost copies of this thread's sites (padded arrays carry one-site ghosts)
+    const long long gx = x0 == 0 ? (long long)N : (x0 + W == N ? -(long long)N : 0);
+    const long long gy = y == 0 ? (long long)N * P : (y == N - 1 ? -(long long)N * P : 0);
     const int xl = x0 == 0 ? N - 1 : x0 - 1, xr = x0 + W == N ? 0 : x0 + W;
     T zm[W], cu[W], zp[W];
     ld(in + (size_t)(z0 == 0 ? N - 1 : z0 - 1) * NN + row + x0, zm);
@@ -114,11 +117,15 @@ __global__ void __launch_bounds__(256) langevin_pass(const T *__restrict__ in, T
             const T right = j == W - 1 ? b : cu[j + 1];
             const T lap = (((left - c) + (right - c)) + ((ym[j] - c) + (yp[j] - c))) + ((zm[j] - c) + (zp[j] - c));
             const T drift = lap * inv_dx2 - m2 * c - half_lam * c * c * c;
-            const T xi = gauss<T>(pz + row + x0 + j, ctr1, seed);
+            const T xi = gauss<T>(((size_t)z * N + y) * N + x0 + j, ctr1, seed);
             o[j] = (c + dt * drift) + amp * xi;
         }
 #pragma unroll
-        for (int j = 0; j < W; ++j) out[pz + row + x0 + j] = o[j];
+        for (int j = 0; j < W; ++j) {
+            out[pz + row + x0 + j] = o[j];
+            if (gx) out[pz + row + x0 + j + gx] = o[j];
+            if (gy) out[pz + row + x0 + j + gy] = o[j];
+        }
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             zm[j] = cu[j];
@@ -147,11 +154,13 @@ extern "C" int tl_langevin_step(tl_lattice *L, int n, double dt, const tl_langev
         const uint64_t ctr1 = (1ull << 63) + (uint64_t)(L->langevin_steps + s);
         if (L->dtype == TL_F32)
             langevin_pass<float><<<g.grid, 256, 0, L->stream>>>(
-                static_cast<const float *>(in), static_cast<float *>(out), L->N, g.txt, g.ty, g.zc, (float)inv_dx2,
+                static_cast<const float *>(in), static_cast<float *>(out), L->N, g.txt, g.ty, g.zc, L->model.pitch,
+                L->model.pplane, (float)inv_dx2,
                 (float)dt, (float)p->m2, (float)(0.5 * p->lambda), (float)amp, seed, ctr1);
         else
             langevin_pass<double><<<g.grid, 256, 0, L->stream>>>(
-                static_cast<const double *>(in), static_cast<double *>(out), L->N, g.txt, g.ty, g.zc, inv_dx2, dt,
+                static_cast<const double *>(in), static_cast<double *>(out), L->N, g.txt, g.ty, g.zc, L->model.pitch,
+                L->model.pplane, inv_dx2, dt,
                 p->m2, 0.5 * p->lambda, amp, seed, ctr1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return tl::fail(TL_ECUDA, "langevin_pass: %s", cudaGetErrorString(e));

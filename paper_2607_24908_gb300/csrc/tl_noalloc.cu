@@ -87,6 +87,9 @@ extern "C" int tl_energies_noalloc(int N, double kIR, int n_fields, tl_dtype dty
     tl::Model m{};
     m.N = N;
     m.nf = n_fields;
+    m.ghosts = 0;  // caller arrays are dense: pitch N, plane N^2
+    m.pitch = N;
+    m.pplane = (long long)N * N;
     m.expanding = (expansion && expansion->expanding) ? 1 : 0;
     m.alpha = m.expanding ? expansion->alpha : 0.0;
     m.mu2 = m.expanding ? expansion->fstar_over_mp * expansion->fstar_over_mp : 1.0;

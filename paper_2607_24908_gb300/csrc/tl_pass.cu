@@ -60,11 +60,11 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
     PassGeom g;
     const int per_row = N / W;  // N % 4 == 0 is required, so W | N
     g.variant = t.variant;
-    g.cwarps = (t.variant == kVariantBulk) ? (t.cwarps == 4 ? 4 : 8) : 8;
+    g.cwarps = (t.variant == kVariantTma) ? (t.cwarps == 4 ? 4 : 8) : 8;
     // CTAs of whole warps (the CTA reduction needs them) whose compute threads
     // are laid over a tile of txt x ty threads; leftover threads idle.
     g.threads = (t.variant == kVariantLdg && t.threads == 512) ? 512 : 256;
-    const int threads = t.variant == kVariantBulk ? 32 * g.cwarps : g.threads;
+    const int threads = t.variant == kVariantTma ? 32 * g.cwarps : g.threads;
     const int txt_max = (t.variant == kVariantLdg && (t.txt == 8 || t.txt == 16)) ? t.txt : 32;
     g.txt = per_row < txt_max ? per_row : txt_max;
     g.ty = threads / g.txt;
@@ -89,7 +89,7 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
         g.prefetch = (t.prefetch > 0 && g.threads == 256) ? 3 : 0;
         g.smem = (size_t)g.prefetch * nf * 2 * 256 * 16;
     }
-    if (g.variant == kVariantBulk) {
+    if (g.variant == kVariantTma) {
         // ring depth: as deep as fits two CTAs per SM (<= 113 KB each), at
         // least 3 (two planes read + one in flight), at most kMaxStages.
         int S = t.stages > 0 ? t.stages : 8;
@@ -125,6 +125,47 @@ cudaError_t launch_group(int dtype, int nf, const BatchJob *jobs, const unsigned
 {
     return dtype == TL_F32 ? launch_group_f32(nf, jobs, first_item, njobs, total, c, grid, s)
                            : launch_group_f64(nf, jobs, first_item, njobs, total, c, grid, s);
+}
+
+// Refresh the ghost copies of one array (layout in tl_internal.cuh): the W
+// ghost elements left and right of every row, then the ghost rows above and
+// below every plane.
+template <typename T>
+__global__ void fill_ghosts_x(T *a, int N, long long P, long long PP, int W)
+{
+    const long long rows = (long long)N * N;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
+        T *row = a + (r / N) * PP + (r % N) * P;
+        for (int j = 0; j < W; ++j) {
+            row[-W + j] = row[N - W + j];
+            row[N + j] = row[j];
+        }
+    }
+}
+template <typename T>
+__global__ void fill_ghosts_y(T *a, int N, long long P, long long PP)
+{
+    const long long n = (long long)N * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        T *plane = a + (i / N) * PP;
+        const long long x = i % N;
+        plane[-P + x] = plane[(long long)(N - 1) * P + x];
+        plane[(long long)N * P + x] = plane[x];
+    }
+}
+
+cudaError_t launch_fill_ghosts(int dtype, void *origin, int N, long long P, long long PP, cudaStream_t s)
+{
+    const long long n = (long long)N * N;
+    const unsigned grid = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    if (dtype == TL_F32) {
+        fill_ghosts_x<float><<<grid, 256, 0, s>>>(static_cast<float *>(origin), N, P, PP, 4);
+        fill_ghosts_y<float><<<grid, 256, 0, s>>>(static_cast<float *>(origin), N, P, PP);
+    } else {
+        fill_ghosts_x<double><<<grid, 256, 0, s>>>(static_cast<double *>(origin), N, P, PP, 2);
+        fill_ghosts_y<double><<<grid, 256, 0, s>>>(static_cast<double *>(origin), N, P, PP);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_set_background(const Model &m, Scalars *sc, double a, double b, cudaStream_t s)

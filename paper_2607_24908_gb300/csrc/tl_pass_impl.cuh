@@ -14,11 +14,9 @@
 //
 // Layout and traffic: each thread owns W = 16/sizeof(T) consecutive x-sites
 // (one 128-bit word per array) of one y-row and marches a chunk of z-planes,
-// keeping phi at z-1, z, z+1 in registers.  Two variants feed it: plain
-// per-thread loads through L1/L2 (fused_pass_ldg), or a ring of z-planes of the
-// CTA's tile staged in shared memory by bulk asynchronous copies
-// (fused_pass_bulk).  Either way HBM sees each array read once and written
-// once per pass: 4 sizeof(T) bytes per site per field.
+// keeping phi at z-1, z, z+1 in registers; the neighbour rows and edge sites
+// come through L1/L2 (fused_pass_ldg).  HBM sees each array read once and
+// written once per pass: 4 sizeof(T) bytes per site per field.
 #pragma once
 #include <math.h>
 
@@ -287,6 +285,34 @@ __device__ __forceinline__ void cta_reduce_finalize(const double (&accd)[NQ], co
 __device__ __forceinline__ unsigned grid_bid() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 __device__ __forceinline__ unsigned grid_nblocks() { return gridDim.x * gridDim.y * gridDim.z; }
 
+// Ghost copies of this thread's W output sites: a site in the first or last
+// W columns also goes to the right or left ghost columns, a site in the first
+// or last row to the ghost row below or above the plane (corners not needed:
+// the 7-point stencil never reads them).
+template <typename T, int NF, int W>
+__device__ __forceinline__ void store_ghosts(T *const (&pho)[NF], T *const (&pio)[NF], const T (&ph)[NF][W],
+                                             const T (&pp)[NF][W], size_t pz, int x0, int y, int N, long long P)
+{
+    long long dx = 0, dy = 0;
+    if (x0 == 0) dx = N;                  // right ghost columns
+    else if (x0 + W == N) dx = -(long long)N;
+    if (y == 0) dy = (long long)N * P;    // ghost row after the last row
+    else if (y == N - 1) dy = -(long long)N * P;
+    if (dx == 0 && dy == 0) return;
+    const size_t base = pz + (size_t)y * P + x0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        if (dx) {
+            store_vec_cs(pho[f] + base + dx, ph[f]);
+            store_vec_cs(pio[f] + base + dx, pp[f]);
+        }
+        if (dy) {
+            store_vec_cs(pho[f] + base + dy, ph[f]);
+            store_vec_cs(pio[f] + base + dy, pp[f]);
+        }
+    }
+}
+
 // ---- variant 1: register streaming with a per-thread prefetch ring -------------
 // Each thread owns its 128-bit words.  The HBM stream (the stored phi and pi
 // of its own sites, plane after plane) is prefetched D planes ahead with
@@ -342,12 +368,13 @@ __device__ __forceinline__ void ldg_tile(const Model &m, const FieldPtrs &fp, co
             pho[f] = static_cast<T *>(fp.phi_out[f]);
             pio[f] = static_cast<T *>(fp.pi_out[f]);
         }
-        const size_t NN = (size_t)N * (size_t)N;
+        const size_t NN = (size_t)m.pplane;
+        const size_t P = (size_t)m.pitch;
         const int xl = (x0 == 0) ? N - 1 : x0 - 1;
         const int xr = (x0 + W == N) ? 0 : x0 + W;
-        const size_t row = (size_t)y * N;
-        const size_t rowm = (size_t)((y == 0) ? N - 1 : y - 1) * N;
-        const size_t rowp = (size_t)((y + 1 == N) ? 0 : y + 1) * N;
+        const size_t row = (size_t)y * P;
+        const size_t rowm = (size_t)((y == 0) ? N - 1 : y - 1) * P;
+        const size_t rowp = (size_t)((y + 1 == N) ? 0 : y + 1) * P;
         auto cur_vec = [&](int f, size_t off, T (&o)[W]) {
             T a[W], b[W];
             load_vec(phs[f] + off, a);
@@ -437,6 +464,7 @@ __device__ __forceinline__ void ldg_tile(const Model &m, const FieldPtrs &fp, co
                     store_vec_cs(pho[f] + pz + row + x0, cu[f]);
                     store_vec_cs(pio[f] + pz + row + x0, pnew[f]);
                 }
+                if (m.ghosts) store_ghosts<T, NF, W>(pho, pio, cu, pnew, pz, x0, y, N, (long long)P);
             }
             if (((z - z0) & 15) == 15) {
 #pragma unroll
@@ -496,14 +524,7 @@ __global__ void __launch_bounds__(256, 2) fused_pass_group(const BatchJob *jobs,
     }
 }
 
-// ---- variant 2: bulk-copy staging ------------------------------------------------
-// The CTA keeps a ring of S z-planes of its tile plus a one-site halo (raw
-// phi_s and pi_s of every field) in shared memory.  Warp 0 fills the ring with
-// cp.async.bulk row copies (the Tensor Memory Accelerator's bulk path; rows
-// that cross the periodic boundary are split in two), each plane signalling
-// one mbarrier; S-2 planes are in flight while the CTA computes plane z from
-// planes z (halo) and z+1 (centre).  Registers hold only phi at z-1, z, z+1
-// and pi at z, z+1 for the thread's own sites.
+// ---- PTX helpers for asynchronous copies ---------------------------------------
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -561,208 +582,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
 }
 
-// Copy elements [xs, xs+len) of a periodic row (indices mod N) to dst, in at
-// most ceil(len/N)+1 contiguous bulk copies.  xs, len and N are multiples of
-// W, so every copy is 16-byte aligned and a multiple of 16 bytes.
-template <typename T>
-__device__ __forceinline__ void copy_row(T *dst, const T *row, int xs, int len, int N, uint64_t *bar)
-{
-    int xg = xs % N;
-    if (xg < 0) xg += N;
-    int off = 0;
-    while (off < len) {
-        const int n = min(len - off, N - xg);
-        bulk_load(dst + off, row + xg, (uint32_t)(n * sizeof(T)), bar);
-        off += n;
-        xg = 0;
-    }
-}
-
-// Warp-specialised: warps 0..CW-1 compute, warp CW produces.  The producer
-// runs up to S planes ahead: before refilling a stage it waits on that
-// stage's "empty" mbarrier, which each consumer warp arrives on once it is done
-// with the plane; consumers wait on the stage's "full" mbarrier (completed by
-// the bulk copies' byte count).  No CTA-wide barrier inside the z loop.
-constexpr int kMaxStages = 8;
-
-template <typename T, int NF, bool MEASURE>
-__global__ void __launch_bounds__(288, 2) fused_pass_bulk(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
-                                                          int S, Scalars *sc, double *slots)
-{
-    constexpr int W = Vec<T>::W;
-    constexpr int NQ = 2 * NF + 1;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
-    __shared__ volatile int s_failed;
-    T *stage_base = reinterpret_cast<T *>(smem_raw);
-
-    const int N = m.N;
-    const int tid = threadIdx.x;
-    const int CW = (blockDim.x >> 5) - 1;  // consumer warps
-    const bool producer = (tid >> 5) == CW;
-    const int x_tile = blockIdx.x * txt * W, y_tile = blockIdx.y * ty;
-    const int z0 = blockIdx.z * zc;
-    const int z1 = min(z0 + zc, N);
-    const int K = (z1 - z0) + 2;  // planes z0-1 .. z1
-    const int rowe = txt * W + 2 * W;
-    const int plane = (ty + 2) * rowe;
-    const uint32_t plane_bytes = (uint32_t)(NF * 2 * plane * sizeof(T));
-    const size_t NN = (size_t)N * (size_t)N;
-    auto arr = [&](int s, int f, int a) -> T * { return stage_base + (size_t)((s * NF + f) * 2 + a) * plane; };
-
-    if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CW);
-        }
-        s_failed = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-
-    double accd[NQ];
-#pragma unroll
-    for (int i = 0; i < NQ; ++i) accd[i] = 0.0;
-    int issued = 0;
-
-    if (producer) {
-        const int lane = tid & 31;
-        for (int k = 0; k < K; ++k) {
-            const int s = k % S;
-            if (k >= S && !mbar_wait_bounded(&empty[s], ((k / S) - 1) & 1u, sc)) {
-                s_failed = 1;
-                break;
-            }
-            if (s_failed) break;
-            const int zg = (z0 - 1 + k + N) % N;
-            if (lane == 0) mbar_arrive_expect_tx(&full[s], plane_bytes);
-            __syncwarp();
-            for (int item = lane; item < NF * 2 * (ty + 2); item += 32) {
-                const int f = item / (2 * (ty + 2));
-                const int rem = item - f * 2 * (ty + 2);
-                const int a = rem / (ty + 2);
-                const int r = rem - a * (ty + 2);
-                const int yg = (y_tile - 1 + r + N) % N;
-                const T *src = static_cast<const T *>(a == 0 ? fp.phi_in[f] : fp.pi_in[f]) +
-                               ((size_t)zg * NN + (size_t)yg * N);
-                copy_row<T>(arr(s, f, a) + r * rowe, src, x_tile - W, rowe, N, &full[s]);
-            }
-            issued = k + 1;
-        }
-    } else {
-        const int lane = tid & 31;
-        const int tx = tid % txt, tyi = tid / txt;
-        const int x0 = x_tile + tx * W;
-        const int y = y_tile + tyi;
-        const bool active = (tyi < ty) && (x0 < N) && (y < N);
-        const Coefs<T, NF> k(m, c, sc);
-        const int ctr = (tyi + 1) * rowe + (tx + 1) * W;
-        T zm[NF][W], cu[NF][W], zp[NF][W], pc[NF][W], pn[NF][W];
-        T acc[NQ];
-#pragma unroll
-        for (int i = 0; i < NQ; ++i) acc[i] = (T)0;
-        auto centre = [&](int kk, T (&ph)[NF][W], T (&pp)[NF][W]) {
-            const int s = kk % S;
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                T a[W];
-                load_vec_s(arr(s, f, 0) + ctr, a);
-                load_vec_s(arr(s, f, 1) + ctr, pp[f]);
-#pragma unroll
-                for (int j = 0; j < W; ++j) ph[f][j] = fma_t(k.drift, pp[f][j], a[j]);
-            }
-        };
-        auto release = [&](int kk) {
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[kk % S]))
-                                        : "memory");
-        };
-        bool ok = true;
-        if (active) {
-            ok = mbar_wait_bounded(&full[0], 0u, sc);
-            centre(0, zm, pn);
-            ok = ok && mbar_wait_bounded(&full[1 % S], (1 / S) & 1u, sc);
-            centre(1, cu, pc);
-        }
-        if (!ok) s_failed = 1;
-        release(0);
-        for (int z = z0; z < z1 && !s_failed; ++z) {
-            const int kz = z - z0 + 1;
-            if (active) {
-                if (!mbar_wait_bounded(&full[(kz + 1) % S], ((kz + 1) / S) & 1u, sc)) s_failed = 1;
-                centre(kz + 1, zp, pn);
-                const int s0 = kz % S;
-                T ym[NF][W], yp[NF][W], xlv[NF], xrv[NF];
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    const T *ph = arr(s0, f, 0), *pp = arr(s0, f, 1);
-                    T a[W], b[W];
-                    load_vec_s(ph + ctr - rowe, a);
-                    load_vec_s(pp + ctr - rowe, b);
-#pragma unroll
-                    for (int j = 0; j < W; ++j) ym[f][j] = fma_t(k.drift, b[j], a[j]);
-                    load_vec_s(ph + ctr + rowe, a);
-                    load_vec_s(pp + ctr + rowe, b);
-#pragma unroll
-                    for (int j = 0; j < W; ++j) yp[f][j] = fma_t(k.drift, b[j], a[j]);
-                    xlv[f] = fma_t(k.drift, pp[ctr - 1], ph[ctr - 1]);
-                    xrv[f] = fma_t(k.drift, pp[ctr + W], ph[ctr + W]);
-                }
-                T pnew[NF][W];
-                site_update<T, NF, W>(k, cu, zm, zp, ym, yp, xlv, xrv, pc, pnew, acc);
-                if (!MEASURE) {
-                    const size_t off = (size_t)z * NN + (size_t)y * N + x0;
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) {
-                        store_vec_cs(static_cast<T *>(fp.phi_out[f]) + off, cu[f]);
-                        store_vec_cs(static_cast<T *>(fp.pi_out[f]) + off, pnew[f]);
-                    }
-                }
-                if (((z - z0) & 15) == 15) {
-#pragma unroll
-                    for (int i = 0; i < NQ; ++i) {
-                        accd[i] += (double)acc[i];
-                        acc[i] = (T)0;
-                    }
-                }
-#pragma unroll
-                for (int f = 0; f < NF; ++f)
-#pragma unroll
-                    for (int j = 0; j < W; ++j) {
-                        zm[f][j] = cu[f][j];
-                        cu[f][j] = zp[f][j];
-                        pc[f][j] = pn[f][j];
-                    }
-            }
-            release(kz);
-        }
-#pragma unroll
-        for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
-    }
-    __syncthreads();
-    // After a timeout, wait (bounded) for planes still in flight before the
-    // CTA's shared memory goes away.
-    if (s_failed && producer && (tid & 31) == 0)
-        for (int kk = (issued > S ? issued - S : 0); kk < issued; ++kk)
-            mbar_wait_bounded(&full[kk % S], (kk / S) & 1u, sc);
-    cta_reduce_finalize<NQ>(accd, m, c, sc, slots, grid_bid(), grid_nblocks());
-}
-
-template <typename T, int NF, bool MEASURE>
-static cudaError_t launch_bulk(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
-                               double *slots, cudaStream_t s)
-{
-    static size_t configured = 0;  // dynamic shared memory the attribute allows so far
-    auto kern = fused_pass_bulk<T, NF, MEASURE>;
-    if (g.smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-        if (e != cudaSuccess) return e;
-        configured = g.smem;
-    }
-    kern<<<g.grid, 32 * (g.cwarps + 1), g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, g.stages, sc, slots);
-    return cudaGetLastError();
-}
-
 template <typename T, int NF, bool MEASURE, int D, int NT>
 static cudaError_t launch_ldg(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
                               double *slots, cudaStream_t s)
@@ -782,9 +601,6 @@ template <typename T, int NF>
 static cudaError_t launch_t(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
                             double *slots, bool measure_only, cudaStream_t s)
 {
-    if (g.variant == kVariantBulk)
-        return measure_only ? launch_bulk<T, NF, true>(m, fp, c, g, sc, slots, s)
-                            : launch_bulk<T, NF, false>(m, fp, c, g, sc, slots, s);
     const bool big = g.threads == 512;
     if (g.prefetch == 0) {
         if (big)

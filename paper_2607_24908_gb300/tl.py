@@ -69,6 +69,9 @@ _SIGS = {
                                                       ctypes.c_int, ctypes.c_int, ctypes.POINTER(tl_expansion),
                                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t]),
     "tl_state_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "tl_array_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t),
+                                       ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                       ctypes.POINTER(ctypes.c_size_t)]),
     "tl_lattice_destroy": (None, [ctypes.c_void_p]),
     "tl_set_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_potential)]),
     "tl_init_fluctuations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(tl_init_spec)]),
@@ -159,6 +162,13 @@ def tl_lattice_create_with_buffers(N: int, kIR: float, n_fields: int, dtype: int
 
 def tl_state_bytes(N: int, n_fields: int, dtype: int) -> int:
     return lib().tl_state_bytes(N, n_fields, dtype)
+
+
+def tl_array_layout(N: int, dtype: int):
+    """(elems, row_pitch, plane_pitch, origin) of one device field array."""
+    v = [ctypes.c_size_t() for _ in range(4)]
+    _check(lib().tl_array_layout(N, dtype, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def tl_lattice_destroy(h):

@@ -36,8 +36,14 @@ def test_spectrum_bins_and_state_bytes_without_gpu():
     import math
     for N in (8, 32, 48, 1024):
         assert tl.tl_spectrum_bins(N) == math.ceil(math.sqrt(3) * N / 2) + 1
-    assert tl.tl_state_bytes(1024, 2, tl.F32) == 4 * 2 * 1024 ** 3 * 4
-    assert tl.tl_state_bytes(32, 1, tl.F64) == 4 * 32 ** 3 * 8
+    # padded device layout: W = 16/sizeof ghost elements per row side, one ghost row per plane side
+    for N, dt, esz in ((1024, tl.F32, 4), (32, tl.F64, 8)):
+        W = 16 // esz
+        elems, pitch, plane, origin = tl.tl_array_layout(N, dt)
+        assert pitch == N + 2 * W and plane == (N + 2) * pitch and elems == N * plane and origin == pitch + W
+        assert (origin * esz) % 16 == 0 and (pitch * esz) % 16 == 0
+    assert tl.tl_state_bytes(1024, 2, tl.F32) == 4 * 2 * tl.tl_array_layout(1024, tl.F32)[0] * 4
+    assert tl.tl_state_bytes(32, 1, tl.F64) == 4 * tl.tl_array_layout(32, tl.F64)[0] * 8
 
 
 def test_create_without_gpu_fails_cleanly():

@@ -27,12 +27,16 @@ def test_noalloc_energies_match_lattice_energies(dtype, N, nf, expanding):
     npd = np.float32 if dtype == "f32" else np.float64
     phi, pi = white_noise_state(N, nf, seed=N + nf, phi0=(1.0, 0.2, 0.1), sigma_phi=1e-2, sigma_pi=1e-2)
     a = 1.3 if expanding else 1.0
+    import torch
     with T.Lattice(N, 0.5, nf, dtype, expanding, 1.0, 1.0, 1.0) as lat:
         lat.set_potential(1.0, 20.0, M2)
         lat.set_state(phi.astype(npd), pi.astype(npd), a, 0.1, False)
         ref = lat.energies().vector()
-        phip = [lat.device_ptr(f, 0) for f in range(nf)]
-        pip = [lat.device_ptr(f, 1) for f in range(nf)]
+        # the entry point takes dense caller-owned device arrays [z][y][x]
+        dev = [torch.from_numpy(np.ascontiguousarray(x[f].astype(npd))).cuda() for x in (phi, pi) for f in range(nf)]
+        torch.cuda.synchronize()
+        phip = [t.data_ptr() for t in dev[:nf]]
+        pip = [t.data_ptr() for t in dev[nf:]]
         ex = T.tl_expansion(int(expanding), 1.0, 1.0, 1.0)
         tol = 1e-12 if dtype == "f64" else 1e-5
         for _ in range(2):
