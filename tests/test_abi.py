@@ -70,7 +70,8 @@ def test_serving_job_generator_and_budget_arithmetic():
         assert j.N in (64, 128, 256, 384) and 1 <= j.n_fields <= 3 and j.q in (1.0, 100.0)
         assert 500 <= j.steps <= 5000 and j.steps % 100 == 0 and j.dtype in ("f32", "f64")
         esz = 4 if j.dtype == "f32" else 8
-        assert j.state_bytes() == 4 * j.n_fields * j.N ** 3 * esz
+        W = 16 // esz
+        assert j.state_bytes() == 4 * j.n_fields * j.N * (j.N + 2) * (j.N + 2 * W) * esz
         assert j.budget_bytes() > j.state_bytes()
     # mean inter-arrival ~ 1/rate
     gaps = np.diff([0.0] + arr)
