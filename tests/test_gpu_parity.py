@@ -334,3 +334,51 @@ def test_chaotic_regime_energies_and_spectra_within_one_percent(dtype):
         sel = (oc >= 100) & (oP >= 1e-6 * oP.max())
         assert sel.sum() > 10
         assert np.max(np.abs(P[sel] - oP[sel]) / oP[sel]) < 0.01
+
+
+# --- padded layout: caller-owned buffers, ghosts kept current ---------------------------
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_caller_buffers_and_ghost_cells(dtype):
+    """tl_lattice_create_with_buffers on torch-allocated padded arrays: after
+    init and several passes every ghost equals its periodic image, and the
+    results are bitwise those of a library-allocated lattice."""
+    import torch
+    N, nf = 24, 2
+    esz = 4 if dtype == "f32" else 8
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    elems, P, PP, origin = T.tl_array_layout(N, T.DTYPES[dtype])
+    W = 16 // esz
+    bufs = [torch.zeros(elems, dtype=tdt, device="cuda") for _ in range(4 * nf)]
+    ex = T.tl_expansion(1, 1.0, 1.0, 1.0)
+    h = T.tl_lattice_create_with_buffers(N, 0.5, nf, T.DTYPES[dtype], ex, 0, [b.data_ptr() for b in bufs])
+    try:
+        T.tl_set_potential(h, 1.0, 100.0, (0.0, 0.0, 0.0))
+        T.tl_init_fluctuations(h, 5, 1e-4, (3.0, 100.0, 0.0), (1.0, 0.0, 0.0))
+        T.tl_step(h, 7, 0.005, T.YOSHIDA4)
+        T.tl_energies(h)
+        torch.cuda.synchronize()
+        for f in range(nf):
+            for which in range(2):
+                ptr = T.tl_state_device_ptr(h, f, which)
+                b = next(b for b in bufs if b.data_ptr() + origin * esz == ptr)
+                a = b.view(N, N + 2, P)  # [z][row incl. ghosts][x incl. ghosts]
+                inner = a[:, 1:N + 1, W:W + N]
+                assert torch.equal(a[:, 1:N + 1, :W], inner[:, :, N - W:])     # left ghosts
+                assert torch.equal(a[:, 1:N + 1, W + N:], inner[:, :, :W])     # right ghosts
+                assert torch.equal(a[:, 0, W:W + N], inner[:, N - 1, :])       # row above
+                assert torch.equal(a[:, N + 1, W:W + N], inner[:, 0, :])       # row below
+                out = np.empty((N, N, N), np.float32 if dtype == "f32" else np.float64)
+                T.tl_get_state(h, f, which, out)
+                assert np.array_equal(out, inner.cpu().numpy())
+        with T.Lattice(N, 0.5, nf, dtype, True, 1.0, 1.0, 1.0) as lat:
+            lat.set_potential(1.0, 100.0, (0.0, 0.0, 0.0))
+            lat.init_fluctuations(5, A=1e-4, meff2=(3.0, 100.0, 0.0), phi0=(1.0, 0.0, 0.0))
+            lat.step(7, 0.005, "yoshida4")
+            for f in range(nf):
+                ref = lat.get(f, 0)
+                out = np.empty_like(ref)
+                T.tl_get_state(h, f, 0, out)
+                assert np.array_equal(out, ref)
+    finally:
+        T.tl_lattice_destroy(h)
