@@ -124,13 +124,15 @@ int tl_lattice_create_with_buffers(tl_lattice **out, int N, double kIR, int n_fi
 /* Device bytes tl_lattice_create would allocate for the field arrays. */
 size_t tl_state_bytes(int N, int n_fields, tl_dtype dtype);
 
-/* Device layout of one field array of a lattice.  Rows carry W = 16/sizeof
- * ghost elements on each side and every z-plane one ghost row above and below
- * (one-site ghost copies of the periodic neighbours, kept current by every
- * pass, so that a tile plus its halo is one in-bounds box): element (x, y, z)
- * is at origin + z plane_pitch + y row_pitch + x, with row_pitch = N + 2W,
- * plane_pitch = (N + 2) row_pitch, origin = row_pitch + W, and elems = N
- * plane_pitch elements per array.  Any output may be NULL. */
+/* Device layout of one field array of a lattice.  Every row carries W =
+ * 16/sizeof ghost elements on each side (x in [-W, 0) and [N, N + W)) and
+ * every z-plane one ghost row above and below: one-site ghost copies of the
+ * periodic neighbours, kept current by every pass, so that a tile plus its
+ * halo is one in-bounds box.  Element (x, y, z) is at
+ * origin + z plane_pitch + y row_pitch + x; rows start x = 0 on a 128-byte
+ * boundary (a left pad of 128 bytes) and row_pitch is a multiple of 128
+ * bytes; plane_pitch = (N + 2) row_pitch, origin = row_pitch + 128/sizeof,
+ * elems = N plane_pitch elements per array.  Any output may be NULL. */
 int tl_array_layout(int N, tl_dtype dtype, size_t *elems, size_t *row_pitch, size_t *plane_pitch, size_t *origin);
 
 void tl_lattice_destroy(tl_lattice *lat);

@@ -125,44 +125,24 @@ namespace {
 size_t n3_of(int N) { return (size_t)N * (size_t)N * (size_t)N; }
 
 // Padded array layout (see tl_internal.cuh): W = 16/esz ghost elements on
-// each side of a row, one ghost row on each side of a plane, no z ghosts.
+// each side of a row (the left ones inside a 128-byte pad so that x = 0 of
+// every row starts a 128-byte line), rows padded to a multiple of 128 bytes,
+// one ghost row on each side of a plane, no z ghosts.
 struct Layout {
-    long long W, pitch, pplane;
+    long long W, lpad, pitch, pplane;
     size_t elems, origin;
 };
 Layout layout_of(int N, size_t esz)
 {
     Layout l;
+    const long long line = (long long)(128 / esz);
     l.W = (long long)(16 / esz);
-    l.pitch = N + 2 * l.W;
+    l.lpad = line;
+    l.pitch = (l.lpad + N + l.W + line - 1) / line * line;
     l.pplane = (long long)(N + 2) * l.pitch;
     l.elems = (size_t)N * (size_t)l.pplane;
-    l.origin = (size_t)(l.pitch + l.W);
+    l.origin = (size_t)(l.pitch + l.lpad);
     return l;
-}
-
-// Bytes between consecutive field arrays beyond their size (TL_ARRAY_STAGGER,
-// rounded to 256 bytes; default 0).
-size_t array_stagger()
-{
-    const char *v = getenv("TL_ARRAY_STAGGER");
-    long b = v ? atol(v) : 0;
-    if (b < 0) b = 0;
-    return (size_t)((b + 255) / 256 * 256);
-}
-
-int check_dims(int N, double kIR, int n_fields, tl_dtype dtype, const tl_expansion *ex)
-{
-    if (N < 8 || N % 4 != 0 || N > 2048) return fail(TL_EINVAL, "N must be a multiple of 4 in [8, 2048], got %d", N);
-    if (!(kIR > 0.0) || !isfinite(kIR)) return fail(TL_EINVAL, "kIR must be positive and finite");
-    if (n_fields < 1 || n_fields > TL_MAX_FIELDS) return fail(TL_EINVAL, "n_fields must be 1..%d", TL_MAX_FIELDS);
-    if (dtype != TL_F32 && dtype != TL_F64) return fail(TL_EINVAL, "unknown dtype %d", (int)dtype);
-    if (ex && ex->expanding) {
-        if (!isfinite(ex->alpha)) return fail(TL_EINVAL, "alpha must be finite");
-        if (!(ex->a0 > 0.0)) return fail(TL_EINVAL, "a0 must be positive");
-        if (!(ex->fstar_over_mp > 0.0)) return fail(TL_EINVAL, "fstar_over_mp must be positive");
-    }
-    return TL_OK;
 }
 
 void refresh_model(tl_lattice *L)

@@ -32,9 +32,10 @@ struct Scalars {
 // Field arrays are addressed from their element (0, 0, 0) as
 // z * pplane + y * pitch + x.  A dense array has pitch = N, pplane = N^2;
 // the lattice's own arrays carry ghost copies (ghosts = 1): W = 16/sizeof(T)
-// elements left and right of every row and one row above and below every
-// z-plane, pitch = N + 2W, pplane = (N + 2) pitch, which every pass keeps
-// current for the sites it writes.
+// elements left and right of every row (x in [-W, 0) and [N, N + W)) and one
+// row above and below every z-plane, which every pass keeps current for the
+// sites it writes; rows are padded to a multiple of 128 bytes with x = 0 on a
+// 128-byte boundary, pplane = (N + 2) pitch.
 struct Model {
     int N;
     int nf;

@@ -37,11 +37,13 @@ def test_spectrum_bins_and_state_bytes_without_gpu():
     for N in (8, 32, 48, 1024):
         assert tl.tl_spectrum_bins(N) == math.ceil(math.sqrt(3) * N / 2) + 1
     # padded device layout: W = 16/sizeof ghost elements per row side, one ghost row per plane side
-    for N, dt, esz in ((1024, tl.F32, 4), (32, tl.F64, 8)):
+    for N, dt, esz in ((1024, tl.F32, 4), (32, tl.F64, 8), (40, tl.F32, 4)):
         W = 16 // esz
         elems, pitch, plane, origin = tl.tl_array_layout(N, dt)
-        assert pitch == N + 2 * W and plane == (N + 2) * pitch and elems == N * plane and origin == pitch + W
-        assert (origin * esz) % 16 == 0 and (pitch * esz) % 16 == 0
+        lpad = 128 // esz
+        assert pitch >= lpad + N + W and (pitch * esz) % 128 == 0
+        assert plane == (N + 2) * pitch and elems == N * plane and origin == pitch + lpad
+        assert (origin * esz) % 128 == 0
     assert tl.tl_state_bytes(1024, 2, tl.F32) == 4 * 2 * tl.tl_array_layout(1024, tl.F32)[0] * 4
     assert tl.tl_state_bytes(32, 1, tl.F64) == 4 * tl.tl_array_layout(32, tl.F64)[0] * 8
 
@@ -70,8 +72,9 @@ def test_serving_job_generator_and_budget_arithmetic():
         assert j.N in (64, 128, 256, 384) and 1 <= j.n_fields <= 3 and j.q in (1.0, 100.0)
         assert 500 <= j.steps <= 5000 and j.steps % 100 == 0 and j.dtype in ("f32", "f64")
         esz = 4 if j.dtype == "f32" else 8
-        W = 16 // esz
-        assert j.state_bytes() == 4 * j.n_fields * j.N * (j.N + 2) * (j.N + 2 * W) * esz
+        line = 128 // esz
+        pitch = -(-(line + j.N + 16 // esz) // line) * line
+        assert j.state_bytes() == 4 * j.n_fields * j.N * (j.N + 2) * pitch * esz
         assert j.budget_bytes() > j.state_bytes()
     # mean inter-arrival ~ 1/rate
     gaps = np.diff([0.0] + arr)

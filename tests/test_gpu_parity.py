@@ -362,12 +362,13 @@ def test_caller_buffers_and_ghost_cells(dtype):
             for which in range(2):
                 ptr = T.tl_state_device_ptr(h, f, which)
                 b = next(b for b in bufs if b.data_ptr() + origin * esz == ptr)
-                a = b.view(N, N + 2, P)  # [z][row incl. ghosts][x incl. ghosts]
-                inner = a[:, 1:N + 1, W:W + N]
-                assert torch.equal(a[:, 1:N + 1, :W], inner[:, :, N - W:])     # left ghosts
-                assert torch.equal(a[:, 1:N + 1, W + N:], inner[:, :, :W])     # right ghosts
-                assert torch.equal(a[:, 0, W:W + N], inner[:, N - 1, :])       # row above
-                assert torch.equal(a[:, N + 1, W:W + N], inner[:, 0, :])       # row below
+                a = b.view(N, N + 2, P)  # [z][row incl. ghost rows][padded row]
+                L0 = origin - P  # x = 0 within a padded row
+                inner = a[:, 1:N + 1, L0:L0 + N]
+                assert torch.equal(a[:, 1:N + 1, L0 - W:L0], inner[:, :, N - W:])       # left ghosts
+                assert torch.equal(a[:, 1:N + 1, L0 + N:L0 + N + W], inner[:, :, :W])   # right ghosts
+                assert torch.equal(a[:, 0, L0:L0 + N], inner[:, N - 1, :])              # row above
+                assert torch.equal(a[:, N + 1, L0:L0 + N], inner[:, 0, :])              # row below
                 out = np.empty((N, N, N), np.float32 if dtype == "f32" else np.float64)
                 T.tl_get_state(h, f, which, out)
                 assert np.array_equal(out, inner.cpu().numpy())
