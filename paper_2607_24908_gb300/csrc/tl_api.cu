@@ -145,6 +145,20 @@ Layout layout_of(int N, size_t esz)
     return l;
 }
 
+int check_dims(int N, double kIR, int n_fields, tl_dtype dtype, const tl_expansion *ex)
+{
+    if (N < 8 || N % 4 != 0 || N > 2048) return fail(TL_EINVAL, "N must be a multiple of 4 in [8, 2048], got %d", N);
+    if (!(kIR > 0.0) || !isfinite(kIR)) return fail(TL_EINVAL, "kIR must be positive and finite");
+    if (n_fields < 1 || n_fields > TL_MAX_FIELDS) return fail(TL_EINVAL, "n_fields must be 1..%d", TL_MAX_FIELDS);
+    if (dtype != TL_F32 && dtype != TL_F64) return fail(TL_EINVAL, "unknown dtype %d", (int)dtype);
+    if (ex && ex->expanding) {
+        if (!isfinite(ex->alpha)) return fail(TL_EINVAL, "alpha must be finite");
+        if (!(ex->a0 > 0.0)) return fail(TL_EINVAL, "a0 must be positive");
+        if (!(ex->fstar_over_mp > 0.0)) return fail(TL_EINVAL, "fstar_over_mp must be positive");
+    }
+    return TL_OK;
+}
+
 void refresh_model(tl_lattice *L)
 {
     Model &m = L->model;
