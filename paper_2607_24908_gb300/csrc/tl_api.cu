@@ -145,6 +145,16 @@ Layout layout_of(int N, size_t esz)
     return l;
 }
 
+// Bytes between consecutive field arrays beyond their size (TL_ARRAY_STAGGER,
+// rounded to 256 bytes; default 0).
+size_t array_stagger()
+{
+    const char *v = getenv("TL_ARRAY_STAGGER");
+    long b = v ? atol(v) : 0;
+    if (b < 0) b = 0;
+    return (size_t)((b + 255) / 256 * 256);
+}
+
 int check_dims(int N, double kIR, int n_fields, tl_dtype dtype, const tl_expansion *ex)
 {
     if (N < 8 || N % 4 != 0 || N > 2048) return fail(TL_EINVAL, "N must be a multiple of 4 in [8, 2048], got %d", N);
