@@ -1,5 +1,7 @@
 // Host runtime behind include/tl.h: lattice objects, the integrator schedule
 // (pass list), launches, state transfer, initial fields and spectra.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cufft.h>
 #include <math.h>
 #include <stdarg.h>
@@ -216,8 +218,62 @@ int finish_create(tl_lattice *L, int N, double kIR, int nf, tl_dtype dtype, cons
     return TL_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Encode the tensor maps of both buffer parities for the current tile shape:
+// 3-D (padded row, row incl. ghost rows, plane) over each array, box
+// (txt W + 2W) x (ty + 2) x 1.
+int ensure_tma_maps(tl_lattice *L)
+{
+    const tl::PassGeom &g = L->geom;
+    if (L->maps_txt == g.txt && L->maps_ty == g.ty) return TL_OK;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return fail(TL_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const size_t esz = L->esz;
+    const int W = (int)(16 / esz);
+    const Layout lay = layout_of(L->N, esz);
+    const cuuint64_t dims[3] = {(cuuint64_t)lay.pitch, (cuuint64_t)(L->N + 2), (cuuint64_t)L->N};
+    const cuuint64_t strides[2] = {(cuuint64_t)lay.pitch * esz, (cuuint64_t)lay.pplane * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)(g.txt * W + 2 * W), (cuuint32_t)(g.ty + 2), 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    for (int par = 0; par < 2; ++par)
+        for (int f = 0; f < L->nf; ++f)
+            for (int a = 0; a < 2; ++a) {
+                void *base = static_cast<char *>(L->buf[par][a][f]) - lay.origin * esz;
+                CUresult r = enc(&L->maps[par].map[2 * f + a],
+                                 esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base,
+                                 dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) return fail(TL_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+            }
+    L->maps_txt = g.txt;
+    L->maps_ty = g.ty;
+    return TL_OK;
+}
+
 int launch(tl_lattice *L, const PassCoef &c, bool measure_only)
 {
+    const tl::TmaMaps *maps = nullptr;
+    if (L->geom.variant == tl::kVariantTma) {
+        int rc = ensure_tma_maps(L);
+        if (rc) return rc;
+        maps = &L->maps[L->cur];
+    }
     FieldPtrs fp;
     for (int f = 0; f < TL_MAX_FIELDS; ++f) {
         fp.phi_in[f] = L->buf[L->cur][0][f];
@@ -225,7 +281,8 @@ int launch(tl_lattice *L, const PassCoef &c, bool measure_only)
         fp.phi_out[f] = L->buf[L->cur ^ 1][0][f];
         fp.pi_out[f] = L->buf[L->cur ^ 1][1][f];
     }
-    TL_CK(tl::launch_pass((int)L->dtype, L->model, fp, c, L->geom, L->d_sc, L->d_slots, measure_only, L->stream));
+    TL_CK(tl::launch_pass((int)L->dtype, L->model, fp, c, L->geom, L->d_sc, L->d_slots, measure_only, L->stream,
+                          maps));
     if (!measure_only) L->cur ^= 1;
     return TL_OK;
 }

@@ -299,6 +299,7 @@ int set_geometry(tl_lattice *L, const tl::PassTuning &t)
     }
     L->geom = g;
     L->tuning = t;
+    L->maps_txt = L->maps_ty = -1;  // re-encode tensor maps for the new tile shape
     return TL_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libtl.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -84,6 +85,13 @@ struct PassTuning {
     int txt;      // ldg: threads along x per tile row, 32 (default), 16 or 8
 };
 
+// Tensor maps of the input arrays of a TMA pass: [2 f + a], a = 0 phi, 1 pi,
+// each 3-D over the padded array (x incl. pads, rows incl. ghost rows, planes)
+// with the pass's tile-plus-halo box.
+struct TmaMaps {
+    CUtensorMap map[2 * kMaxFields];
+};
+
 // Launch geometry of the fused pass.
 struct PassGeom {
     int txt;  // threads along x (each owns VEC consecutive sites)
@@ -95,6 +103,7 @@ struct PassGeom {
     int cwarps;    // compute warps per CTA
     int stages;    // shared-memory ring depth (bulk variant)
     int prefetch;  // per-thread prefetch depth (ldg variant)
+    int lpad;      // TMA variant: padded-row index of x = 0 (128 bytes / element size)
     int threads;   // threads per CTA (ldg variant)
     size_t smem;   // dynamic shared memory per CTA
 };
@@ -123,7 +132,8 @@ cudaError_t launch_group(int dtype, int nf, const BatchJob *jobs, const unsigned
 
 // Enqueue one fused pass (measure_only: energies of the stored state, no writes).
 cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,
-                        Scalars *sc, double *slots, bool measure_only, cudaStream_t s);
+                        Scalars *sc, double *slots, bool measure_only, cudaStream_t s,
+                        const TmaMaps *maps = nullptr);
 
 // Record msg+detail as this thread's tl_last_error() text; returns code.
 int set_error(int code, const char *msg, const char *detail);

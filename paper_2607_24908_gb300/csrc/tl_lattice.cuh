@@ -27,6 +27,8 @@ struct tl_lattice {
     double *d_slots = nullptr;
     unsigned slots_cap = 0;       // CTA slots d_slots holds
     tl::PassTuning tuning{};      // launch parameters in use
+    tl::TmaMaps maps[2];          // tensor maps of the arrays of parity 0 / 1 (TMA variant)
+    int maps_txt = -1, maps_ty = -1;  // tile shape the maps were encoded for
     tl::PassGeom geom{};
     tl::Model model{};
     int sm_count = 0;

@@ -73,7 +73,10 @@ extern "C" int tl_energies_noalloc(int N, double kIR, int n_fields, tl_dtype dty
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(TL_ECUDA, "device query: ", cudaGetErrorString(e));
-    const tl::PassGeom g = tl::pass_geometry(N, dtype == TL_F32 ? 4 : 8, sms, n_fields, tl::default_tuning());
+    tl::PassTuning tune = tl::default_tuning();
+    tune.variant = tl::kVariantLdg;  // dense caller arrays have no ghost layer for tiled copies
+    tune.prefetch = 0;
+    const tl::PassGeom g = tl::pass_geometry(N, dtype == TL_F32 ? 4 : 8, sms, n_fields, tune);
     if (g.nblocks > kMaxSlotBlocks)
         return fail(TL_EINVAL, "lattice needs more reduction slots than the static scratch holds (max 16384 CTAs)");
 

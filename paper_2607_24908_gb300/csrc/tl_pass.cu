@@ -49,11 +49,6 @@ __global__ void set_background_kernel(Model m, Scalars *sc, double a, double b)
     for (int i = 0; i < kMaxQ; ++i) sc->E[i] = 0.0;
 }
 
-size_t bulk_smem_bytes(int txt, int ty, int W, int nf, int stages, int elem_bytes)
-{
-    return (size_t)stages * nf * 2 * (ty + 2) * (txt * W + 2 * W) * (size_t)elem_bytes;
-}
-
 PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTuning &t)
 {
     const int W = 16 / elem_bytes;
@@ -89,30 +84,36 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
         g.prefetch = (t.prefetch > 0 && g.threads == 256) ? 3 : 0;
         g.smem = (size_t)g.prefetch * nf * 2 * 256 * 16;
     }
+    g.lpad = 128 / elem_bytes;
     if (g.variant == kVariantTma) {
         // ring depth: as deep as fits two CTAs per SM (<= 113 KB each), at
-        // least 3 (two planes read + one in flight), at most kMaxStages.
+        // least 3 (two planes read + one in flight), at most 8; each stage
+        // holds 2 nf boxes of (ty + 2) x (txt W + 2W) elements in 128-byte
+        // aligned regions.
+        const size_t box = (size_t)(g.ty + 2) * (g.txt * W + 2 * W) * (size_t)elem_bytes;
+        const size_t region = (box + 127) / 128 * 128;
+        const size_t per_stage = (size_t)nf * 2 * region;
         int S = t.stages > 0 ? t.stages : 8;
         if (S > 8) S = 8;
-        while (S > 3 && bulk_smem_bytes(g.txt, g.ty, W, nf, S, elem_bytes) > (t.stages > 0 ? 227u : 113u) * 1024u) --S;
-        if (S < 3) S = 3;
+        const size_t cap = (t.stages > 0 ? 227u : 113u) * 1024u;
+        while (S > 3 && per_stage * S > cap) --S;
         g.stages = S;
-        g.smem = bulk_smem_bytes(g.txt, g.ty, W, nf, S, elem_bytes);
+        g.smem = per_stage * S;
     }
     return g;
 }
 
 cudaError_t launch_pass_f32(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
-                            double *slots, bool measure_only, cudaStream_t s);
+                            double *slots, bool measure_only, cudaStream_t s, const TmaMaps *maps);
 cudaError_t launch_pass_f64(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
-                            double *slots, bool measure_only, cudaStream_t s);
+                            double *slots, bool measure_only, cudaStream_t s, const TmaMaps *maps);
 
 cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,
-                        Scalars *sc, double *slots, bool measure_only, cudaStream_t s)
+                        Scalars *sc, double *slots, bool measure_only, cudaStream_t s, const TmaMaps *maps)
 {
     if (m.nf < 1 || m.nf > kMaxFields) return cudaErrorInvalidValue;
-    return dtype == TL_F32 ? launch_pass_f32(m, fp, c, g, sc, slots, measure_only, s)
-                           : launch_pass_f64(m, fp, c, g, sc, slots, measure_only, s);
+    return dtype == TL_F32 ? launch_pass_f32(m, fp, c, g, sc, slots, measure_only, s, maps)
+                           : launch_pass_f64(m, fp, c, g, sc, slots, measure_only, s, maps);
 }
 
 cudaError_t launch_group_f32(int nf, const BatchJob *jobs, const unsigned *first_item, int njobs, unsigned total,

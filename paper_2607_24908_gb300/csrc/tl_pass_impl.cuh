@@ -18,6 +18,7 @@
 // come through L1/L2 (fused_pass_ldg).  HBM sees each array read once and
 // written once per pass: 4 sizeof(T) bytes per site per field.
 #pragma once
+#include <cuda.h>
 #include <math.h>
 
 #include "tl_internal.cuh"
@@ -582,6 +583,211 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
 }
 
+
+// ---- variant 2: tiled TMA staging on the ghost-padded layout ---------------------
+// Warps 0..CW-1 compute, warp CW produces.  A CTA owns a tile of txt W x ty
+// sites and a chunk of z-planes.  For every plane its producer lane issues one
+// 3-D tensor copy per array (cp.async.bulk.tensor: a box of txt W + 2W by ty + 2
+// sites and one plane, starting at the tile's left ghost column and the row
+// above it; with the ghost layer the box never wraps) into a ring of S stages,
+// completing on the stage's "full" mbarrier; consumers release a stage on its
+// "empty" mbarrier once they are done with it.  Consumers read the centre of
+// plane z+1 and the halo of plane z from shared memory and run the same
+// per-site update as the register-streaming variant.
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+constexpr int kMaxStages = 8;
+
+template <typename T, int NF, bool MEASURE>
+__global__ void __launch_bounds__(288, 2) fused_pass_tma(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
+                                                         int S, int lpad, const __grid_constant__ TmaMaps maps,
+                                                         Scalars *sc, double *slots)
+{
+    constexpr int W = Vec<T>::W;
+    constexpr int NQ = 2 * NF + 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+    __shared__ volatile int s_failed;
+
+    const int N = m.N;
+    const int tid = threadIdx.x;
+    const int CW = (blockDim.x >> 5) - 1;
+    const bool producer = (tid >> 5) == CW;
+    const int x_tile = blockIdx.x * txt * W, y_tile = blockIdx.y * ty;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(z0 + zc, N);
+    const int K = (z1 - z0) + 2;  // planes z0-1 .. z1
+    const int rowe = txt * W + 2 * W;
+    const uint32_t box_bytes = (uint32_t)((ty + 2) * rowe * sizeof(T));
+    const uint32_t region = (box_bytes + 127u) & ~127u;  // 128-byte aligned stage regions
+    auto arr = [&](int s, int f, int a) -> T * {
+        return reinterpret_cast<T *>(smem_raw + (size_t)((s * NF + f) * 2 + a) * region);
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CW);
+        }
+        s_failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    double accd[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) accd[i] = 0.0;
+    int issued = 0;
+
+    if (producer) {
+        if ((tid & 31) == 0) {
+            for (int k = 0; k < K; ++k) {
+                const int s = k % S;
+                if (k >= S && !mbar_wait_bounded(&empty[s], ((k / S) - 1) & 1u, sc)) {
+                    s_failed = 1;
+                    break;
+                }
+                if (s_failed) break;
+                const int zg = (z0 - 1 + k + N) % N;
+                mbar_arrive_expect_tx(&full[s], (uint32_t)(NF * 2) * box_bytes);
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+                        tma_load_3d(arr(s, f, a), &maps.map[2 * f + a], lpad + x_tile - W, y_tile, zg, &full[s]);
+                issued = k + 1;
+            }
+        }
+    } else {
+        const int lane = tid & 31;
+        const int tx = tid % txt, tyi = tid / txt;
+        const int x0 = x_tile + tx * W;
+        const int y = y_tile + tyi;
+        const bool active = (tyi < ty) && (x0 < N) && (y < N);
+        const Coefs<T, NF> k(m, c, sc);
+        const int ctr = (tyi + 1) * rowe + (tx + 1) * W;
+        const size_t P = (size_t)m.pitch, PP = (size_t)m.pplane;
+        T *pho[NF], *pio[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            pho[f] = static_cast<T *>(fp.phi_out[f]);
+            pio[f] = static_cast<T *>(fp.pi_out[f]);
+        }
+        T zm[NF][W], cu[NF][W], zp[NF][W], pc[NF][W], pn[NF][W];
+        T acc[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) acc[i] = (T)0;
+        auto centre = [&](int kk, T (&ph)[NF][W], T (&pp)[NF][W]) {
+            const int s = kk % S;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                T a[W];
+                load_vec_s(arr(s, f, 0) + ctr, a);
+                load_vec_s(arr(s, f, 1) + ctr, pp[f]);
+#pragma unroll
+                for (int j = 0; j < W; ++j) ph[f][j] = fma_t(k.drift, pp[f][j], a[j]);
+            }
+        };
+        auto release = [&](int kk) {
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[kk % S])) : "memory");
+        };
+        bool ok = true;
+        if (active) {
+            ok = mbar_wait_bounded(&full[0], 0u, sc);
+            centre(0, zm, pn);
+            ok = ok && mbar_wait_bounded(&full[1 % S], (1 / S) & 1u, sc);
+            centre(1, cu, pc);
+        }
+        if (!ok) s_failed = 1;
+        release(0);
+        for (int z = z0; z < z1 && !s_failed; ++z) {
+            const int kz = z - z0 + 1;
+            if (active) {
+                if (!mbar_wait_bounded(&full[(kz + 1) % S], ((kz + 1) / S) & 1u, sc)) s_failed = 1;
+                centre(kz + 1, zp, pn);
+                const int s0 = kz % S;
+                T ym[NF][W], yp[NF][W], xlv[NF], xrv[NF];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    const T *ph = arr(s0, f, 0), *pp = arr(s0, f, 1);
+                    T a[W], b[W];
+                    load_vec_s(ph + ctr - rowe, a);
+                    load_vec_s(pp + ctr - rowe, b);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) ym[f][j] = fma_t(k.drift, b[j], a[j]);
+                    load_vec_s(ph + ctr + rowe, a);
+                    load_vec_s(pp + ctr + rowe, b);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) yp[f][j] = fma_t(k.drift, b[j], a[j]);
+                    xlv[f] = fma_t(k.drift, pp[ctr - 1], ph[ctr - 1]);
+                    xrv[f] = fma_t(k.drift, pp[ctr + W], ph[ctr + W]);
+                }
+                T pnew[NF][W];
+                site_update<T, NF, W>(k, cu, zm, zp, ym, yp, xlv, xrv, pc, pnew, acc);
+                if (!MEASURE) {
+                    const size_t pz = (size_t)z * PP;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        store_vec_cs(pho[f] + pz + (size_t)y * P + x0, cu[f]);
+                        store_vec_cs(pio[f] + pz + (size_t)y * P + x0, pnew[f]);
+                    }
+                    if (m.ghosts) store_ghosts<T, NF, W>(pho, pio, cu, pnew, pz, x0, y, N, (long long)P);
+                }
+                if (((z - z0) & 15) == 15) {
+#pragma unroll
+                    for (int i = 0; i < NQ; ++i) {
+                        accd[i] += (double)acc[i];
+                        acc[i] = (T)0;
+                    }
+                }
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        zm[f][j] = cu[f][j];
+                        cu[f][j] = zp[f][j];
+                        pc[f][j] = pn[f][j];
+                    }
+            }
+            release(kz);
+        }
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
+    }
+    __syncthreads();
+    // After a timeout, wait (bounded) for the copies still in flight before the
+    // CTA's shared memory goes away.
+    if (s_failed && producer && (tid & 31) == 0)
+        for (int kk = (issued > S ? issued - S : 0); kk < issued; ++kk)
+            mbar_wait_bounded(&full[kk % S], (kk / S) & 1u, sc);
+    cta_reduce_finalize<NQ>(accd, m, c, sc, slots, grid_bid(), grid_nblocks());
+}
+
+template <typename T, int NF, bool MEASURE>
+static cudaError_t launch_tma(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,
+                              const TmaMaps &maps, Scalars *sc, double *slots, cudaStream_t s)
+{
+    static size_t configured = 0;
+    auto kern = fused_pass_tma<T, NF, MEASURE>;
+    if (g.smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+        if (e != cudaSuccess) return e;
+        configured = g.smem;
+    }
+    kern<<<g.grid, 32 * (g.cwarps + 1), g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, g.stages, g.lpad, maps, sc, slots);
+    return cudaGetLastError();
+}
+
 template <typename T, int NF, bool MEASURE, int D, int NT>
 static cudaError_t launch_ldg(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
                               double *slots, cudaStream_t s)
@@ -599,8 +805,13 @@ static cudaError_t launch_ldg(const Model &m, const FieldPtrs &fp, const PassCoe
 
 template <typename T, int NF>
 static cudaError_t launch_t(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
-                            double *slots, bool measure_only, cudaStream_t s)
+                            double *slots, bool measure_only, cudaStream_t s, const TmaMaps *maps)
 {
+    if (g.variant == kVariantTma) {
+        if (!maps || !m.ghosts) return cudaErrorInvalidValue;
+        return measure_only ? launch_tma<T, NF, true>(m, fp, c, g, *maps, sc, slots, s)
+                            : launch_tma<T, NF, false>(m, fp, c, g, *maps, sc, slots, s);
+    }
     const bool big = g.threads == 512;
     if (g.prefetch == 0) {
         if (big)
