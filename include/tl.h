@@ -284,15 +284,51 @@ int tl_batch_step(tl_batch *batch, int n, double dt, tl_integrator integrator);
 
 void tl_batch_destroy(tl_batch *batch);
 
-/* Time candidate launch geometries of the fused pass on this lattice (the
- * z-planes per CTA of the register-streaming kernel, from 4 to the whole
- * lattice) with passes whose kick and drift coefficients are zero, which
+/* Time candidate launch shapes of the fused pass on this lattice (both
+ * kinds of tl_pass_config: z-planes per CTA from 4 to the whole lattice and
+ * the tile rows of the streaming kernel, the warps and ring depths of the TMA
+ * kernel) with passes whose kick and drift coefficients are zero, which
  * rewrite the state unchanged, and keep the fastest.  Results are cached per
  * (N, n_fields, dtype, SM count) for the process and, if the environment
  * variable TL_TUNE_FILE names a file, appended there and reused by later
  * processes.  best_ms_per_pass (may be NULL) receives the winner's time.
  * Synchronises the lattice stream.  Errors: TL_ESTATE (in a batch), TL_ECUDA. */
 int tl_autotune(tl_lattice *lat, double *best_ms_per_pass);
+
+/* Launch shape of the fused pass (the one kernel a step launches per
+ * (sub)step, Sec. 4's kick and drift with the energy sums of Sec. 3.2).
+ * Both kinds compute every site with the same operations in the same order,
+ * so fields agree bitwise between them; only the energy sums, whose order
+ * follows the CTA tiles, differ by rounding (and through a'' the fields of an
+ * expanding run).
+ *   TL_PASS_STREAM  each thread streams its column of sites through z-planes
+ *                   in registers, neighbour rows from L1/L2 (the shape the
+ *                   batched launch runs);
+ *   TL_PASS_TMA     a producer warp stages tile-plus-halo boxes of each plane
+ *                   in shared memory with tensor copies (cp.async.bulk.tensor)
+ *                   through a ring of mbarrier-guarded stages; compute warps
+ *                   read neighbours from the stage. */
+typedef enum { TL_PASS_STREAM = 0, TL_PASS_TMA = 1 } tl_pass_kind;
+
+typedef struct {
+    int kind;    /* tl_pass_kind */
+    int warps;   /* TMA: compute warps per CTA, 7 (two CTAs per SM) or 15 (one); 0 = 7 */
+    int stages;  /* TMA: ring depth 3..8; 0 = as deep as the shared memory allows */
+    int z_chunk; /* z-planes per CTA, 1..N; 0 = automatic (at least ~8 CTAs per SM) */
+    int tile_x;  /* STREAM: threads along a tile row, 8, 16 or 32; 0 = 32 */
+    int threads; /* STREAM: threads per CTA, 256 or 512; 0 = 256 */
+} tl_pass_config;
+
+/* Set the launch shape of lat's fused pass (takes effect at the next launch;
+ * the lattice's state is untouched).  Values out of range are TL_EINVAL;
+ * TL_ESTATE while the lattice is in a batch.  May synchronise the lattice
+ * stream (to grow its reduction slots).  A new lattice starts on TL_PASS_TMA
+ * for N >= 128 and on TL_PASS_STREAM below; the environment variable
+ * TL_PASS_VARIANT=tma|ldg overrides that default at creation. */
+int tl_set_pass_config(tl_lattice *lat, const tl_pass_config *cfg);
+
+/* The launch shape lat runs now, with automatic values resolved. */
+int tl_get_pass_config(const tl_lattice *lat, tl_pass_config *cfg);
 
 /* Message for the last error on this thread ("" if none). */
 const char *tl_last_error(void);

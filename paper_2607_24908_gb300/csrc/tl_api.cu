@@ -53,11 +53,12 @@ int fail(int code, const char *fmt, ...)
 
 }  // namespace
 
-tl::PassTuning tl::default_tuning()
+tl::PassTuning tl::default_tuning(int N)
 {
-    tl::PassTuning t{tl::kVariantLdg, 8, 0, 0, 0, 256, 0};
+    tl::PassTuning t{N >= 256 ? tl::kVariantTma : tl::kVariantLdg, 7, 0, 0, 0, 256, 0};
     const char *v = getenv("TL_PASS_VARIANT");
     if (v && strcmp(v, "tma") == 0) t.variant = tl::kVariantTma;
+    if (v && strcmp(v, "ldg") == 0) t.variant = tl::kVariantLdg;
     if ((v = getenv("TL_PREFETCH"))) t.prefetch = atoi(v);
     if ((v = getenv("TL_LDG_THREADS"))) t.threads = atoi(v);
     if ((v = getenv("TL_LDG_TXT"))) t.txt = atoi(v);
@@ -207,7 +208,7 @@ int finish_create(tl_lattice *L, int N, double kIR, int nf, tl_dtype dtype, cons
     int dev = 0;
     TL_CK(cudaGetDevice(&dev));
     TL_CK(cudaDeviceGetAttribute(&L->sm_count, cudaDevAttrMultiProcessorCount, dev));
-    L->tuning = tl::default_tuning();
+    L->tuning = tl::default_tuning(N);
     L->geom = tl::pass_geometry(N, (int)L->esz, L->sm_count, nf, L->tuning);
     TL_CK(cudaMalloc(&L->d_sc, sizeof(Scalars)));
     TL_CK(cudaMemset(L->d_sc, 0, sizeof(Scalars)));
@@ -354,6 +355,23 @@ int shared_plan(int N, cufftType type, cufftHandle *out)
 }  // namespace
 
 int tl::lattice_launch(tl_lattice *L, const PassCoef &c, bool measure_only) { return launch(L, c, measure_only); }
+
+int tl::set_geometry(tl_lattice *L, const PassTuning &t)
+{
+    const PassGeom g = pass_geometry(L->N, (int)L->esz, L->sm_count, L->nf, t);
+    if (g.nblocks > L->slots_cap) {
+        double *p = nullptr;
+        TL_CK(cudaStreamSynchronize(L->stream));
+        TL_CK(cudaMalloc(&p, sizeof(double) * kMaxQ * g.nblocks));
+        cudaFree(L->d_slots);
+        L->d_slots = p;
+        L->slots_cap = g.nblocks;
+    }
+    L->geom = g;
+    L->tuning = t;
+    L->maps_txt = L->maps_ty = -1;  // re-encode tensor maps for the new tile shape
+    return TL_OK;
+}
 
 extern "C" {
 
@@ -602,6 +620,49 @@ int tl_state_device_ptr(tl_lattice *L, int field, int which, void **dev_ptr)
     if (rc) return rc;
     if (!dev_ptr) return fail(TL_EINVAL, "NULL dev_ptr");
     *dev_ptr = L->buf[L->cur][which][field];
+    return TL_OK;
+}
+
+int tl_set_pass_config(tl_lattice *L, const tl_pass_config *cfg)
+{
+    g_err[0] = 0;
+    if (!L || !cfg) return fail(TL_EINVAL, "NULL argument");
+    if (L->batch_refs > 0) return fail(TL_ESTATE, "lattice is part of a batch");
+    if (cfg->kind != TL_PASS_STREAM && cfg->kind != TL_PASS_TMA) return fail(TL_EINVAL, "unknown pass kind %d", cfg->kind);
+    if (cfg->z_chunk < 0 || cfg->z_chunk > L->N) return fail(TL_EINVAL, "z_chunk must be in 0..N");
+    tl::PassTuning t{tl::kVariantLdg, 7, 0, cfg->z_chunk, 0, 256, 0};
+    if (cfg->kind == TL_PASS_TMA) {
+        if (cfg->warps != 0 && cfg->warps != 7 && cfg->warps != 15) return fail(TL_EINVAL, "TMA warps must be 0, 7 or 15");
+        if (cfg->stages != 0 && (cfg->stages < 3 || cfg->stages > 8))
+            return fail(TL_EINVAL, "TMA stages must be 0 or 3..8");
+        if (cfg->tile_x != 0 || cfg->threads != 0) return fail(TL_EINVAL, "tile_x and threads apply to TL_PASS_STREAM");
+        t.variant = tl::kVariantTma;
+        t.cwarps = cfg->warps ? cfg->warps : 7;
+        t.stages = cfg->stages;
+    } else {
+        if (cfg->tile_x != 0 && cfg->tile_x != 8 && cfg->tile_x != 16 && cfg->tile_x != 32)
+            return fail(TL_EINVAL, "tile_x must be 0, 8, 16 or 32");
+        if (cfg->threads != 0 && cfg->threads != 256 && cfg->threads != 512)
+            return fail(TL_EINVAL, "threads must be 0, 256 or 512");
+        if (cfg->warps != 0 || cfg->stages != 0) return fail(TL_EINVAL, "warps and stages apply to TL_PASS_TMA");
+        t.txt = cfg->tile_x;
+        t.threads = cfg->threads ? cfg->threads : 256;
+    }
+    return tl::set_geometry(L, t);
+}
+
+int tl_get_pass_config(const tl_lattice *L, tl_pass_config *cfg)
+{
+    g_err[0] = 0;
+    if (!L || !cfg) return fail(TL_EINVAL, "NULL argument");
+    const tl::PassGeom &g = L->geom;
+    const bool tma = g.variant == tl::kVariantTma;
+    cfg->kind = tma ? TL_PASS_TMA : TL_PASS_STREAM;
+    cfg->warps = tma ? g.cwarps : 0;
+    cfg->stages = tma ? g.stages : 0;
+    cfg->z_chunk = g.zc;
+    cfg->tile_x = tma ? 0 : g.txt;
+    cfg->threads = tma ? 0 : g.threads;
     return TL_OK;
 }
 

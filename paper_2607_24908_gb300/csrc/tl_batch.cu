@@ -142,12 +142,19 @@ int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_s
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
         if (!lats[i]) return tl::fail(TL_EINVAL, "lattice %d is NULL", i);
-        if (lats[i]->geom.variant != tl::kVariantLdg || lats[i]->geom.threads != 256)
-            return tl::fail(TL_EINVAL, "lattice %d uses a launch shape the batched kernel does not run "
-                                       "(it needs the register-streaming pass with 256-thread CTAs)", i);
         if (lats[i]->dtype != lats[0]->dtype) return tl::fail(TL_EINVAL, "all lattices of a batch share one dtype");
         for (int k = 0; k < i; ++k)
             if (lats[k] == lats[i]) return tl::fail(TL_EINVAL, "lattice %d appears twice", i);
+    }
+    // the grouped kernel runs the register-streaming tiles with 256-thread
+    // CTAs: members on another shape move to it (and keep it afterwards)
+    for (int i = 0; i < n; ++i) {
+        tl_lattice *L = lats[i];
+        if (L->geom.variant != tl::kVariantLdg || L->geom.threads != 256 || L->geom.prefetch != 0) {
+            const tl::PassTuning t{tl::kVariantLdg, 7, 0, L->tuning.zc, 0, 256, L->tuning.txt};
+            int rc = tl::set_geometry(L, t);
+            if (rc) return rc;
+        }
     }
     tl_batch *B = new (std::nothrow) tl_batch();
     if (!B) return tl::fail(TL_ENOMEM, "host allocation failed");
@@ -266,10 +273,16 @@ void load_tune_file()
     if (!path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    int N, nf, dt, sms, var, zc, pf, th, txt;
+    // one entry per line: N fields dtype SMs variant warps stages zc prefetch threads txt ms
+    int N, nf, dt, sms, var, cw, st, zc, pf, th, txt;
     double ms;
-    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %lf", &N, &nf, &dt, &sms, &var, &zc, &pf, &th, &txt, &ms) == 10) {
-        tl::PassTuning t{var, 8, 0, zc, pf, th, txt};
+    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %lf", &N, &nf, &dt, &sms, &var, &cw, &st, &zc, &pf, &th, &txt,
+                  &ms) == 12) {
+        const bool ok = (var == tl::kVariantLdg || var == tl::kVariantTma) && (cw == 7 || cw == 15) &&
+                        (st == 0 || (st >= 3 && st <= 8)) && zc >= 0 && zc <= N && (pf == 0 || pf == 3) &&
+                        (th == 256 || th == 512) && (txt == 0 || txt == 8 || txt == 16 || txt == 32);
+        if (!ok) continue;  // not an entry this library wrote
+        tl::PassTuning t{var, cw, st, zc, pf, th, txt};
         g_tune[TuneKey(N, nf, dt, sms)] = TuneVal{t, ms};
     }
     fclose(f);
@@ -281,26 +294,9 @@ void save_tune_entry(const TuneKey &k, const TuneVal &v)
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%d %d %d %d %d %d %d %d %d %.6f\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
-            v.t.variant, v.t.zc, v.t.prefetch, v.t.threads, v.t.txt, v.ms);
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %.6f\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+            std::get<3>(k), v.t.variant, v.t.cwarps, v.t.stages, v.t.zc, v.t.prefetch, v.t.threads, v.t.txt, v.ms);
     fclose(f);
-}
-
-int set_geometry(tl_lattice *L, const tl::PassTuning &t)
-{
-    tl::PassGeom g = tl::pass_geometry(L->N, (int)L->esz, L->sm_count, L->nf, t);
-    if (g.nblocks > L->slots_cap) {
-        double *p = nullptr;
-        TB_CK(cudaStreamSynchronize(L->stream));
-        TB_CK(cudaMalloc(&p, sizeof(double) * tl::kMaxQ * g.nblocks));
-        cudaFree(L->d_slots);
-        L->d_slots = p;
-        L->slots_cap = g.nblocks;
-    }
-    L->geom = g;
-    L->tuning = t;
-    L->maps_txt = L->maps_ty = -1;  // re-encode tensor maps for the new tile shape
-    return TL_OK;
 }
 
 }  // namespace
@@ -317,17 +313,24 @@ extern "C" int tl_autotune(tl_lattice *L, double *best_ms_per_pass)
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
             if (best_ms_per_pass) *best_ms_per_pass = it->second.ms;
-            return set_geometry(L, it->second.t);
+            return tl::set_geometry(L, it->second.t);
         }
     }
     // candidates: the register-streaming pass with 256-thread CTAs (the shape
     // the batched launch runs), tile rows of 32, 16 or 8 threads, and z-chunks
-    // from 4 planes to the whole lattice, plus the automatic choice
+    // from 4 planes to the whole lattice, plus the automatic choice; the TMA
+    // pass with 7 or 15 compute warps, the deepest ring that fits and the same
+    // z-chunks
     std::vector<tl::PassTuning> cands;
-    cands.push_back(tl::PassTuning{tl::kVariantLdg, 8, 0, 0, 0, 256, 0});
+    cands.push_back(tl::PassTuning{tl::kVariantLdg, 7, 0, 0, 0, 256, 0});
     for (int txt : {32, 16, 8})
         for (int zc = 4; zc <= L->N && zc <= 256; zc *= 2)
-            cands.push_back(tl::PassTuning{tl::kVariantLdg, 8, 0, zc, 0, 256, txt});
+            cands.push_back(tl::PassTuning{tl::kVariantLdg, 7, 0, zc, 0, 256, txt});
+    for (int cw : {7, 15}) {
+        cands.push_back(tl::PassTuning{tl::kVariantTma, cw, 0, 0, 0, 256, 0});
+        for (int zc = 4; zc <= L->N && zc <= 256; zc *= 2)
+            cands.push_back(tl::PassTuning{tl::kVariantTma, cw, 0, zc, 0, 256, 0});
+    }
     const tl::PassTuning saved = L->tuning;
     cudaEvent_t e0, e1;
     TB_CK(cudaEventCreate(&e0));
@@ -338,7 +341,7 @@ extern "C" int tl_autotune(tl_lattice *L, double *best_ms_per_pass)
     tl::PassTuning best_t = saved;
     int rc = TL_OK;
     for (const auto &t : cands) {
-        if ((rc = set_geometry(L, t))) break;
+        if ((rc = tl::set_geometry(L, t))) break;
         for (int i = 0; i < 2 && rc == TL_OK; ++i) rc = tl::lattice_launch(L, ident, false);
         if (rc) break;
         cudaEventRecord(e0, L->stream);
@@ -360,10 +363,10 @@ extern "C" int tl_autotune(tl_lattice *L, double *best_ms_per_pass)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) {
-        set_geometry(L, saved);
+        tl::set_geometry(L, saved);
         return rc;
     }
-    rc = set_geometry(L, best_t);
+    rc = tl::set_geometry(L, best_t);
     if (rc) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -77,7 +77,7 @@ constexpr int kVariantTma = 1;
 // Tunable launch parameters of the fused pass (0 = choose automatically).
 struct PassTuning {
     int variant;  // kVariantLdg or kVariantTma
-    int cwarps;   // bulk: compute warps per CTA (4 or 8; one producer warp is added)
+    int cwarps;   // tma: compute warps per CTA (7 or 15; one producer warp is added)
     int stages;   // bulk: shared-memory ring depth in z-planes (3..8)
     int zc;       // z-planes per CTA
     int prefetch; // ldg: planes prefetched per thread with cp.async (0 or 3)
@@ -112,7 +112,9 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
 
 // Tuning from the environment (TL_PASS_VARIANT=ldg|bulk, TL_PREFETCH, TL_LDG_THREADS, TL_LDG_TXT,
 // TL_BULK_WARPS, TL_BULK_STAGES, TL_PASS_ZC), else the built-in defaults.
-PassTuning default_tuning();
+// Launch shape a new lattice of side N starts with (TMA from N = 256 up,
+// where it measured faster than the streaming pass).
+PassTuning default_tuning(int N);
 
 // One lattice of a batched (grouped) launch: its model, fields for this pass,
 // scalars, reduction slots and its own launch geometry.

@@ -45,4 +45,7 @@ int lattice_launch(tl_lattice *L, const PassCoef &c, bool measure_only);
 int fail(int code, const char *fmt, ...);
 // Coefficients of the n P + 1 passes of n steps (false: unknown integrator).
 bool pass_schedule(int n, double dt, int integrator, std::vector<PassCoef> &out);
+// Switch a lattice to launch shape t (grows its reduction slots if needed and
+// re-encodes tensor maps at the next TMA launch).
+int set_geometry(tl_lattice *L, const PassTuning &t);
 }  // namespace tl

@@ -55,7 +55,7 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
     PassGeom g;
     const int per_row = N / W;  // N % 4 == 0 is required, so W | N
     g.variant = t.variant;
-    g.cwarps = (t.variant == kVariantTma) ? (t.cwarps == 4 ? 4 : 8) : 8;
+    g.cwarps = (t.variant == kVariantTma) ? (t.cwarps == 15 ? 15 : 7) : 8;
     // CTAs of whole warps (the CTA reduction needs them) whose compute threads
     // are laid over a tile of txt x ty threads; leftover threads idle.
     g.threads = (t.variant == kVariantLdg && t.threads == 512) ? 512 : 256;
@@ -95,7 +95,8 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
         const size_t per_stage = (size_t)nf * 2 * region;
         int S = t.stages > 0 ? t.stages : 8;
         if (S > 8) S = 8;
-        const size_t cap = (t.stages > 0 ? 227u : 113u) * 1024u;
+        // two CTAs per SM for 7 compute warps, one for 15
+        const size_t cap = (t.stages > 0 || g.cwarps > 7 ? 227u : 113u) * 1024u;
         while (S > 3 && per_stage * S > cap) --S;
         g.stages = S;
         g.smem = per_stage * S;

@@ -234,7 +234,7 @@ template <int NQ>
 __device__ __forceinline__ void cta_reduce_finalize(const double (&accd)[NQ], const Model &m, const PassCoef &c,
                                                     Scalars *sc, double *slots, unsigned bid, unsigned nblocks)
 {
-    __shared__ double red[16][NQ];
+    __shared__ double red[32][NQ];
     __shared__ bool last;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -289,14 +289,20 @@ __device__ __forceinline__ unsigned grid_nblocks() { return gridDim.x * gridDim.
 // Ghost copies of this thread's W output sites: a site in the first or last
 // W columns also goes to the right or left ghost columns, a site in the first
 // or last row to the ghost row below or above the plane (corners not needed:
-// the 7-point stencil never reads them).
+// the 7-point stencil never reads them).  Column ghosts are written as whole
+// 32-byte sectors (the ghost word plus the unused pad word beside it) so that
+// the memory system never has to merge a partial sector.
 template <typename T, int NF, int W>
 __device__ __forceinline__ void store_ghosts(T *const (&pho)[NF], T *const (&pio)[NF], const T (&ph)[NF][W],
                                              const T (&pp)[NF][W], size_t pz, int x0, int y, int N, long long P)
 {
     long long dx = 0, dy = 0;
-    if (x0 == 0) dx = N;                  // right ghost columns
-    else if (x0 + W == N) dx = -(long long)N;
+    bool left = false;
+    if (x0 == 0) dx = N;  // right ghost columns [N, N + W), pad [N + W, N + 2W)
+    else if (x0 + W == N) {
+        dx = -(long long)N;  // left ghost columns [-W, 0), pad [-2W, -W)
+        left = true;
+    }
     if (y == 0) dy = (long long)N * P;    // ghost row after the last row
     else if (y == N - 1) dy = -(long long)N * P;
     if (dx == 0 && dy == 0) return;
@@ -304,8 +310,11 @@ __device__ __forceinline__ void store_ghosts(T *const (&pho)[NF], T *const (&pio
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         if (dx) {
-            store_vec_cs(pho[f] + base + dx, ph[f]);
-            store_vec_cs(pio[f] + base + dx, pp[f]);
+            const long long o = (long long)base + dx;
+            store_vec_cs(pho[f] + o, ph[f]);
+            store_vec_cs(pio[f] + o, pp[f]);
+            store_vec_cs(pho[f] + (left ? o - W : o + W), ph[f]);  // fill the rest of the sector
+            store_vec_cs(pio[f] + (left ? o - W : o + W), pp[f]);
         }
         if (dy) {
             store_vec_cs(pho[f] + base + dy, ph[f]);
@@ -606,8 +615,8 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 
 constexpr int kMaxStages = 8;
 
-template <typename T, int NF, bool MEASURE>
-__global__ void __launch_bounds__(288, 2) fused_pass_tma(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
+template <typename T, int NF, bool MEASURE, int NTHR>
+__global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
                                                          int S, int lpad, const __grid_constant__ TmaMaps maps,
                                                          Scalars *sc, double *slots)
 {
@@ -616,12 +625,26 @@ __global__ void __launch_bounds__(288, 2) fused_pass_tma(Model m, FieldPtrs fp, 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
     __shared__ volatile int s_failed;
+    __shared__ int s_warps;
 
     const int N = m.N;
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int CW = (blockDim.x >> 5) - 1;
     const bool producer = (tid >> 5) == CW;
     const int x_tile = blockIdx.x * txt * W, y_tile = blockIdx.y * ty;
+    const int tx = tid % txt, tyi = tid / txt;
+    const int x0 = x_tile + tx * W;
+    const int y = y_tile + tyi;
+    const bool active = !producer && (tyi < ty) && (x0 < N) && (y < N);
+    // Compute warps without an active lane (rows past the lattice edge in the
+    // last tile row) stay out of the ring: the "empty" barriers count only the
+    // others, so no warp can release a stage ahead of the ones still reading it.
+    const bool warp_active = __any_sync(0xffffffffu, active);
+    if (tid == 0) s_warps = 0;
+    __syncthreads();
+    if (lane == 0 && warp_active) atomicAdd(&s_warps, 1);
+    __syncthreads();
     const int z0 = blockIdx.z * zc;
     const int z1 = min(z0 + zc, N);
     const int K = (z1 - z0) + 2;  // planes z0-1 .. z1
@@ -635,7 +658,7 @@ __global__ void __launch_bounds__(288, 2) fused_pass_tma(Model m, FieldPtrs fp, 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CW);
+            mbar_init(&empty[s], s_warps);
         }
         s_failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -666,12 +689,15 @@ __global__ void __launch_bounds__(288, 2) fused_pass_tma(Model m, FieldPtrs fp, 
                 issued = k + 1;
             }
         }
-    } else {
-        const int lane = tid & 31;
-        const int tx = tid % txt, tyi = tid / txt;
-        const int x0 = x_tile + tx * W;
-        const int y = y_tile + tyi;
-        const bool active = (tyi < ty) && (x0 < N) && (y < N);
+    } else if (warp_active) {
+        // x-neighbours: the left site is the last one of the thread to the left
+        // in the same row and warp, the right site the first one of the thread
+        // to the right (warp shuffles, no shared-memory bank conflicts);
+        // threads at a row end or a warp edge read theirs from the stage.
+        const unsigned amask = __ballot_sync(0xffffffffu, active);
+        const bool own_l = tx == 0 || lane == 0;
+        const bool own_r = tx == txt - 1 || x0 + W >= N || lane == 31;
+        const int src_l = own_l ? lane : lane - 1, src_r = own_r ? lane : lane + 1;
         const Coefs<T, NF> k(m, c, sc);
         const int ctr = (tyi + 1) * rowe + (tx + 1) * W;
         const size_t P = (size_t)m.pitch, PP = (size_t)m.pplane;
@@ -710,7 +736,8 @@ __global__ void __launch_bounds__(288, 2) fused_pass_tma(Model m, FieldPtrs fp, 
         }
         if (!ok) s_failed = 1;
         release(0);
-        for (int z = z0; z < z1 && !s_failed; ++z) {
+        for (int z = z0; z < z1; ++z) {
+            if (__any_sync(0xffffffffu, s_failed != 0)) break;  // warp-uniform exit
             const int kz = z - z0 + 1;
             if (active) {
                 if (!mbar_wait_bounded(&full[(kz + 1) % S], ((kz + 1) / S) & 1u, sc)) s_failed = 1;
@@ -729,8 +756,10 @@ __global__ void __launch_bounds__(288, 2) fused_pass_tma(Model m, FieldPtrs fp, 
                     load_vec_s(pp + ctr + rowe, b);
 #pragma unroll
                     for (int j = 0; j < W; ++j) yp[f][j] = fma_t(k.drift, b[j], a[j]);
-                    xlv[f] = fma_t(k.drift, pp[ctr - 1], ph[ctr - 1]);
-                    xrv[f] = fma_t(k.drift, pp[ctr + W], ph[ctr + W]);
+                    const T l = __shfl_sync(amask, cu[f][W - 1], src_l);
+                    const T r = __shfl_sync(amask, cu[f][0], src_r);
+                    xlv[f] = own_l ? fma_t(k.drift, pp[ctr - 1], ph[ctr - 1]) : l;
+                    xrv[f] = own_r ? fma_t(k.drift, pp[ctr + W], ph[ctr + W]) : r;
                 }
                 T pnew[NF][W];
                 site_update<T, NF, W>(k, cu, zm, zp, ym, yp, xlv, xrv, pc, pnew, acc);
@@ -777,12 +806,15 @@ template <typename T, int NF, bool MEASURE>
 static cudaError_t launch_tma(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,
                               const TmaMaps &maps, Scalars *sc, double *slots, cudaStream_t s)
 {
-    static size_t configured = 0;
-    auto kern = fused_pass_tma<T, NF, MEASURE>;
-    if (g.smem > configured) {
+    // 7 + 1 warps (two CTAs per SM) or 15 + 1 warps (one CTA per SM): 16
+    // warps per SM, at most 4 per SM sub-partition, so 128 registers a thread
+    static size_t configured[2] = {0, 0};
+    const int big = g.cwarps > 7 ? 1 : 0;
+    auto kern = big ? fused_pass_tma<T, NF, MEASURE, 512> : fused_pass_tma<T, NF, MEASURE, 256>;
+    if (g.smem > configured[big]) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
         if (e != cudaSuccess) return e;
-        configured = g.smem;
+        configured[big] = g.smem;
     }
     kern<<<g.grid, 32 * (g.cwarps + 1), g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, g.stages, g.lpad, maps, sc, slots);
     return cudaGetLastError();

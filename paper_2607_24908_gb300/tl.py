@@ -59,6 +59,15 @@ class tl_energies_t(ctypes.Structure):
                 ("hubble_resid", ctypes.c_double)]
 
 
+PASS_STREAM, PASS_TMA = 0, 1
+PASS_KINDS = {"stream": PASS_STREAM, "tma": PASS_TMA}
+
+
+class tl_pass_config(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("warps", ctypes.c_int), ("stages", ctypes.c_int),
+                ("z_chunk", ctypes.c_int), ("tile_x", ctypes.c_int), ("threads", ctypes.c_int)]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -96,6 +105,8 @@ _SIGS = {
     "tl_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
     "tl_batch_destroy": (None, [ctypes.c_void_p]),
     "tl_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "tl_set_pass_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_pass_config)]),
+    "tl_get_pass_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_pass_config)]),
     "tl_langevin_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                         ctypes.POINTER(tl_langevin_params), ctypes.c_uint64]),
     "tl_su2_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
@@ -321,6 +332,20 @@ def tl_autotune(h) -> float:
     return ms.value
 
 
+def tl_set_pass_config(h, kind: int, warps: int = 0, stages: int = 0, z_chunk: int = 0, tile_x: int = 0,
+                       threads: int = 0):
+    cfg = tl_pass_config(kind, warps, stages, z_chunk, tile_x, threads)
+    _check(lib().tl_set_pass_config(h, ctypes.byref(cfg)))
+
+
+def tl_get_pass_config(h) -> dict:
+    cfg = tl_pass_config()
+    _check(lib().tl_get_pass_config(h, ctypes.byref(cfg)))
+    kind = {v: k for k, v in PASS_KINDS.items()}[cfg.kind]
+    return {"kind": kind, "warps": cfg.warps, "stages": cfg.stages, "z_chunk": cfg.z_chunk,
+            "tile_x": cfg.tile_x, "threads": cfg.threads}
+
+
 class Batch:
     """Several lattices advanced together (see tl_batch_step)."""
 
@@ -441,3 +466,12 @@ class Lattice:
     def autotune(self) -> float:
         """Pick the fastest launch geometry for this lattice shape; returns ms per pass."""
         return tl_autotune(self.h)
+
+    def set_pass_config(self, kind: str = "tma", warps: int = 0, stages: int = 0, z_chunk: int = 0,
+                        tile_x: int = 0, threads: int = 0):
+        """Launch shape of the fused pass (see tl_set_pass_config); kind "stream" or "tma"."""
+        tl_set_pass_config(self.h, PASS_KINDS[kind], warps, stages, z_chunk, tile_x, threads)
+
+    def pass_config(self) -> dict:
+        """The launch shape in use, automatic values resolved."""
+        return tl_get_pass_config(self.h)
