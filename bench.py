@@ -56,6 +56,15 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def kernel_name(shape) -> str:
+    """The fused-pass kernel a launch shape runs (FP32, two fields)."""
+    if shape is None:
+        return "fused_pass<float,2>"
+    if shape["kind"] == "tma":
+        return f"fused_pass_tma<float,2> ({shape['warps']}+1 warps, {shape['stages']} stages)"
+    return f"fused_pass_ldg<float,2> ({shape['threads']} threads)"
+
+
 def measured_traffic():
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source (else None)."""
@@ -222,6 +231,7 @@ def run_ours(args):
     lat = T.Lattice(N, kIR, WL.nf, WL.dtype, WL.expanding, WL.alpha, WL.fstar_over_mp, 1.0, stream=sptr)
     lat.set_potential(WL.lam, WL.q, WL.m2)
     lat.init_fluctuations(WL.seed + 1000 * rank, A=WL.A, meff2=WL.meff2, phi0=WL.phi0)
+    args.pass_shape = lat.pass_config()
 
     # warm-up: W steps (one call each)
     for _ in range(args.warmup):
@@ -309,12 +319,13 @@ def _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_ran
             "scaling": "weak", "vs_baseline": None, "dtype": WL.dtype, "data": "synthetic",
             "config": {"workload": WL.name if N == WL.N else f"{WL.name} reduced to {N}^3 (same dx)", "N": N, "n_fields": WL.nf, "integrator": WL.integrator,
                        "passes_per_step": PASSES, "dt": WL.dt, "storage": "fp32 fields/momenta, fp64 reductions",
+                       "pass_shape": getattr(args, "pass_shape", None),
                        "l2": f"inputs ({4 * WL.nf * sites * (4 if WL.dtype == 'f32' else 8) / 2**30:.1f} GiB "
                              "state) larger than L2; no flush", "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": measured_traffic() if N == WL.N else None, "algorithmic_bytes_per_launch": alg_bytes,
-                         "kernel": "fused_pass<float,2>", "ms_per_launch": ms_pass},
+                         "kernel": kernel_name(getattr(args, "pass_shape", None)), "ms_per_launch": ms_pass},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": state_bytes / args.steps,
                     "d2h_bytes_per_step": (state_bytes + 136) / args.steps,
