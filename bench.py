@@ -142,6 +142,27 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(rank: int) -> int:
+    """Seed of a replica's initial state: every rank evolves its own lattice."""
+    return WL.seed + 1000 * rank
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """Max of x over all ranks (all_reduce MAX of one FP64 value on `device`:
+    the GPU under NCCL, the CPU under gloo)."""
+    if ws <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(work_per_rank: float, ws: int, t_max_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return work_per_rank * ws / (t_max_ms / 1e3)
+
+
 # ---------------------------------------------------------------------------------
 # CPU oracle leg (reported baseline / --impl reference)
 # ---------------------------------------------------------------------------------
@@ -230,7 +251,7 @@ def run_ours(args):
     kIR = WL.kIR * WL.N / N  # same lattice spacing dx when N is reduced for profiling
     lat = T.Lattice(N, kIR, WL.nf, WL.dtype, WL.expanding, WL.alpha, WL.fstar_over_mp, 1.0, stream=sptr)
     lat.set_potential(WL.lam, WL.q, WL.m2)
-    lat.init_fluctuations(WL.seed + 1000 * rank, A=WL.A, meff2=WL.meff2, phi0=WL.phi0)
+    lat.init_fluctuations(replica_seed(rank), A=WL.A, meff2=WL.meff2, phi0=WL.phi0)
     args.pass_shape = lat.pass_config()
 
     # warm-up: W steps (one call each)
@@ -256,14 +277,10 @@ def run_ours(args):
     launches = PASSES * args.steps + 1
     ms_pass = ms / launches
 
-    t_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, ws, "cuda")
     sites = N ** 3
     work_per_rank = sites * WL.nf * PASSES * args.steps
-    value = work_per_rank * ws / (t_max / 1e3)
+    value = job_value(work_per_rank, ws, t_max)
 
     # end-to-end through the C ABI with host buffers: H2D of the state from
     # pinned memory, K steps, energies and D2H of the state, every call inside
@@ -292,10 +309,7 @@ def run_ours(args):
         for w in range(2):
             T.tl_get_state(lat.h, f, w, host[2 * f + w].numpy())
     t_e2e = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(t_e2e, ws, "cuda")
     state_bytes = 2 * WL.nf * sites * np.dtype(npd).itemsize
     lat.close()
     return _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_rank, t_e2e, state_bytes,
