@@ -17,8 +17,8 @@ def main():
     t_max = bench.max_over_ranks(ms, ws, "cpu")
     value = bench.job_value(1.0e9, ws, t_max)
     dist.barrier()
-    print(json.dumps({"rank": rank, "ws": ws, "t_max": t_max, "value": value, "seed": bench.replica_seed(rank)}),
-          flush=True)
+    with open(os.path.join(sys.argv[1], f"rank{rank}.json"), "w") as f:  # one file per rank: no interleaving
+        json.dump({"rank": rank, "ws": ws, "t_max": t_max, "value": value, "seed": bench.replica_seed(rank)}, f)
     dist.destroy_process_group()
 
 

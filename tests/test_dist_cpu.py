@@ -27,10 +27,10 @@ def json_lines(out: str):
     return [json.loads(l) for l in out.splitlines() if l.startswith("{")]
 
 
-def test_replica_aggregation_gloo_world_size_2():
-    r = torchrun([os.path.join("tests", "_dist_worker.py")])
+def test_replica_aggregation_gloo_world_size_2(tmp_path):
+    r = torchrun([os.path.join("tests", "_dist_worker.py"), str(tmp_path)])
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = sorted(json_lines(r.stdout), key=lambda d: d["rank"])
+    lines = [json.load(open(tmp_path / f"rank{k}.json")) for k in range(2)]
     assert [d["rank"] for d in lines] == [0, 1]
     for d in lines:
         assert d["ws"] == 2
