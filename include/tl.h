@@ -323,7 +323,8 @@ typedef struct {
  * the lattice's state is untouched).  Values out of range are TL_EINVAL;
  * TL_ESTATE while the lattice is in a batch.  May synchronise the lattice
  * stream (to grow its reduction slots).  A new lattice starts on TL_PASS_TMA
- * for N >= 256 and on TL_PASS_STREAM below; the environment variable
+ * when it is FP32 with two or more fields and N >= 192, on TL_PASS_STREAM
+ * otherwise (where that measured faster); the environment variable
  * TL_PASS_VARIANT=tma|ldg overrides that default at creation. */
 int tl_set_pass_config(tl_lattice *lat, const tl_pass_config *cfg);
 

@@ -28,7 +28,7 @@ namespace {
 
 thread_local char g_err[512] = "";
 
-int fail(int code, const char *fmt, ...)
+__attribute__((format(printf, 2, 3))) int fail(int code, const char *fmt, ...)
 {
     va_list ap;
     va_start(ap, fmt);
@@ -53,9 +53,10 @@ int fail(int code, const char *fmt, ...)
 
 }  // namespace
 
-tl::PassTuning tl::default_tuning(int N)
+tl::PassTuning tl::default_tuning(int N, int nf, int elem_bytes)
 {
-    tl::PassTuning t{N >= 256 ? tl::kVariantTma : tl::kVariantLdg, 7, 0, 0, 0, 256, 0};
+    const bool tma = elem_bytes == 4 && nf >= 2 && N >= 192;
+    tl::PassTuning t{tma ? tl::kVariantTma : tl::kVariantLdg, 7, 0, 0, 0, 256, 0};
     const char *v = getenv("TL_PASS_VARIANT");
     if (v && strcmp(v, "tma") == 0) t.variant = tl::kVariantTma;
     if (v && strcmp(v, "ldg") == 0) t.variant = tl::kVariantLdg;
@@ -208,7 +209,7 @@ int finish_create(tl_lattice *L, int N, double kIR, int nf, tl_dtype dtype, cons
     int dev = 0;
     TL_CK(cudaGetDevice(&dev));
     TL_CK(cudaDeviceGetAttribute(&L->sm_count, cudaDevAttrMultiProcessorCount, dev));
-    L->tuning = tl::default_tuning(N);
+    L->tuning = tl::default_tuning(N, nf, (int)L->esz);
     L->geom = tl::pass_geometry(N, (int)L->esz, L->sm_count, nf, L->tuning);
     TL_CK(cudaMalloc(&L->d_sc, sizeof(Scalars)));
     TL_CK(cudaMemset(L->d_sc, 0, sizeof(Scalars)));

@@ -42,7 +42,7 @@ namespace tl {
 // Launch one fused pass of a lattice on its stream and flip its buffers.
 int lattice_launch(tl_lattice *L, const PassCoef &c, bool measure_only);
 // Record an error message for tl_last_error(); returns code.
-int fail(int code, const char *fmt, ...);
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 // Coefficients of the n P + 1 passes of n steps (false: unknown integrator).
 bool pass_schedule(int n, double dt, int integrator, std::vector<PassCoef> &out);
 // Switch a lattice to launch shape t (grows its reduction slots if needed and

@@ -72,8 +72,8 @@ extern "C" int tl_energies_noalloc(int N, double kIR, int n_fields, tl_dtype dty
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return fail(TL_ECUDA, "device query: %s", cudaGetErrorString(e));
-    tl::PassTuning tune = tl::default_tuning(N);
+    if (e != cudaSuccess) return fail(TL_ECUDA, "device query: ", cudaGetErrorString(e));
+    tl::PassTuning tune = tl::default_tuning(N, n_fields, dtype == TL_F32 ? 4 : 8);
     tune.variant = tl::kVariantLdg;  // dense caller arrays have no ghost layer for tiled copies
     tune.prefetch = 0;
     const tl::PassGeom g = tl::pass_geometry(N, dtype == TL_F32 ? 4 : 8, sms, n_fields, tune);
