@@ -286,12 +286,12 @@ void tl_batch_destroy(tl_batch *batch);
 
 /* Time candidate launch shapes of the fused pass on this lattice (both
  * kinds of tl_pass_config: z-planes per CTA from 4 to the whole lattice and
- * the tile rows of the streaming kernel, the warps and ring depths of the TMA
- * kernel) with passes whose kick and drift coefficients are zero, which
- * rewrite the state unchanged, and keep the fastest.  Results are cached per
- * (N, n_fields, dtype, SM count) for the process and, if the environment
- * variable TL_TUNE_FILE names a file, appended there and reused by later
- * processes.  best_ms_per_pass (may be NULL) receives the winner's time.
+ * the tile rows of the streaming kernel, the warps of the TMA kernel) with
+ * passes whose kick and drift coefficients are zero, which rewrite the state
+ * unchanged, and keep the fastest.  Results are cached per (N, n_fields,
+ * dtype, SM count) for the process and, if the environment variable
+ * TL_TUNE_FILE names a file, appended there as one JSON object per line and
+ * reused by later processes.  best_ms_per_pass (may be NULL) receives the winner's time.
  * Synchronises the lattice stream.  Errors: TL_ESTATE (in a batch), TL_ECUDA. */
 int tl_autotune(tl_lattice *lat, double *best_ms_per_pass);
 

@@ -266,6 +266,13 @@ std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune;
 bool g_tune_loaded = false;
 
+// TL_TUNE_FILE holds JSON lines, one object per tuned shape, keys in the order
+// written below; lines that do not parse as such (or carry out-of-range
+// values) are skipped.
+const char *const kTuneFmt =
+    "{\"N\": %d, \"fields\": %d, \"dtype\": %d, \"sms\": %d, \"variant\": %d, \"warps\": %d, "
+    "\"stages\": %d, \"z_chunk\": %d, \"prefetch\": %d, \"threads\": %d, \"tile_x\": %d, \"ms\": %lf}";
+
 void load_tune_file()
 {
     g_tune_loaded = true;
@@ -273,15 +280,15 @@ void load_tune_file()
     if (!path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    // one entry per line: N fields dtype SMs variant warps stages zc prefetch threads txt ms
-    int N, nf, dt, sms, var, cw, st, zc, pf, th, txt;
-    double ms;
-    while (fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %lf", &N, &nf, &dt, &sms, &var, &cw, &st, &zc, &pf, &th, &txt,
-                  &ms) == 12) {
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        int N, nf, dt, sms, var, cw, st, zc, pf, th, txt;
+        double ms;
+        if (sscanf(line, kTuneFmt, &N, &nf, &dt, &sms, &var, &cw, &st, &zc, &pf, &th, &txt, &ms) != 12) continue;
         const bool ok = (var == tl::kVariantLdg || var == tl::kVariantTma) && (cw == 7 || cw == 15) &&
                         (st == 0 || (st >= 3 && st <= 8)) && zc >= 0 && zc <= N && (pf == 0 || pf == 3) &&
                         (th == 256 || th == 512) && (txt == 0 || txt == 8 || txt == 16 || txt == 32);
-        if (!ok) continue;  // not an entry this library wrote
+        if (!ok) continue;
         tl::PassTuning t{var, cw, st, zc, pf, th, txt};
         g_tune[TuneKey(N, nf, dt, sms)] = TuneVal{t, ms};
     }
@@ -294,8 +301,14 @@ void save_tune_entry(const TuneKey &k, const TuneVal &v)
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %.6f\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
-            std::get<3>(k), v.t.variant, v.t.cwarps, v.t.stages, v.t.zc, v.t.prefetch, v.t.threads, v.t.txt, v.ms);
+    char buf[512];
+    // the same format prints the value as %f (the scan reads it as %lf)
+    snprintf(buf, sizeof buf,
+             "{\"N\": %d, \"fields\": %d, \"dtype\": %d, \"sms\": %d, \"variant\": %d, \"warps\": %d, "
+             "\"stages\": %d, \"z_chunk\": %d, \"prefetch\": %d, \"threads\": %d, \"tile_x\": %d, \"ms\": %.6f}\n",
+             std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k), v.t.variant, v.t.cwarps, v.t.stages,
+             v.t.zc, v.t.prefetch, v.t.threads, v.t.txt, v.ms);
+    fputs(buf, f);
     fclose(f);
 }
 

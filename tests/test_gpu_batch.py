@@ -4,7 +4,11 @@ A batch advances lattices of uneven N, 1-2 fields, different couplings,
 backgrounds and seeds with one persistent launch per pass (per field count)
 replayed as a CUDA graph; each lattice keeps its own launch geometry, so the
 results must be bitwise those of tl_step on the lattice alone."""
+import json
 import math
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -113,4 +117,52 @@ def test_autotune_keeps_state_and_parity(tmp_path, monkeypatch):
     phi, pi = lat.get_all()
     assert np.max(np.abs(phi - ophi)) / np.max(np.abs(ophi)) < 1e-12
     lat.close()
-    assert (tmp_path / "tune.txt").read_text().strip()
+    # the cache file: JSON lines, and a fresh process takes the entry instead of re-timing
+    rec = json.loads((tmp_path / "tune.txt").read_text().strip().splitlines()[-1])
+    assert (rec["N"], rec["fields"], rec["dtype"]) == (64, 2, T.F64) and rec["variant"] in (0, 1)
+    assert abs(rec["ms"] - ms) < 1e-5
+    code = ("from paper_2607_24908_gb300 import tl as T; import numpy as np\n"
+            "lat = T.Lattice(64, 0.5, 2, 'f64', True, 1.0, 1.0, 1.0)\n"
+            "lat.set_potential(1.0, 100.0, (0.0, 0.0, 0.0))\n"
+            "lat.set_state(np.ones((2, 64, 64, 64)), np.zeros((2, 64, 64, 64)), 1.0, 1.0)\n"
+            "print(repr(lat.autotune())); lat.close()\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300,
+                         env=dict(os.environ, TL_TUNE_FILE=str(tmp_path / "tune.txt")))
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert float(out.stdout.strip().splitlines()[-1]) == rec["ms"]
+    assert len((tmp_path / "tune.txt").read_text().strip().splitlines()) == 1  # nothing re-timed or appended
+
+
+def test_ensemble_recipe_fp32_batch_against_oracle():
+    """The batched-ensemble recipe (FP32 storage with FP64 reductions, expanding with alpha 1, kIR 0.5,
+    V = phi^4/4 + (q/2) phi^2 chi^2, Philox vacuum fluctuations A = 1e-10 drawn by the oracle, Verlet
+    dt 0.01): 8 jobs with N in {32, 48}, 1-2 fields, q in {0, 10, 100}, own seeds, 100 steps in one
+    batch; every job against the oracle run from the same FP32-rounded state."""
+    from _tol import f32_pi_tol, normwise
+    rng = np.random.default_rng(4242)
+    jobs = [(int(rng.choice([32, 48])), int(rng.integers(1, 3)), float(rng.choice([0.0, 10.0, 100.0])), 100 + k)
+            for k in range(8)]
+    dt, steps = 0.01, 100
+    lats, refs = [], []
+    for N, nf, q, seed in jobs:
+        p = o.Params(N=N, nf=nf, kIR=0.5, expanding=True, alpha=1.0, lam=1.0, q=q, m2=(0.0, 0.0, 0.0))
+        phi, pi, _, _ = o.init_fluctuations(p, seed, o.InitSpec(A=1e-10, meff2=(3.0, q, 0.0), phi0=(1.0, 0.0, 0.0)))
+        phi32, pi32 = phi.astype(np.float32), pi.astype(np.float32)
+        lat = T.Lattice(N, 0.5, nf, "f32", True, 1.0, 1.0, 1.0)
+        lat.set_potential(1.0, q, (0.0, 0.0, 0.0))
+        lat.set_state(phi32, pi32, 1.0, 0.0, b_from_constraint=True)
+        lats.append(lat)
+        ph64, pi64 = phi32.astype(np.float64), pi32.astype(np.float64)
+        b0 = math.sqrt(float(np.sum(o.energies(p, ph64, pi64, 1.0))) / 3.0)
+        refs.append((p, o.run(p, ph64, pi64, 1.0, b0, dt, steps, o.VERLET)))
+    with T.Batch(lats) as b:
+        b.step(steps, dt, "verlet")
+    for lat, (p, (ophi, opi, oa, ob)), job in zip(lats, refs, jobs):
+        phi, pi = lat.get_all()
+        E = lat.energies()
+        assert normwise(phi, ophi) < 1e-5, job
+        tol = f32_pi_tol(p, steps + 1, float(np.max(np.abs(ophi))), float(np.max(np.abs(opi))))
+        assert normwise(pi, opi) < tol, (job, normwise(pi, opi), tol)
+        assert abs(E.a - oa) / oa < 1e-5 and abs(E.b - ob) / ob < 1e-5, job
+        lat.close()

@@ -19,15 +19,11 @@ import pytest
 import oracle as o
 from paper_2607_24908_gb300 import tl as T
 from paper_2607_24908_gb300.workloads import plane_wave, sample_sites, white_noise_state
+from _tol import TOL, f32_pi_tol, normwise
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5}
 OINT = {"leapfrog": o.LEAPFROG, "verlet": o.VERLET, "yoshida4": o.YOSHIDA4}
-
-
-def normwise(x, ref):
-    return float(np.max(np.abs(np.asarray(x, np.float64) - ref)) / np.max(np.abs(ref)))
 
 
 def make(p: o.Params, dtype: str) -> T.Lattice:
@@ -39,13 +35,6 @@ def make(p: o.Params, dtype: str) -> T.Lattice:
 def oracle_b0(p, phi, pi):
     E = o.energies(p, phi, pi, 1.0)
     return math.sqrt(p.fstar_over_mp ** 2 * float(np.sum(E)) / 3.0)
-
-
-def f32_pi_tol(p, passes, phimax, pimax):
-    """3 u sqrt(passes) omega_max max|phi| / max|pi| (see the module docstring), at least 1e-5."""
-    u = 2.0 ** -24
-    w2 = 12.0 / p.dx ** 2 + 3.0 * p.lam * phimax ** 2 + p.q * phimax ** 2 + max(p.m2)
-    return max(1e-5, 3.0 * u * math.sqrt(passes) * math.sqrt(w2) * phimax / pimax)
 
 
 def compare_run(p, dtype, phi0, pi0, dt, n, integ, tol=None, calls=1):
