@@ -49,14 +49,26 @@ __device__ __forceinline__ double gauss<double>(uint64_t site, uint64_t ctr1, ui
     return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
 }
 
+// x 2^-53 for an integer 0 <= x <= 2^53, formed in FP32 without FP64
+// arithmetic (GB300's FP64 pipe is slow): x = hi 2^29 + lo, hi <= 2^24 exact,
+// lo < 2^29 rounded once on conversion, one more rounding in the fma; the
+// result keeps a relative precision of about 2^-24 at any magnitude, so small
+// u1 (the Gaussian tail) stays as accurate as in a correctly rounded FP64->FP32
+// conversion.
+__device__ __forceinline__ float u53_f32(uint64_t x)
+{
+    const uint32_t hi = (uint32_t)(x >> 29), lo = (uint32_t)(x & 0x1FFFFFFFu);
+    return fmaf((float)hi, 0x1p-24f, (float)lo * 0x1p-53f);
+}
+
 template <>
 __device__ __forceinline__ float gauss<float>(uint64_t site, uint64_t ctr1, uint64_t seed)
 {
     uint64_t w0, w1;
     philox2x64_10(site, ctr1, seed, w0, w1);
-    // same uniforms, Box-Muller in FP32 (the field is stored in FP32)
-    const float u1 = (float)(((double)(w0 >> 11) + 1.0) * (1.0 / 9007199254740992.0));
-    const float u2 = (float)((double)(w1 >> 11) * (1.0 / 9007199254740992.0));
+    // the same 53-bit uniforms, Box-Muller in FP32 (the field is stored in FP32)
+    const float u1 = u53_f32((w0 >> 11) + 1);
+    const float u2 = u53_f32(w1 >> 11);
     float s, c;
     sincospif(2.0f * u2, &s, &c);
     return sqrtf(-2.0f * logf(u1)) * c;
