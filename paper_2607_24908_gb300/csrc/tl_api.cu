@@ -307,19 +307,21 @@ int read_scalars(tl_lattice *L, Scalars *h)
     return TL_OK;
 }
 
-// Dense host array [z][y][x] <-> padded device array, one 2-D copy per z-plane.
+// Dense host array [z][y][x] <-> padded device array: one 3-D copy (rows of
+// N elements; device rows `pitch` apart, planes N + 2 rows apart).
 int copy_planes(tl_lattice *L, void *host, void *dev, bool to_device)
 {
     const size_t N = (size_t)L->N, esz = L->esz;
     const size_t dpitch = (size_t)L->model.pitch * esz;
-    for (size_t z = 0; z < N; ++z) {
-        char *d = static_cast<char *>(dev) + z * (size_t)L->model.pplane * esz;
-        char *h = static_cast<char *>(host) + z * N * N * esz;
-        if (to_device)
-            TL_CK(cudaMemcpy2DAsync(d, dpitch, h, N * esz, N * esz, N, cudaMemcpyHostToDevice, L->stream));
-        else
-            TL_CK(cudaMemcpy2DAsync(h, N * esz, d, dpitch, N * esz, N, cudaMemcpyDeviceToHost, L->stream));
-    }
+    const size_t rows_per_plane = (size_t)L->model.pplane / (size_t)L->model.pitch;  // N + 2
+    cudaMemcpy3DParms p = {};
+    p.extent = make_cudaExtent(N * esz, N, N);
+    const cudaPitchedPtr h = make_cudaPitchedPtr(host, N * esz, N * esz, N);
+    const cudaPitchedPtr d = make_cudaPitchedPtr(dev, dpitch, N * esz, rows_per_plane);
+    p.srcPtr = to_device ? h : d;
+    p.dstPtr = to_device ? d : h;
+    p.kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    TL_CK(cudaMemcpy3DAsync(&p, L->stream));
     return TL_OK;
 }
 
