@@ -527,6 +527,39 @@ def run_expanding256(args):
 
 
 # ---------------------------------------------------------------------------------
+# The 32^3 FP64 static phi^4 workload: launch-bound, time per step direct vs graph replay
+# ---------------------------------------------------------------------------------
+
+def run_static32(args):
+    import torch
+    from paper_2607_24908_gb300 import tl as T
+    from paper_2607_24908_gb300.workloads import PHI4_STATIC_32 as W1
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    lat = T.Lattice(W1.N, W1.kIR, 1, W1.dtype, False, 0.0, 1.0, 1.0, stream=stream.cuda_stream)
+    lat.set_potential(W1.lam, 0.0, W1.m2)
+    lat.init_fluctuations(W1.seed, A=W1.A, meff2=W1.meff2, phi0=W1.phi0)
+    E0 = lat.energies()
+    times = []
+    for _ in range(4):  # call 1 launches directly, call 2 captures, calls 3-4 replay the graph
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.step(W1.steps, W1.dt, W1.integrator)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / W1.steps)
+    E = lat.energies()
+    lat.close()
+    e0t, et = float(np.sum(E0.vector())), float(np.sum(E.vector()))
+    print(json.dumps({"mode": "static32", "workload": W1.name, "steps_per_call": W1.steps,
+                      "ms_per_step_direct": times[0], "ms_per_step_graph": min(times[2:]),
+                      "site_updates_per_s_graph": W1.N ** 3 / (min(times[2:]) / 1e3),
+                      "energy_rel_change_after_1600_steps": abs(et - e0t) / e0t}), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------
 # Langevin phi^4 (the paper's interface example) throughput
 # ---------------------------------------------------------------------------------
 
@@ -604,7 +637,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--N", type=int, default=0, help="lattice size (default: the workload's 1024; for profiling)")
-    ap.add_argument("--mode", default="step", choices=["step", "ensemble", "serve", "expanding256", "langevin", "su2"],
+    ap.add_argument("--mode", default="step",
+                    choices=["step", "ensemble", "serve", "expanding256", "static32", "langevin", "su2"],
                     help="step: the 1024^3 fused step (default); ensemble: batched small lattices vs a plain loop; "
                          "serve: continuous batching of Poisson-arriving jobs vs a sequential loop")
     ap.add_argument("--jobs", type=int, default=0, help="jobs for --mode ensemble (96) / serve (24)")
@@ -624,6 +658,8 @@ def main():
         return run_langevin(args)
     if args.mode == "expanding256":
         return run_expanding256(args)
+    if args.mode == "static32":
+        return run_static32(args)
     if args.mode == "serve":
         args.jobs = args.jobs or 16
         return run_serve(args)

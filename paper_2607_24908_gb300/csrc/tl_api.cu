@@ -189,6 +189,7 @@ void refresh_model(tl_lattice *L)
     m.lambda = L->pot.lambda;
     m.q = L->pot.q;
     for (int f = 0; f < TL_MAX_FIELDS; ++f) m.m2[f] = L->pot.m2[f];
+    tl::invalidate_launches(L);
 }
 
 int finish_create(tl_lattice *L, int N, double kIR, int nf, tl_dtype dtype, const tl_expansion *ex, void *stream)
@@ -268,7 +269,9 @@ int ensure_tma_maps(tl_lattice *L)
     return TL_OK;
 }
 
-int launch(tl_lattice *L, const PassCoef &c, bool measure_only)
+int launch(tl_lattice *L, const PassCoef &c, bool measure_only, cudaStream_t stream);
+int launch(tl_lattice *L, const PassCoef &c, bool measure_only) { return launch(L, c, measure_only, L->stream); }
+int launch(tl_lattice *L, const PassCoef &c, bool measure_only, cudaStream_t stream)
 {
     const tl::TmaMaps *maps = nullptr;
     if (L->geom.variant == tl::kVariantTma) {
@@ -283,8 +286,7 @@ int launch(tl_lattice *L, const PassCoef &c, bool measure_only)
         fp.phi_out[f] = L->buf[L->cur ^ 1][0][f];
         fp.pi_out[f] = L->buf[L->cur ^ 1][1][f];
     }
-    TL_CK(tl::launch_pass((int)L->dtype, L->model, fp, c, L->geom, L->d_sc, L->d_slots, measure_only, L->stream,
-                          maps));
+    TL_CK(tl::launch_pass((int)L->dtype, L->model, fp, c, L->geom, L->d_sc, L->d_slots, measure_only, stream, maps));
     if (!measure_only) L->cur ^= 1;
     return TL_OK;
 }
@@ -372,8 +374,17 @@ int tl::set_geometry(tl_lattice *L, const PassTuning &t)
     }
     L->geom = g;
     L->tuning = t;
-    L->maps_txt = L->maps_ty = -1;  // re-encode tensor maps for the new tile shape
+    invalidate_launches(L);  // re-encodes tensor maps for the new tile shape too
     return TL_OK;
+}
+
+void tl::invalidate_launches(tl_lattice *L)
+{
+    for (auto &g : L->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    L->graphs.clear();
+    L->maps_txt = L->maps_ty = -1;
+    ++L->version;
 }
 
 extern "C" {
@@ -482,6 +493,9 @@ void tl_lattice_destroy(tl_lattice *L)
 {
     if (!L || L->batch_refs > 0) return;  // still held by a tl_batch: destroy the batch first
     if (L->stream || true) cudaStreamSynchronize(L->stream);
+    for (auto &g : L->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (L->capture) cudaStreamDestroy(L->capture);
     if (L->own && L->base) cudaFree(L->base);
     if (L->d_sc) cudaFree(L->d_sc);
     if (L->d_slots) cudaFree(L->d_slots);
@@ -516,6 +530,70 @@ int run_passes(tl_lattice *L, const std::vector<PassCoef> &passes)
     return TL_OK;
 }
 
+// The pass list of tl_step as a CUDA graph: captured on the lattice's private
+// stream (nothing runs during capture), instantiated, replayed on its stream.
+// Returns false if the capture could not be made (the caller then launches
+// directly); L->cur is left as it was.
+bool capture_passes(tl_lattice *L, const std::vector<PassCoef> &passes, cudaGraphExec_t *exec)
+{
+    *exec = nullptr;
+    if (!L->capture && cudaStreamCreateWithFlags(&L->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        L->capture = nullptr;
+        return false;
+    }
+    if (cudaStreamBeginCapture(L->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    const int cur = L->cur;
+    int rc = TL_OK;
+    for (const PassCoef &c : passes)
+        if ((rc = launch(L, c, false, L->capture))) break;
+    L->cur = cur;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(L->capture, &graph);
+    if (rc || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return false;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        *exec = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// tl_step's launches: the first call with a given (n, dt, integrator, buffer
+// parity) on the current lattice version launches the passes directly and
+// remembers the key; a repeat captures them once and from then on replays the
+// graph (one launch per call instead of n P + 1).  TL_STEP_GRAPHS=0 in the
+// environment turns this off.
+constexpr size_t kMaxStepGraphs = 8;
+
+int step_passes(tl_lattice *L, int n, double dt, int integrator, const std::vector<PassCoef> &passes)
+{
+    const char *env = getenv("TL_STEP_GRAPHS");
+    if (env && strcmp(env, "0") == 0) return run_passes(L, passes);
+    auto it = L->graphs.begin();
+    for (; it != L->graphs.end(); ++it)
+        if (it->n == n && it->dt == dt && it->integrator == integrator && it->cur == L->cur &&
+            it->version == L->version)
+            break;
+    if (it == L->graphs.end()) {  // first sight: direct launches, remember the key
+        if (L->graphs.size() >= kMaxStepGraphs) {
+            if (L->graphs.front().exec) cudaGraphExecDestroy(L->graphs.front().exec);
+            L->graphs.erase(L->graphs.begin());
+        }
+        L->graphs.push_back(tl_lattice::StepGraph{n, integrator, L->cur, dt, L->version, nullptr});
+        return run_passes(L, passes);
+    }
+    if (!it->exec && !capture_passes(L, passes, &it->exec)) return run_passes(L, passes);
+    TL_CK(cudaGraphLaunch(it->exec, L->stream));
+    if (passes.size() & 1) L->cur ^= 1;
+    return TL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -531,7 +609,7 @@ int tl_step(tl_lattice *L, int n, double dt, tl_integrator integrator)
     if (n == 0) return TL_OK;
     std::vector<PassCoef> passes;
     if (!tl::pass_schedule(n, dt, (int)integrator, passes)) return fail(TL_EINVAL, "unknown integrator %d", (int)integrator);
-    int rc = run_passes(L, passes);
+    int rc = step_passes(L, n, dt, (int)integrator, passes);
     if (rc) return rc;
     L->step += n;
     L->energies_valid = true;

@@ -182,5 +182,6 @@ extern "C" int tl_langevin_step(tl_lattice *L, int n, double dt, const tl_langev
     }
     L->langevin_steps += n;
     L->energies_valid = false;
+    if (n & 1) tl::invalidate_launches(L);  // phi_0's buffers traded places: tensor maps and graphs are stale
     return TL_OK;
 }

@@ -36,6 +36,18 @@ struct tl_lattice {
     int64_t langevin_steps = 0;  // Langevin steps since the last state reset (noise counters)
     bool energies_valid = false;
     int batch_refs = 0;  // tl_batch objects that hold this lattice
+    // Bumped whenever something a captured pass sequence bakes in changes: the
+    // launch shape, the model (potential, expansion), the buffer assignment.
+    unsigned version = 0;
+    // tl_step's replayable pass sequences (see tl_step), newest last.
+    struct StepGraph {
+        int n, integrator, cur;
+        double dt;
+        unsigned version;
+        cudaGraphExec_t exec;  // null until the key repeats
+    };
+    std::vector<StepGraph> graphs;
+    cudaStream_t capture = nullptr;  // private stream the sequences are captured on
 };
 
 namespace tl {
@@ -45,6 +57,9 @@ int lattice_launch(tl_lattice *L, const PassCoef &c, bool measure_only);
 int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
 // Coefficients of the n P + 1 passes of n steps (false: unknown integrator).
 bool pass_schedule(int n, double dt, int integrator, std::vector<PassCoef> &out);
+// Drop tl_step's captured pass sequences and bump the lattice version (call
+// after any change to what a pass launch bakes in).
+void invalidate_launches(tl_lattice *L);
 // Switch a lattice to launch shape t (grows its reduction slots if needed and
 // re-encodes tensor maps at the next TMA launch).
 int set_geometry(tl_lattice *L, const PassTuning &t);

@@ -67,11 +67,15 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
     const int gx = (per_row + g.txt - 1) / g.txt;
     const int gy = (N + g.ty - 1) / g.ty;
     // z-chunk: long enough to amortise the two extra planes, short enough
-    // for several waves of CTAs over the GPU.
+    // for several waves of CTAs over the GPU.  FP64 passes are bound by the
+    // FP64 pipe, so a small lattice spreads down to one plane per CTA to reach
+    // more SMs (the extra halo planes cost loads, not FP64 work); FP32 passes
+    // keep at least 4 planes, since for them the halo planes are traffic.
     int zc = t.zc > 0 ? t.zc : (N < 128 ? N : 128);
     if (t.zc <= 0) {
         const long target = 8L * (sm_count > 0 ? sm_count : 152);
-        while (zc > 4 && (long)gx * gy * ((N + zc - 1) / zc) < target) zc /= 2;
+        const int zmin = elem_bytes == 8 ? 1 : 4;
+        while (zc > zmin && (long)gx * gy * ((N + zc - 1) / zc) < target) zc /= 2;
     }
     if (zc > N) zc = N;
     g.zc = zc;
