@@ -518,8 +518,10 @@ def run_expanding256(args):
                      "f32_vs_f64_spectrum_rel_max": float(np.max(np.abs(b["P"][sel] - a["P"][sel]) / a["P"][sel])),
                      "P_bins_1_4_16_f64": [float(a["P"][i]) for i in (1, 4, 16)]})
     sites = W2.N ** 3
+    fp64_rate, fp32_rate = T.tl_probe_fma_rates()
     line = {"mode": "expanding256", "workload": W2.name, "steps": steps,
             "ms_per_pass": {"f64": ms64, "f32": ms32},
+            "fp64_fma_per_s_measured": fp64_rate, "fp32_fma_per_s_measured": fp32_rate,
             "site_updates_per_s": {"f64": sites / (ms64 / 1e3), "f32": sites / (ms32 / 1e3)},
             "every_100_steps": rows}
     print(json.dumps(line), flush=True)
@@ -552,7 +554,9 @@ def run_static32(args):
     E = lat.energies()
     lat.close()
     e0t, et = float(np.sum(E0.vector())), float(np.sum(E.vector()))
+    fp64_rate, _ = T.tl_probe_fma_rates()
     print(json.dumps({"mode": "static32", "workload": W1.name, "steps_per_call": W1.steps,
+                      "fp64_fma_per_s_measured": fp64_rate,
                       "ms_per_step_direct": times[0], "ms_per_step_graph": min(times[2:]),
                       "site_updates_per_s_graph": W1.N ** 3 / (min(times[2:]) / 1e3),
                       "energy_rel_change_after_1600_steps": abs(et - e0t) / e0t}), flush=True)

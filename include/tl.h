@@ -331,6 +331,13 @@ int tl_set_pass_config(tl_lattice *lat, const tl_pass_config *cfg);
 /* The launch shape lat runs now, with automatic values resolved. */
 int tl_get_pass_config(const tl_lattice *lat, tl_pass_config *cfg);
 
+/* Diagnostic (no counterpart in the paper): the device's FP64 and FP32 FMA
+ * issue rates in FMA operations per second, measured by timing a kernel of
+ * independent FMA chains over 8 CTAs of 256 threads per SM.  They are the
+ * arithmetic roofline of passes bound by the FP64 pipe.  Synchronises
+ * cuda_stream.  Errors: TL_EINVAL (NULL), TL_ENOMEM, TL_ECUDA. */
+int tl_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s, void *cuda_stream);
+
 /* Message for the last error on this thread ("" if none). */
 const char *tl_last_error(void);
 

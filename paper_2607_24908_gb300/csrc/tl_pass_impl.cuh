@@ -196,27 +196,38 @@ __device__ __forceinline__ void site_update(const Coefs<T, NF> &k, const T (&cu)
         T v[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) v[f] = cu[f][j];
-        T others = (T)0;
-#pragma unroll
-        for (int f = 1; f < NF; ++f) others += v[f] * v[f];
         const T v02 = v[0] * v[0];
         T dv[NF];
-        dv[0] = k.m2[0] * v[0] + k.lam * v02 * v[0] + k.q * v[0] * others;
-        T Vs = (T)0.5 * k.m2[0] * v02 + (T)0.25 * k.lam * v02 * v02 + (T)0.5 * k.q * v02 * others;
+        dv[0] = k.m2[0] * v[0] + k.lam * v02 * v[0];
+        T Vs = (T)0.5 * k.m2[0] * v02 + (T)0.25 * k.lam * v02 * v02;
+        if constexpr (NF > 1) {  // the coupling terms (with one field they are zero: skip them)
+            T others = (T)0;
 #pragma unroll
-        for (int f = 1; f < NF; ++f) {
-            dv[f] = k.m2[f] * v[f] + k.q * v02 * v[f];
-            Vs += (T)0.5 * k.m2[f] * v[f] * v[f];
+            for (int f = 1; f < NF; ++f) others += v[f] * v[f];
+            dv[0] += k.q * v[0] * others;
+            Vs += (T)0.5 * k.q * v02 * others;
+#pragma unroll
+            for (int f = 1; f < NF; ++f) {
+                dv[f] = k.m2[f] * v[f] + k.q * v02 * v[f];
+                Vs += (T)0.5 * k.m2[f] * v[f] * v[f];
+            }
         }
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             const T cc = v[f];
             const T left = (j == 0) ? xl[f] : cu[f][j - 1];
             const T right = (j == W - 1) ? xr[f] : cu[f][j + 1];
-            const T dxm = left - cc, dxp = right - cc;
-            const T dym = ym[f][j] - cc, dyp = yp[f][j] - cc;
-            const T dzm = zm[f][j] - cc, dzp = zp[f][j] - cc;
-            const T lap = ((dxm + dxp) + (dym + dyp)) + (dzm + dzp);
+            const T dxp = right - cc, dyp = yp[f][j] - cc, dzp = zp[f][j] - cc;
+            T lap;
+            if constexpr (sizeof(T) == 8) {
+                // FP64: the neighbour sum minus 6 phi (fewer FP64-pipe operations; the
+                // differences below are only needed for the gradient energy)
+                lap = fma_t((T)-6, cc, ((left + right) + (ym[f][j] + yp[f][j])) + (zm[f][j] + zp[f][j]));
+            } else {
+                // FP32: differences first, so the small gradients stay exact
+                const T dxm = left - cc, dym = ym[f][j] - cc, dzm = zm[f][j] - cc;
+                lap = ((dxm + dxp) + (dym + dyp)) + (dzm + dzp);
+            }
             const T F = k.wlx * lap - k.wv * dv[f];
             const T pint = fma_t(k.hdt, F, pc[f][j]);
             pnew[f][j] = fma_t(k.kdt, F, pc[f][j]);

@@ -106,6 +106,8 @@ _SIGS = {
     "tl_batch_destroy": (None, [ctypes.c_void_p]),
     "tl_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tl_set_pass_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_pass_config)]),
+    "tl_probe_fma_rates": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_void_p]),
     "tl_get_pass_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_pass_config)]),
     "tl_langevin_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                         ctypes.POINTER(tl_langevin_params), ctypes.c_uint64]),
@@ -330,6 +332,13 @@ def tl_autotune(h) -> float:
     ms = ctypes.c_double()
     _check(lib().tl_autotune(h, ctypes.byref(ms)))
     return ms.value
+
+
+def tl_probe_fma_rates(cuda_stream: int = 0):
+    """(FP64, FP32) FMA operations per second measured on the current device."""
+    f64, f32 = ctypes.c_double(), ctypes.c_double()
+    _check(lib().tl_probe_fma_rates(ctypes.byref(f64), ctypes.byref(f32), ctypes.c_void_p(cuda_stream)))
+    return f64.value, f32.value
 
 
 def tl_set_pass_config(h, kind: int, warps: int = 0, stages: int = 0, z_chunk: int = 0, tile_x: int = 0,
