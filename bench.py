@@ -40,6 +40,7 @@ sys.path.insert(0, ROOT)
 from paper_2607_24908_gb300.workloads import TWO_FIELD_1024 as WL  # noqa: E402
 
 METRIC = "site-updates/s per field"
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal (context beside the measured copy peak)
 PASSES = {"leapfrog": 1, "verlet": 1, "yoshida4": 3}[WL.integrator]
 BYTES_PER_SITE_FIELD_PASS = 4 * (4 if WL.dtype == "f32" else 8)  # read phi, pi; write phi, pi
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_pass_1024cubed_2f_f32.md")
@@ -338,6 +339,7 @@ def _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_ran
                              "state) larger than L2; no flush", "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
+                         "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "traffic": measured_traffic() if N == WL.N else None, "algorithmic_bytes_per_launch": alg_bytes,
                          "kernel": kernel_name(getattr(args, "pass_shape", None)), "ms_per_launch": ms_pass},
             "cpu_baseline": cpu,
