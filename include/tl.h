@@ -232,8 +232,10 @@ int tl_langevin_step(tl_lattice *lat, int n, double dt, const tl_langevin_params
 /* ---- SU(2) Yang-Mills in temporal gauge (Sec. 4 benchmark workload) ----
  * Links U_i(x) in SU(2) as unit quaternions (u0, u1, u2, u3) meaning
  * u0 + i (u1 s1 + u2 s2 + u3 s3); electric fields E_i(x) = i e_i.s as 3-vectors.
- * Host/device layout, component-major: U[i][c][z][y][x] (3 x 4 arrays of N^3)
- * and E[i][c][z][y][x] (3 x 3 arrays), elements of dtype.  Lattice units
+ * Host layout, component-major: U[i][c][z][y][x] (3 x 4 arrays of N^3) and
+ * E[i][c][z][y][x] (3 x 3 arrays), elements of dtype.  On the device the
+ * links are quaternion records U[i][z][y][x][c] (one vector load per link)
+ * and E keeps the host layout.  Lattice units
  * (dx = 1).  One step is the paper's leapfrog: kick
  * e_i(x) <- e_i(x) - 2 dt sum_{j != i} Im[U_i(x) S_ij(x)] with the staples
  * S_ij(x) = U_j(x+i) U_i(x+j)^+ U_j(x)^+ + U_j(x+i-j)^+ U_i(x-j)^+ U_j(x-j)

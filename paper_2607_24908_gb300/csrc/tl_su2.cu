@@ -2,9 +2,13 @@
 // workload (Sec. 4), each step a kick of the electric fields by the plaquette
 // staples and a drift of the links by the closed-form SU(2) exponential map.
 //
-// Links are unit quaternions U = u0 + i u.s, electric fields su(2) vectors
-// E = i e.s, both stored component-major (U: [direction][component][site],
-// 12 arrays; E: 9 arrays) so that consecutive threads read consecutive sites.
+// Links are unit quaternions U = u0 + i u.s, stored on the device as
+// quaternion records [direction][site][4] (one 16-byte load per link in FP32,
+// two in FP64; consecutive threads read consecutive records); electric fields
+// su(2) vectors E = i e.s, component-major [direction][component][site] (only
+// a site's own fields are read).  The host layout of both is component-major;
+// tl_su2_set_state / tl_su2_get_state transpose the links through the spare
+// link buffer.
 // One fused pass per step: e_i(x) <- e_i(x) - 2 dt sum_{j != i} Im[U_i S_ij]
 // with the old links, then U_i(x) <- exp(dt E_i(x)) U_i(x) written to the
 // other link buffer (ping-pong), so the neighbours' staples always see the old
@@ -56,11 +60,27 @@ __device__ __forceinline__ size_t sidx(int N, int x, int y, int z)
     return ((size_t)z * N + y) * N + x;
 }
 
-template <typename T>
-__device__ __forceinline__ Q<T> ldU(const T *U, size_t n3, int i, size_t s)
+// Link record of direction i at site s (records are 16- or 32-byte aligned).
+__device__ __forceinline__ Q<float> ldU(const float *U, size_t n3, int i, size_t s)
 {
-    const T *b = U + (size_t)(4 * i) * n3 + s;
-    return Q<T>{__ldg(b), __ldg(b + n3), __ldg(b + 2 * n3), __ldg(b + 3 * n3)};
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(U + ((size_t)i * n3 + s) * 4));
+    return Q<float>{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Q<double> ldU(const double *U, size_t n3, int i, size_t s)
+{
+    const double2 *b = reinterpret_cast<const double2 *>(U + ((size_t)i * n3 + s) * 4);
+    const double2 a = __ldg(b), c = __ldg(b + 1);
+    return Q<double>{a.x, a.y, c.x, c.y};
+}
+__device__ __forceinline__ void stU(float *U, size_t n3, int i, size_t s, const Q<float> &q)
+{
+    *reinterpret_cast<float4 *>(U + ((size_t)i * n3 + s) * 4) = make_float4(q.w, q.x, q.y, q.z);
+}
+__device__ __forceinline__ void stU(double *U, size_t n3, int i, size_t s, const Q<double> &q)
+{
+    double2 *b = reinterpret_cast<double2 *>(U + ((size_t)i * n3 + s) * 4);
+    b[0] = make_double2(q.w, q.x);
+    b[1] = make_double2(q.y, q.z);
 }
 
 template <typename T>
@@ -118,11 +138,7 @@ __global__ void __launch_bounds__(256) su2_pass(const T *__restrict__ U, T *__re
             const T r = rsqrt(u.w * u.w + u.x * u.x + u.y * u.y + u.z * u.z);
             u = Q<T>{u.w * r, u.x * r, u.y * r, u.z * r};
         }
-        T *o = Uout + (size_t)(4 * i) * n3 + s;
-        o[0] = u.w;
-        o[n3] = u.x;
-        o[2 * n3] = u.y;
-        o[3 * n3] = u.z;
+        stU(Uout, n3, i, s, u);
     }
 }
 
@@ -144,8 +160,11 @@ __global__ void __launch_bounds__(256) su2_measure(const T *__restrict__ U, cons
             el += 0.5 * (a * a + b * b + c * c);
             // Gauss: E_i(x) - U_i(x-i)^+ E_i(x-i) U_i(x-i)
             const size_t xm = sidx(N, x - d[i][0], y - d[i][1], z - d[i][2]);
-            const Q<double> Um{(double)U[(4 * i) * n3 + xm], (double)U[(4 * i + 1) * n3 + xm],
-                               (double)U[(4 * i + 2) * n3 + xm], (double)U[(4 * i + 3) * n3 + xm]};
+            auto ld = [&](int k, size_t site) {
+                const Q<T> q = ldU(U, n3, k, site);
+                return Q<double>{(double)q.w, (double)q.x, (double)q.y, (double)q.z};
+            };
+            const Q<double> Um = ld(i, xm);
             const Q<double> Em{0.0, (double)e[xm], (double)e[xm + n3], (double)e[xm + 2 * n3]};
             const Q<double> t = qmul(qmul(qadj(Um), Em), Um);
             G[0] += a - t.x;
@@ -154,10 +173,6 @@ __global__ void __launch_bounds__(256) su2_measure(const T *__restrict__ U, cons
             for (int j = i + 1; j < 3; ++j) {
                 const size_t xpi = sidx(N, x + d[i][0], y + d[i][1], z + d[i][2]);
                 const size_t xpj = sidx(N, x + d[j][0], y + d[j][1], z + d[j][2]);
-                auto ld = [&](int k, size_t site) {
-                    return Q<double>{(double)U[(4 * k) * n3 + site], (double)U[(4 * k + 1) * n3 + site],
-                                     (double)U[(4 * k + 2) * n3 + site], (double)U[(4 * k + 3) * n3 + site]};
-                };
                 const Q<double> P = qmul(qmul(qmul(ld(i, s), ld(j, xpi)), qadj(ld(i, xpj))), qadj(ld(j, s)));
                 mag += 2.0 * (1.0 - P.w);
             }
@@ -236,12 +251,32 @@ __global__ void su2_init(T *U, T *E, int N, uint64_t seed, double amp)
             }
             const double q1 = amp * g[0], q2 = amp * g[1], q3 = amp * g[2];
             const double inv = 1.0 / sqrt(1.0 + q1 * q1 + q2 * q2 + q3 * q3);
-            U[(4 * i) * n3 + s] = (T)inv;
-            U[(4 * i + 1) * n3 + s] = (T)(q1 * inv);
-            U[(4 * i + 2) * n3 + s] = (T)(q2 * inv);
-            U[(4 * i + 3) * n3 + s] = (T)(q3 * inv);
+            stU(U, n3, i, s, Q<T>{(T)inv, (T)(q1 * inv), (T)(q2 * inv), (T)(q3 * inv)});
             for (int c = 0; c < 3; ++c) E[(3 * i + c) * n3 + s] = (T)0;
         }
+    }
+}
+
+// Host layout U[i][c][site] <-> device records U[i][site][c].
+template <typename T>
+__global__ void su2_to_records(const T *__restrict__ cm, T *__restrict__ rec, size_t n3)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 3 * n3; k += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = k / n3, s = k - i * n3;
+        stU(rec, n3, (int)i, s, Q<T>{cm[(4 * i) * n3 + s], cm[(4 * i + 1) * n3 + s], cm[(4 * i + 2) * n3 + s],
+                                    cm[(4 * i + 3) * n3 + s]});
+    }
+}
+template <typename T>
+__global__ void su2_from_records(const T *__restrict__ rec, T *__restrict__ cm, size_t n3)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 3 * n3; k += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = k / n3, s = k - i * n3;
+        const Q<T> q = ldU(rec, n3, (int)i, s);
+        cm[(4 * i) * n3 + s] = q.w;
+        cm[(4 * i + 1) * n3 + s] = q.x;
+        cm[(4 * i + 2) * n3 + s] = q.y;
+        cm[(4 * i + 3) * n3 + s] = q.z;
     }
 }
 
@@ -329,7 +364,15 @@ int tl_su2_set_state(tl_su2 *Y, const void *U, const void *E)
     tl::set_error(TL_OK, "", "");
     if (!Y || !U || !E) return tl::fail(TL_EINVAL, "NULL argument");
     const size_t n3 = (size_t)Y->N * Y->N * Y->N;
-    SU_CK(cudaMemcpyAsync(Y->U[Y->cur], U, 12 * n3 * Y->esz, cudaMemcpyHostToDevice, Y->stream));
+    // host links into the spare buffer, then transposed into records
+    SU_CK(cudaMemcpyAsync(Y->U[Y->cur ^ 1], U, 12 * n3 * Y->esz, cudaMemcpyHostToDevice, Y->stream));
+    if (Y->dtype == TL_F32)
+        su2_to_records<float><<<Y->mblocks, 256, 0, Y->stream>>>(static_cast<const float *>(Y->U[Y->cur ^ 1]),
+                                                                 static_cast<float *>(Y->U[Y->cur]), n3);
+    else
+        su2_to_records<double><<<Y->mblocks, 256, 0, Y->stream>>>(static_cast<const double *>(Y->U[Y->cur ^ 1]),
+                                                                  static_cast<double *>(Y->U[Y->cur]), n3);
+    SU_CK(cudaGetLastError());
     SU_CK(cudaMemcpyAsync(Y->E, E, 9 * n3 * Y->esz, cudaMemcpyHostToDevice, Y->stream));
     SU_CK(cudaStreamSynchronize(Y->stream));
     Y->has_state = true;
@@ -341,7 +384,16 @@ int tl_su2_get_state(tl_su2 *Y, void *U, void *E)
     tl::set_error(TL_OK, "", "");
     if (!Y || (!U && !E)) return tl::fail(TL_EINVAL, "NULL argument");
     const size_t n3 = (size_t)Y->N * Y->N * Y->N;
-    if (U) SU_CK(cudaMemcpyAsync(U, Y->U[Y->cur], 12 * n3 * Y->esz, cudaMemcpyDeviceToHost, Y->stream));
+    if (U) {  // records transposed into the spare buffer, then copied out
+        if (Y->dtype == TL_F32)
+            su2_from_records<float><<<Y->mblocks, 256, 0, Y->stream>>>(static_cast<const float *>(Y->U[Y->cur]),
+                                                                       static_cast<float *>(Y->U[Y->cur ^ 1]), n3);
+        else
+            su2_from_records<double><<<Y->mblocks, 256, 0, Y->stream>>>(static_cast<const double *>(Y->U[Y->cur]),
+                                                                        static_cast<double *>(Y->U[Y->cur ^ 1]), n3);
+        SU_CK(cudaGetLastError());
+        SU_CK(cudaMemcpyAsync(U, Y->U[Y->cur ^ 1], 12 * n3 * Y->esz, cudaMemcpyDeviceToHost, Y->stream));
+    }
     if (E) SU_CK(cudaMemcpyAsync(E, Y->E, 9 * n3 * Y->esz, cudaMemcpyDeviceToHost, Y->stream));
     SU_CK(cudaStreamSynchronize(Y->stream));
     return TL_OK;
