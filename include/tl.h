@@ -189,6 +189,16 @@ int tl_set_background(tl_lattice *lat, double a, double b, int from_constraint);
  * state (padded layout, see tl_array_layout; valid until the next tl_step). */
 int tl_state_device_ptr(tl_lattice *lat, int field, int which, void **dev_ptr);
 
+/* The caller has written every phi_f and pi_f of the current state directly on
+ * the device (through tl_state_device_ptr or its own buffers of
+ * tl_lattice_create_with_buffers, interior sites in the padded layout): refresh
+ * their ghost copies and take them as the state, like tl_set_state of every
+ * array without a host copy (step and time reset to 0, a = a0, b = 0; call
+ * tl_set_background afterwards when expanding).  Synchronises the lattice
+ * stream (the caller's writes must be ordered before the call on that stream
+ * or complete).  Errors: TL_EINVAL (NULL), TL_ESTATE (in a batch), TL_ECUDA. */
+int tl_commit_state(tl_lattice *lat);
+
 /* Energies of a caller-owned device state, allocating no device memory.
  * No counterpart in the paper: this serves callers that cannot call
  * cudaMalloc (a host framework that owns all device memory, or code that must

@@ -680,6 +680,25 @@ int tl_set_state(tl_lattice *L, int field, int which, const void *host, size_t b
     return TL_OK;
 }
 
+int tl_commit_state(tl_lattice *L)
+{
+    g_err[0] = 0;
+    if (!L) return fail(TL_EINVAL, "NULL lattice");
+    if (L->batch_refs > 0) return fail(TL_ESTATE, "lattice is part of a batch");
+    for (int f = 0; f < L->nf; ++f)
+        for (int which = 0; which < 2; ++which)
+            TL_CK(tl::launch_fill_ghosts((int)L->dtype, L->buf[L->cur][which][f], L->N, L->model.pitch,
+                                         L->model.pplane, L->stream));
+    TL_CK(tl::launch_set_background(L->model, L->d_sc, L->ex.a0, 0.0, L->stream));
+    TL_CK(cudaStreamSynchronize(L->stream));
+    L->state_mask = (1u << (2 * L->nf)) - 1u;
+    L->has_state = true;
+    L->step = 0;
+    L->langevin_steps = 0;
+    L->energies_valid = false;
+    return TL_OK;
+}
+
 int tl_set_background(tl_lattice *L, double a, double b, int from_constraint)
 {
     g_err[0] = 0;

@@ -106,6 +106,7 @@ _SIGS = {
     "tl_batch_destroy": (None, [ctypes.c_void_p]),
     "tl_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tl_set_pass_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_pass_config)]),
+    "tl_commit_state": (ctypes.c_int, [ctypes.c_void_p]),
     "tl_probe_fma_rates": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                           ctypes.c_void_p]),
     "tl_get_pass_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_pass_config)]),
@@ -332,6 +333,10 @@ def tl_autotune(h) -> float:
     ms = ctypes.c_double()
     _check(lib().tl_autotune(h, ctypes.byref(ms)))
     return ms.value
+
+
+def tl_commit_state(h):
+    _check(lib().tl_commit_state(h))
 
 
 def tl_probe_fma_rates(cuda_stream: int = 0):
