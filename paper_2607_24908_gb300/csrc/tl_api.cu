@@ -252,7 +252,12 @@ int ensure_tma_maps(tl_lattice *L)
     const Layout lay = layout_of(L->N, esz);
     const cuuint64_t dims[3] = {(cuuint64_t)lay.pitch, (cuuint64_t)(L->N + 2), (cuuint64_t)L->N};
     const cuuint64_t strides[2] = {(cuuint64_t)lay.pitch * esz, (cuuint64_t)lay.pplane * esz};
-    const cuuint32_t box[3] = {(cuuint32_t)(g.txt * W + 2 * W), (cuuint32_t)(g.ty + 2), 1u};
+    // Test hook (host-side fault injection): TL_TEST_STALL_TMA encodes boxes one
+    // row short, so every stage receives fewer bytes than its barrier expects and
+    // the kernel's bounded waits expire (TL_ETIMEOUT) -- a wait that runs out,
+    // with every copy inside its stage region.
+    const bool stall = getenv("TL_TEST_STALL_TMA") != nullptr;
+    const cuuint32_t box[3] = {(cuuint32_t)(g.txt * W + 2 * W), (cuuint32_t)(g.ty + (stall ? 1 : 2)), 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     for (int par = 0; par < 2; ++par)
         for (int f = 0; f < L->nf; ++f)

@@ -1,8 +1,9 @@
 """Edge cases of the lattice path on the GPU: the smallest lattice under
 every launch shape, a zero-step call, a state written on the device and
-committed (tl_commit_state), and the largest lattice the ABI accepts (2048^3),
-checked through a property that holds at any size: a homogeneous state
-evolves exactly like the same state on the smallest lattice."""
+committed (tl_commit_state), the largest lattice the ABI accepts (2048^3),
+checked through a property that holds at any size (a homogeneous state
+evolves exactly like the same state on the smallest lattice), and a device
+wait made to run out (TL_ETIMEOUT, then recovery)."""
 import math
 
 import numpy as np
@@ -151,3 +152,38 @@ def test_largest_lattice_homogeneous_state():
     finally:
         del bufs
         torch.cuda.empty_cache()
+
+
+def test_expired_device_wait_reports_etimeout_and_recovers(monkeypatch):
+    """Failure detection without a fault: the host encodes the TMA boxes one row short
+    (TL_TEST_STALL_TMA), so the ring's stages never complete; the kernel's bounded waits
+    give up after about a second, record TL_ETIMEOUT and return, the context stays usable,
+    and a fresh state on re-encoded maps steps bitwise like the streaming shape."""
+    import time
+    N, nf = 24, 2
+    phi0, pi0 = white_noise_state(N, nf, seed=31, phi0=(1.0, 0.0), sigma_phi=1e-2, sigma_pi=1e-2)
+    phi0, pi0 = phi0.astype(np.float32), pi0.astype(np.float32)
+    monkeypatch.setenv("TL_TEST_STALL_TMA", "1")
+    with T.Lattice(N, 0.5, nf, "f32") as lat:
+        lat.set_pass_config("tma")
+        lat.set_potential(1.0, 10.0, (0.0, 0.2, 0.0))
+        lat.set_state(phi0, pi0)
+        t0 = time.perf_counter()
+        lat.step(1, 0.01, "verlet")
+        with pytest.raises(T.TLError) as e:
+            lat.energies()
+        assert e.value.code == T.ETIMEOUT
+        assert 0.9 < time.perf_counter() - t0 < 120.0
+        monkeypatch.delenv("TL_TEST_STALL_TMA")
+        lat.set_pass_config("tma")  # re-encodes the tensor maps
+        lat.set_state(phi0, pi0)    # resets the status word
+        lat.step(3, 0.01, "verlet")
+        phi, pi = lat.get_all()
+        lat.energies()
+    with T.Lattice(N, 0.5, nf, "f32") as ref:
+        ref.set_pass_config("stream")
+        ref.set_potential(1.0, 10.0, (0.0, 0.2, 0.0))
+        ref.set_state(phi0, pi0)
+        ref.step(3, 0.01, "verlet")
+        rphi, rpi = ref.get_all()
+    assert np.array_equal(phi, rphi) and np.array_equal(pi, rpi)
