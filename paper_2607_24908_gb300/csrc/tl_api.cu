@@ -24,18 +24,11 @@ using tl::PassCoef;
 using tl::PassGeom;
 using tl::Scalars;
 
+using tl::fail;
+
 namespace {
 
 thread_local char g_err[512] = "";
-
-__attribute__((format(printf, 2, 3))) int fail(int code, const char *fmt, ...)
-{
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(g_err, sizeof g_err, fmt, ap);
-    va_end(ap);
-    return code;
-}
 
 #define TL_CK(call)                                                                                 \
     do {                                                                                            \
@@ -497,7 +490,7 @@ int tl_lattice_create_with_buffers(tl_lattice **out, int N, double kIR, int n_fi
 void tl_lattice_destroy(tl_lattice *L)
 {
     if (!L || L->batch_refs > 0) return;  // still held by a tl_batch: destroy the batch first
-    if (L->stream || true) cudaStreamSynchronize(L->stream);
+    cudaStreamSynchronize(L->stream);
     for (auto &g : L->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (L->capture) cudaStreamDestroy(L->capture);

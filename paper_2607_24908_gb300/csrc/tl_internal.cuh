@@ -101,7 +101,7 @@ struct PassGeom {
     unsigned nblocks;
     int variant;   // kVariantLdg or kVariantTma
     int cwarps;    // compute warps per CTA
-    int stages;    // shared-memory ring depth (bulk variant)
+    int stages;    // shared-memory ring depth (TMA variant)
     int prefetch;  // per-thread prefetch depth (ldg variant)
     int lpad;      // TMA variant: padded-row index of x = 0 (128 bytes / element size)
     int threads;   // threads per CTA (ldg variant)
