@@ -90,16 +90,19 @@ __device__ __forceinline__ void sincos_t<float>(float a, float *s, float *c) { s
 template <>
 __device__ __forceinline__ void sincos_t<double>(double a, double *s, double *c) { sincos(a, s, c); }
 
-// One leapfrog step for the site owned by this thread (all three links).
+// One leapfrog step of site (x, y, z) (all three links).
 template <typename T>
-__global__ void __launch_bounds__(256) su2_pass(const T *__restrict__ U, T *__restrict__ Uout, T *__restrict__ E,
-                                                int N, T dt)
+__device__ __forceinline__ void su2_site(const T *__restrict__ U, T *__restrict__ Uout, T *__restrict__ E, int N,
+                                         size_t n3, T dt, int x, int y, int z)
 {
-    const size_t n3 = (size_t)N * N * N;
-    const size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (s >= n3) return;
-    const int x = (int)(s % N), y = (int)((s / N) % N), z = (int)(s / ((size_t)N * N));
-    const int d[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    const size_t s = ((size_t)z * N + y) * N + x;
+    // signed index steps to the periodic neighbours +mu and -mu (the wrap folded
+    // in; a step in one axis never changes the wrap of another)
+    const long long NN = (long long)N * N;
+    const long long up[3] = {x + 1 == N ? 1LL - N : 1LL, y + 1 == N ? (1LL - N) * N : (long long)N,
+                             z + 1 == N ? (1LL - N) * NN : NN};
+    const long long dn[3] = {x == 0 ? N - 1LL : -1LL, y == 0 ? (N - 1LL) * N : -(long long)N,
+                             z == 0 ? (N - 1LL) * NN : -NN};
     Q<T> Ux[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) Ux[i] = ldU(U, n3, i, s);
@@ -109,10 +112,10 @@ __global__ void __launch_bounds__(256) su2_pass(const T *__restrict__ U, T *__re
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             if (j == i) continue;
-            const size_t xpi = sidx(N, x + d[i][0], y + d[i][1], z + d[i][2]);
-            const size_t xpj = sidx(N, x + d[j][0], y + d[j][1], z + d[j][2]);
-            const size_t xmj = sidx(N, x - d[j][0], y - d[j][1], z - d[j][2]);
-            const size_t xpimj = sidx(N, x + d[i][0] - d[j][0], y + d[i][1] - d[j][1], z + d[i][2] - d[j][2]);
+            const size_t xpi = s + up[i];
+            const size_t xpj = s + up[j];
+            const size_t xmj = s + dn[j];
+            const size_t xpimj = s + up[i] + dn[j];
             // forward staple U_j(x+i) U_i(x+j)^+ U_j(x)^+
             const Q<T> f = qmul(qmul(ldU(U, n3, j, xpi), qadj(ldU(U, n3, i, xpj))), qadj(Ux[j]));
             // backward staple U_j(x+i-j)^+ U_i(x-j)^+ U_j(x-j)
@@ -140,6 +143,24 @@ __global__ void __launch_bounds__(256) su2_pass(const T *__restrict__ U, T *__re
         }
         stU(Uout, n3, i, s, u);
     }
+}
+
+// CTAs of 32 x 8 site columns; each thread marches a chunk of z-planes, so the
+// tile's links of planes z-1, z and z+1 are reused from L1 by the staples of
+// the neighbouring threads and of the next plane (most neighbour links are
+// then L1 hits instead of L2 round trips).
+constexpr int kSu2Tx = 32, kSu2Ty = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) su2_pass(const T *__restrict__ U, T *__restrict__ Uout, T *__restrict__ E,
+                                                int N, int zc, T dt)
+{
+    const int x = blockIdx.x * kSu2Tx + (int)(threadIdx.x % kSu2Tx);
+    const int y = blockIdx.y * kSu2Ty + (int)(threadIdx.x / kSu2Tx);
+    if (x >= N || y >= N) return;
+    const size_t n3 = (size_t)N * N * N;
+    const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, N);
+    for (int z = z0; z < z1; ++z) su2_site(U, Uout, E, N, n3, dt, x, y, z);
 }
 
 // Per-CTA partial sums of |e|^2/2, 2(1 - Re P_ij) and |G|^2, and the CTA's
@@ -420,17 +441,21 @@ int tl_su2_step(tl_su2 *Y, int n, double dt)
     if (!Y) return tl::fail(TL_EINVAL, "NULL lattice");
     if (n < 0 || !isfinite(dt) || dt == 0.0) return tl::fail(TL_EINVAL, "n >= 0 and a finite nonzero dt needed");
     if (!Y->has_state) return tl::fail(TL_ESTATE, "no state");
-    const size_t n3 = (size_t)Y->N * Y->N * Y->N;
-    const unsigned grid = (unsigned)((n3 + 255) / 256);
+    const int N = Y->N;
+    const int gx = (N + kSu2Tx - 1) / kSu2Tx, gy = (N + kSu2Ty - 1) / kSu2Ty;
+    // z-chunk: as long as possible (more reuse) while the grid keeps ~8 CTAs per SM
+    int zc = N;
+    while (zc > 1 && (long)gx * gy * ((N + zc - 1) / zc) < 8L * (Y->sm_count > 0 ? Y->sm_count : 152)) zc = (zc + 1) / 2;
+    const dim3 grid(gx, gy, (N + zc - 1) / zc);
     for (int k = 0; k < n; ++k) {
         if (Y->dtype == TL_F32)
             su2_pass<float><<<grid, 256, 0, Y->stream>>>(static_cast<const float *>(Y->U[Y->cur]),
                                                          static_cast<float *>(Y->U[Y->cur ^ 1]),
-                                                         static_cast<float *>(Y->E), Y->N, (float)dt);
+                                                         static_cast<float *>(Y->E), N, zc, (float)dt);
         else
             su2_pass<double><<<grid, 256, 0, Y->stream>>>(static_cast<const double *>(Y->U[Y->cur]),
                                                           static_cast<double *>(Y->U[Y->cur ^ 1]),
-                                                          static_cast<double *>(Y->E), Y->N, dt);
+                                                          static_cast<double *>(Y->E), N, zc, dt);
         SU_CK(cudaGetLastError());
         Y->cur ^= 1;
     }
