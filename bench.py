@@ -397,8 +397,12 @@ def run_ensemble(args):
     # one job at a time
     t0 = time.perf_counter()
     seq = []
+    t_seq_init = 0.0
     for j in jobs:
+        ti = time.perf_counter()
         lat = new(j)
+        torch.cuda.synchronize()
+        t_seq_init += time.perf_counter() - ti
         lat.step(steps, dt, "verlet")
         seq.append(lat.energies())
         lat.close()
@@ -407,6 +411,8 @@ def run_ensemble(args):
     # batched: all jobs resident, one grouped launch per pass, graph replay
     t0 = time.perf_counter()
     lats = [new(j) for j in jobs]
+    torch.cuda.synchronize()
+    t_bat_init = time.perf_counter() - t0
     with T.Batch(lats) as b:
         b.step(steps, dt, "verlet")
     bat = [lat.energies() for lat in lats]
@@ -423,6 +429,8 @@ def run_ensemble(args):
                                    f"{steps} Verlet steps dt={dt}, FP32 storage, expanding alpha=1, kIR=0.5",
                        "jobs": len(jobs), "steps": steps},
             "batched_s": t_bat, "sequential_s": t_seq, "sequential_jobs_per_s": len(jobs) / t_seq,
+            "init_s": {"batched": t_bat_init, "sequential": t_seq_init},
+            "stepping_s": {"batched": t_bat - t_bat_init, "sequential": t_seq - t_seq_init},
             "speedup": t_seq / t_bat, "site_updates_per_s_batched": site_updates / t_bat,
             "max_rel_energy_diff_batched_vs_sequential": diff}
     print(json.dumps(line), flush=True)

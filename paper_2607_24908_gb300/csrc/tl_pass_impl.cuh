@@ -166,19 +166,25 @@ template <typename T, int NF>
 struct Coefs {
     T drift, wlx, wv, kdt, hdt, lam, q;
     T m2[NF];
-    __device__ Coefs(const Model &m, const PassCoef &c, const Scalars *sc)
-    {
-        drift = (T)sc->drift;
-        wlx = (T)(sc->wl * m.inv_dx2);
-        wv = (T)sc->wv;
-        kdt = (T)c.kdt;
-        hdt = (T)c.hdt;
-        lam = (T)m.lambda;
-        q = (T)m.q;
-#pragma unroll
-        for (int f = 0; f < NF; ++f) m2[f] = (T)m.m2[f];
-    }
 };
+
+template <typename T, int NF>
+__device__ __forceinline__ Coefs<T, NF> make_coefs(const Model &m, const PassCoef &c, const Scalars *sc)
+{
+    Coefs<T, NF> k;
+    k.drift = (T)sc->drift;
+    k.wlx = (T)(sc->wl * m.inv_dx2);
+    k.wv = (T)sc->wv;
+    k.kdt = (T)c.kdt;
+    k.hdt = (T)c.hdt;
+    k.lam = (T)m.lambda;
+    k.q = (T)m.q;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) k.m2[f] = (T)m.m2[f];
+    return k;
+}
+
+
 
 // Update W consecutive sites of one row of plane z, all fields: Laplacian from
 // the six neighbours (differences first, so FP32 keeps the small gradients
@@ -241,7 +247,11 @@ __device__ __forceinline__ void site_update(const Coefs<T, NF> &k, const T (&cu)
 // CTA sum in a fixed order (warp trees, then warps in index order) into this
 // CTA's slot; the last CTA to arrive sums all slots in index order and runs
 // finalize().  Deterministic for a given launch geometry.
-template <int NQ>
+// F32TREE (FP32 lattices): the warp tree runs in FP32 and each warp adds its
+// sum to the CTA's FP64 total -- thread sums (FP32 in-thread, promoted to FP64
+// every 16 planes), FP32 warp tree, FP64 from there on; FP64 lattices keep the
+// whole tree in FP64.
+template <int NQ, bool F32TREE = false>
 __device__ __forceinline__ void cta_reduce_finalize(const double (&accd)[NQ], const Model &m, const PassCoef &c,
                                                     Scalars *sc, double *slots, unsigned bid, unsigned nblocks)
 {
@@ -252,7 +262,15 @@ __device__ __forceinline__ void cta_reduce_finalize(const double (&accd)[NQ], co
     const int nwarps = blockDim.x >> 5;
 #pragma unroll
     for (int i = 0; i < NQ; ++i) {
-        double v = warp_sum(accd[i]);
+        double v;
+        if constexpr (F32TREE) {
+            float w = (float)accd[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            v = (double)w;
+        } else {
+            v = warp_sum(accd[i]);
+        }
         if (lane == 0) red[warp][i] = v;
     }
     __syncthreads();
@@ -379,7 +397,7 @@ __device__ __forceinline__ void ldg_tile(const Model &m, const FieldPtrs &fp, co
     for (int i = 0; i < NQ; ++i) accd[i] = 0.0;
 
     if (active) {
-        const Coefs<T, NF> k(m, c, sc);
+        const Coefs<T, NF> k = make_coefs<T, NF>(m, c, sc);
         const T *phs[NF], *pis[NF];
         T *pho[NF], *pio[NF];
 #pragma unroll
@@ -507,7 +525,7 @@ __device__ __forceinline__ void ldg_tile(const Model &m, const FieldPtrs &fp, co
 #pragma unroll
         for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
     }
-    cta_reduce_finalize<NQ>(accd, m, c, sc, slots, bid, nblocks);
+    cta_reduce_finalize<NQ, sizeof(T) == 4>(accd, m, c, sc, slots, bid, nblocks);
 }
 
 template <typename T, int NF, bool MEASURE, int D, int NT>
@@ -571,13 +589,6 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
         : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
     return ok != 0;
-}
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
 }
 __device__ __forceinline__ uint64_t global_ns()
 {
@@ -709,7 +720,7 @@ __global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Mo
         const bool own_l = tx == 0 || lane == 0;
         const bool own_r = tx == txt - 1 || x0 + W >= N || lane == 31;
         const int src_l = own_l ? lane : lane - 1, src_r = own_r ? lane : lane + 1;
-        const Coefs<T, NF> k(m, c, sc);
+        const Coefs<T, NF> k = make_coefs<T, NF>(m, c, sc);
         const int ctr = (tyi + 1) * rowe + (tx + 1) * W;
         const size_t P = (size_t)m.pitch, PP = (size_t)m.pplane;
         T *pho[NF], *pio[NF];
@@ -810,7 +821,7 @@ __global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Mo
     if (s_failed && producer && (tid & 31) == 0)
         for (int kk = (issued > S ? issued - S : 0); kk < issued; ++kk)
             mbar_wait_bounded(&full[kk % S], (kk / S) & 1u, sc);
-    cta_reduce_finalize<NQ>(accd, m, c, sc, slots, grid_bid(), grid_nblocks());
+    cta_reduce_finalize<NQ, sizeof(T) == 4>(accd, m, c, sc, slots, grid_bid(), grid_nblocks());
 }
 
 template <typename T, int NF, bool MEASURE>
