@@ -273,40 +273,6 @@ int tl_su2_step(tl_su2 *lat, int n, double dt);
  * (Gauss's law), averages over sites; fixed-order FP64 sums.  Synchronises. */
 int tl_su2_measure(tl_su2 *lat, double *out4);
 
-/* ---- batched ensembles and launch tuning (beyond the paper's single
- * lattice: many independent small lattices advanced together) ---- */
-
-typedef struct tl_batch tl_batch; /* opaque */
-
-/* Group n existing lattices (same dtype; any N, n_fields, potential,
- * background) into a batch that tl_batch_step advances together.  The
- * lattices stay owned by the caller and cannot be destroyed or autotuned
- * while the batch exists; their own calls (tl_energies, tl_get_state,
- * tl_spectrum ...) keep working between batch steps.  cuda_stream: the
- * stream the batch runs on.  Errors: TL_EINVAL, TL_ENOMEM, TL_ECUDA. */
-int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_stream);
-
-/* Advance every lattice of the batch by n steps of size dt, as tl_step
- * would, with one persistent launch per pass and per field count (each
- * launch walks all lattices' CTA tiles), the whole pass sequence captured
- * once as a CUDA graph per (n, dt, integrator) and replayed.  Each lattice
- * keeps its own launch geometry and reduction order, so its results are
- * bitwise those of tl_step on it alone.  Enqueues only. */
-int tl_batch_step(tl_batch *batch, int n, double dt, tl_integrator integrator);
-
-void tl_batch_destroy(tl_batch *batch);
-
-/* Time candidate launch shapes of the fused pass on this lattice (both
- * kinds of tl_pass_config: z-planes per CTA from 4 to the whole lattice and
- * the tile rows of the streaming kernel, the warps of the TMA kernel) with
- * passes whose kick and drift coefficients are zero, which rewrite the state
- * unchanged, and keep the fastest.  Results are cached per (N, n_fields,
- * dtype, SM count) for the process and, if the environment variable
- * TL_TUNE_FILE names a file, appended there as one JSON object per line and
- * reused by later processes.  best_ms_per_pass (may be NULL) receives the winner's time.
- * Synchronises the lattice stream.  Errors: TL_ESTATE (in a batch), TL_ECUDA. */
-int tl_autotune(tl_lattice *lat, double *best_ms_per_pass);
-
 /* Launch shape of the fused pass (the one kernel a step launches per
  * (sub)step, Sec. 4's kick and drift with the energy sums of Sec. 3.2).
  * Both kinds compute every site with the same operations in the same order,
@@ -330,6 +296,49 @@ typedef struct {
     int tile_x;  /* STREAM: threads along a tile row, 8, 16 or 32; 0 = 32 */
     int threads; /* STREAM: threads per CTA, 256 or 512; 0 = 256 */
 } tl_pass_config;
+
+/* ---- batched ensembles and launch tuning (beyond the paper's single
+ * lattice: many independent small lattices advanced together) ---- */
+
+typedef struct tl_batch tl_batch; /* opaque */
+
+/* Group n existing lattices (same dtype; any N, n_fields, potential,
+ * background) into a batch that tl_batch_step advances together.  Each
+ * lattice is moved to the batch launch shape (tl_batch_pass_config) if it is
+ * not on it, and keeps it afterwards; a batch step is bitwise tl_step of the
+ * lattice alone on that shape.  The
+ * lattices stay owned by the caller and cannot be destroyed or autotuned
+ * while the batch exists; their own calls (tl_energies, tl_get_state,
+ * tl_spectrum ...) keep working between batch steps.  cuda_stream: the
+ * stream the batch runs on.  Errors: TL_EINVAL, TL_ENOMEM, TL_ECUDA. */
+int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_stream);
+
+/* The launch shape tl_batch_create gives a lattice of this size: the
+ * TL_PASS_STREAM kernel with 256-thread CTAs and z-chunks of min(N, 32)
+ * planes.  Set it with tl_set_pass_config on a lattice that should step alone
+ * bitwise like its batched twin.  Errors: TL_EINVAL. */
+int tl_batch_pass_config(int N, int n_fields, tl_dtype dtype, tl_pass_config *out);
+
+/* Advance every lattice of the batch by n steps of size dt, as tl_step
+ * would, with one persistent launch per pass and per field count (each
+ * launch walks all lattices' CTA tiles), the whole pass sequence captured
+ * once as a CUDA graph per (n, dt, integrator) and replayed.  Each lattice
+ * keeps its own launch geometry and reduction order, so its results are
+ * bitwise those of tl_step on it alone.  Enqueues only. */
+int tl_batch_step(tl_batch *batch, int n, double dt, tl_integrator integrator);
+
+void tl_batch_destroy(tl_batch *batch);
+
+/* Time candidate launch shapes of the fused pass on this lattice (both
+ * kinds of tl_pass_config: z-planes per CTA from 4 to the whole lattice and
+ * the tile rows of the streaming kernel, the warps of the TMA kernel) with
+ * passes whose kick and drift coefficients are zero, which rewrite the state
+ * unchanged, and keep the fastest.  Results are cached per (N, n_fields,
+ * dtype, SM count) for the process and, if the environment variable
+ * TL_TUNE_FILE names a file, appended there as one JSON object per line and
+ * reused by later processes.  best_ms_per_pass (may be NULL) receives the winner's time.
+ * Synchronises the lattice stream.  Errors: TL_ESTATE (in a batch), TL_ECUDA. */
+int tl_autotune(tl_lattice *lat, double *best_ms_per_pass);
 
 /* Set the launch shape of lat's fused pass (takes effect at the next launch;
  * the lattice's state is untouched).  Values out of range are TL_EINVAL;

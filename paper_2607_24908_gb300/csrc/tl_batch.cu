@@ -133,7 +133,30 @@ int build_graph(tl_batch *B, int n, double dt, int integrator)
 
 }  // namespace
 
+namespace {
+
+// The launch shape of batch members: the register-streaming tiles with
+// 256-thread CTAs (what the grouped kernel runs) and z-chunks of 32 planes
+// (the whole lattice below that), so that each (lattice, tile) item of the
+// grouped launch carries enough planes to amortise its fixed costs (locating
+// the job, the coefficient set-up, the FP64 reduction of its sums).
+tl::PassTuning batch_tuning(int N) { return tl::PassTuning{tl::kVariantLdg, 7, 0, N < 32 ? N : 32, 0, 256, 0}; }
+
+}  // namespace
+
 extern "C" {
+
+int tl_batch_pass_config(int N, int n_fields, tl_dtype dtype, tl_pass_config *out)
+{
+    tl::set_error(TL_OK, "", "");
+    if (!out) return tl::fail(TL_EINVAL, "NULL out");
+    if (N < 8 || N % 4 != 0 || N > 2048 || n_fields < 1 || n_fields > TL_MAX_FIELDS ||
+        (dtype != TL_F32 && dtype != TL_F64))
+        return tl::fail(TL_EINVAL, "bad lattice shape");
+    const tl::PassTuning t = batch_tuning(N);
+    *out = tl_pass_config{TL_PASS_STREAM, 0, 0, t.zc, 0, t.threads};
+    return TL_OK;
+}
 
 int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_stream)
 {
@@ -146,12 +169,12 @@ int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_s
         for (int k = 0; k < i; ++k)
             if (lats[k] == lats[i]) return tl::fail(TL_EINVAL, "lattice %d appears twice", i);
     }
-    // the grouped kernel runs the register-streaming tiles with 256-thread
-    // CTAs: members on another shape move to it (and keep it afterwards)
+    // members move to the batch shape (and keep it afterwards)
     for (int i = 0; i < n; ++i) {
         tl_lattice *L = lats[i];
-        if (L->geom.variant != tl::kVariantLdg || L->geom.threads != 256 || L->geom.prefetch != 0) {
-            const tl::PassTuning t{tl::kVariantLdg, 7, 0, L->tuning.zc, 0, 256, L->tuning.txt};
+        const tl::PassTuning t = batch_tuning(L->N);
+        if (L->tuning.variant != t.variant || L->tuning.threads != t.threads || L->tuning.zc != t.zc ||
+            L->tuning.txt != t.txt || L->tuning.prefetch != t.prefetch) {
             int rc = tl::set_geometry(L, t);
             if (rc) return rc;
         }

@@ -543,19 +543,31 @@ __global__ void __launch_bounds__(NT, 512 / NT) fused_pass_ldg(Model m, FieldPtr
 // its results are bitwise the same alone and in a batch).  The CTAs of the
 // launch walk the flattened list of (job, tile) items.
 
+// The job table (first item of each job) is staged in shared memory once per
+// CTA when it fits (kGroupStagedJobs entries), so locating an item's job is a
+// binary search in shared memory rather than a chain of dependent global loads.
+constexpr int kGroupStagedJobs = 8192;
+
 template <typename T, int NF>
 __global__ void __launch_bounds__(256, 2) fused_pass_group(const BatchJob *jobs, const unsigned *first_item, int njobs,
                                                            unsigned total, PassCoef c)
 {
+    extern __shared__ unsigned s_first[];
+    const bool staged = njobs <= kGroupStagedJobs;
+    if (staged) {
+        for (int i = threadIdx.x; i < njobs; i += blockDim.x) s_first[i] = __ldg(first_item + i);
+        __syncthreads();
+    }
+    const unsigned *first = staged ? s_first : first_item;
     for (unsigned item = blockIdx.x; item < total; item += gridDim.x) {
         int lo = 0, hi = njobs - 1;  // last job whose first item <= item
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(first_item + mid) <= item) lo = mid;
+            if (first[mid] <= item) lo = mid;
             else hi = mid - 1;
         }
         const BatchJob &j = jobs[lo];
-        const unsigned local = item - __ldg(first_item + lo);
+        const unsigned local = item - first[lo];
         const int bx = (int)(local % (unsigned)j.gx);
         const int by = (int)((local / (unsigned)j.gx) % (unsigned)j.gy);
         const int bz = (int)(local / ((unsigned)j.gx * (unsigned)j.gy));

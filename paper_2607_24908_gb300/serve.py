@@ -76,10 +76,10 @@ class JobResult:
 
 def _new_lattice(spec: JobSpec, stream: int) -> T.Lattice:
     lat = T.Lattice(spec.N, spec.kIR, spec.n_fields, spec.dtype, True, 1.0, 1.0, 1.0, stream=stream)
-    # served jobs advance in batches, whose grouped kernel runs the streaming
-    # launch shape; every job starts on it, so a job's energy sums (and thus
-    # its expansion) are the same served and alone
-    lat.set_pass_config("stream")
+    # served jobs advance in batches; every job starts on the batch launch
+    # shape, so its energy sums (and thus its expansion) are the same served
+    # and alone
+    lat.set_pass_config(**T.batch_pass_config(spec.N, spec.n_fields, spec.dtype))
     lat.set_potential(1.0, spec.q, (0.0, 0.0, 0.0))
     meff2 = (3.0,) + (spec.q,) * (spec.n_fields - 1)
     lat.init_fluctuations(spec.seed, A=spec.A, meff2=meff2, phi0=(1.0, 0.0, 0.0))

@@ -107,6 +107,7 @@ _SIGS = {
     "tl_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tl_set_pass_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_pass_config)]),
     "tl_commit_state": (ctypes.c_int, [ctypes.c_void_p]),
+    "tl_batch_pass_config": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(tl_pass_config)]),
     "tl_probe_fma_rates": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                           ctypes.c_void_p]),
     "tl_get_pass_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_pass_config)]),
@@ -352,12 +353,24 @@ def tl_set_pass_config(h, kind: int, warps: int = 0, stages: int = 0, z_chunk: i
     _check(lib().tl_set_pass_config(h, ctypes.byref(cfg)))
 
 
-def tl_get_pass_config(h) -> dict:
-    cfg = tl_pass_config()
-    _check(lib().tl_get_pass_config(h, ctypes.byref(cfg)))
+def _cfg_dict(cfg: tl_pass_config) -> dict:
     kind = {v: k for k, v in PASS_KINDS.items()}[cfg.kind]
     return {"kind": kind, "warps": cfg.warps, "stages": cfg.stages, "z_chunk": cfg.z_chunk,
             "tile_x": cfg.tile_x, "threads": cfg.threads}
+
+
+def tl_get_pass_config(h) -> dict:
+    cfg = tl_pass_config()
+    _check(lib().tl_get_pass_config(h, ctypes.byref(cfg)))
+    return _cfg_dict(cfg)
+
+
+def batch_pass_config(N: int, n_fields: int, dtype: str) -> dict:
+    """The launch shape tl_batch_create gives a lattice of this size (keyword
+    arguments for Lattice.set_pass_config)."""
+    cfg = tl_pass_config()
+    _check(lib().tl_batch_pass_config(N, n_fields, DTYPES[dtype], ctypes.byref(cfg)))
+    return _cfg_dict(cfg)
 
 
 class Batch:

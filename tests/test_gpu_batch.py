@@ -2,8 +2,9 @@
 
 A batch advances lattices of uneven N, 1-2 fields, different couplings,
 backgrounds and seeds with one persistent launch per pass (per field count)
-replayed as a CUDA graph; each lattice keeps its own launch geometry, so the
-results must be bitwise those of tl_step on the lattice alone."""
+replayed as a CUDA graph; each lattice runs on the batch launch shape
+(tl_batch_pass_config), so the results must be bitwise those of tl_step on
+the lattice alone on that shape."""
 import json
 import math
 import os
@@ -27,6 +28,7 @@ JOBS = [  # N, fields, q, expanding, dtype seed
 
 def make(N, nf, q, expanding, dtype):
     lat = T.Lattice(N, 0.5, nf, dtype, expanding, 1.0, 1.0, 1.0)
+    lat.set_pass_config(**T.batch_pass_config(N, nf, dtype))  # the shape a batch gives it
     lat.set_potential(1.0, q, (0.0, 0.1, 0.0))
     return lat
 

@@ -105,7 +105,7 @@ def test_default_shape_and_errors():
         assert (c2["kind"], c2["tile_x"], c2["threads"], c2["z_chunk"]) == ("stream", 16, 512, 32)
 
 
-def test_batch_moves_members_to_the_streaming_shape():
+def test_batch_moves_members_to_the_batch_shape():
     N, nf = 128, 2
     phi, pi = white_noise_state(N, nf, seed=4, phi0=(1.0, 0.0), sigma_phi=1e-2, sigma_pi=1e-2)
 
@@ -115,8 +115,8 @@ def test_batch_moves_members_to_the_streaming_shape():
         lat.set_state(phi.astype(np.float32), pi.astype(np.float32))
         return lat
 
-    with new() as ref:  # alone, on the streaming shape
-        ref.set_pass_config("stream")
+    with new() as ref:  # alone, on the batch shape
+        ref.set_pass_config(**T.batch_pass_config(N, nf, "f32"))
         ref.step(10, 0.01, "verlet")
         rphi, rpi = ref.get_all()
         rE = ref.energies().vector()
@@ -129,7 +129,8 @@ def test_batch_moves_members_to_the_streaming_shape():
         assert e.value.code == T.ESTATE
         b.step(10, 0.01, "verlet")
     for lat in lats:
-        assert lat.pass_config()["kind"] == "stream"
+        cfg = lat.pass_config()
+        assert cfg["kind"] == "stream" and cfg["z_chunk"] == 32 and cfg["threads"] == 256
         p, q = lat.get_all()
         assert np.array_equal(p, rphi) and np.array_equal(q, rpi)
         assert np.array_equal(lat.energies().vector(), rE)
