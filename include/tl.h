@@ -231,9 +231,10 @@ typedef struct {
 
 /* n Euler-Maruyama steps of phi_0:  phi <- phi + dt (Lap phi - m2 phi -
  * lambda/2 phi^3) + noise sqrt(dt) xi, xi a unit Gaussian per site and step:
- * Philox-2x64-10 of counter (site index [z][y][x], 2^63 + step) under key
- * seed, Box-Muller on the two words (u1 = (w0 >> 11 + 1) 2^-53,
- * u2 = (w1 >> 11) 2^-53, xi = sqrt(-2 ln u1) cos(2 pi u2)).  Steps are counted
+ * the sites of dense index s = [z][y][x] = 2k and 2k + 1 share Philox-2x64-10
+ * of counter (k, 2^63 + step) under key seed; Box-Muller on the two words
+ * (u1 = (w0 >> 11 + 1) 2^-53, u2 = (w1 >> 11) 2^-53, r = sqrt(-2 ln u1))
+ * gives xi(2k) = r cos(2 pi u2) and xi(2k + 1) = r sin(2 pi u2).  Steps are counted
  * from the last tl_set_state / tl_init_fluctuations.  Only phi_0 evolves (the
  * momenta are untouched); the energies are re-measured on demand.  Enqueues
  * only.  Errors: TL_EINVAL, TL_ESTATE (phi_0 not set, or in a batch), TL_ECUDA. */

@@ -354,12 +354,18 @@ LANGEVIN_STREAM = 1 << 63  # high bit of the second Philox counter word marks La
 
 
 def langevin_noise(N: int, seed: int, step: int) -> np.ndarray:
-    """Unit Gaussian per site for one step: Philox-2x64-10 of counter
-    (site index, 2^63 + step) under key seed, Box-Muller on the two words
-    (u1 in (0, 1], u2 in [0, 1)): xi = sqrt(-2 ln u1) cos(2 pi u2)."""
-    w = philox2x64(np.arange(N ** 3, dtype=np.uint64), LANGEVIN_STREAM + int(step), seed)
+    """Unit Gaussian per site for one step: the sites with dense indices 2k and
+    2k + 1 share Philox-2x64-10 of counter (k, 2^63 + step) under key seed;
+    Box-Muller on the two words (u1 in (0, 1], u2 in [0, 1)) gives the pair of
+    independent Gaussians sqrt(-2 ln u1) (cos, sin)(2 pi u2), the cosine for
+    site 2k and the sine for site 2k + 1."""
+    w = philox2x64(np.arange(N ** 3 // 2, dtype=np.uint64), LANGEVIN_STREAM + int(step), seed)
     u1, u2 = _uniforms(w)
-    return (np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)).reshape(N, N, N)
+    r = np.sqrt(-2.0 * np.log(u1))
+    xi = np.empty(N ** 3)
+    xi[0::2] = r * np.cos(2.0 * math.pi * u2)
+    xi[1::2] = r * np.sin(2.0 * math.pi * u2)
+    return xi.reshape(N, N, N)
 
 
 def langevin_run(N: int, kIR: float, phi, dt: float, nsteps: int, lam: float, m2: float, noise: float,

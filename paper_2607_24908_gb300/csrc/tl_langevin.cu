@@ -2,9 +2,11 @@
 // Sec. 2, Eq. 1): Euler-Maruyama steps
 //     phi <- phi + dt (Lap phi - m^2 phi - (lambda/2) phi^3) + noise sqrt(dt) xi,
 // with xi a unit Gaussian per site and step (the paper's field-valued random
-// number generator rescaled by 1/sqrt(dt)), drawn from Philox-2x64-10 of the
-// counter (site index, 2^63 + step) under key seed and turned into a Gaussian
-// by Box-Muller on the two output words.
+// number generator rescaled by 1/sqrt(dt)).  The sites with dense indices 2k
+// and 2k + 1 share one Philox-2x64-10 draw of counter (k, 2^63 + step) under
+// key seed; Box-Muller on its two words gives two independent Gaussians, the
+// cosine one for site 2k and the sine one for site 2k + 1 (half the generator
+// work of one draw per site, which bounds this kernel).
 //
 // One kernel per step, marching z-planes like the fused pass: phi at z-1, z,
 // z+1 in registers, the y-neighbour rows and edge sites through L1/L2; HBM
@@ -35,18 +37,23 @@ __device__ __forceinline__ void philox2x64_10(uint64_t c0, uint64_t c1, uint64_t
     o1 = c1;
 }
 
+// The two Gaussians of draw k: (cos, sin) halves of Box-Muller.
 template <typename T>
-__device__ __forceinline__ T gauss(uint64_t site, uint64_t ctr1, uint64_t seed);
+__device__ __forceinline__ void gauss2(uint64_t k, uint64_t ctr1, uint64_t seed, T &gc, T &gs);
 
 template <>
-__device__ __forceinline__ double gauss<double>(uint64_t site, uint64_t ctr1, uint64_t seed)
+__device__ __forceinline__ void gauss2<double>(uint64_t k, uint64_t ctr1, uint64_t seed, double &gc, double &gs)
 {
     uint64_t w0, w1;
-    philox2x64_10(site, ctr1, seed, w0, w1);
+    philox2x64_10(k, ctr1, seed, w0, w1);
     const double two53 = 9007199254740992.0;
     const double u1 = ((double)(w0 >> 11) + 1.0) / two53;
     const double u2 = (double)(w1 >> 11) / two53;
-    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+    const double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    gc = r * c;
+    gs = r * s;
 }
 
 // x 2^-53 for an integer 0 <= x <= 2^53, formed in FP32 without FP64
@@ -62,16 +69,18 @@ __device__ __forceinline__ float u53_f32(uint64_t x)
 }
 
 template <>
-__device__ __forceinline__ float gauss<float>(uint64_t site, uint64_t ctr1, uint64_t seed)
+__device__ __forceinline__ void gauss2<float>(uint64_t k, uint64_t ctr1, uint64_t seed, float &gc, float &gs)
 {
     uint64_t w0, w1;
-    philox2x64_10(site, ctr1, seed, w0, w1);
+    philox2x64_10(k, ctr1, seed, w0, w1);
     // the same 53-bit uniforms, Box-Muller in FP32 (the field is stored in FP32)
     const float u1 = u53_f32((w0 >> 11) + 1);
     const float u2 = u53_f32(w1 >> 11);
+    const float r = sqrtf(-2.0f * logf(u1));
     float s, c;
     sincospif(2.0f * u2, &s, &c);
-    return sqrtf(-2.0f * logf(u1)) * c;
+    gc = r * c;
+    gs = r * s;
 }
 
 template <typename T>
@@ -121,6 +130,10 @@ __global__ void __launch_bounds__(256) langevin_pass(const T *__restrict__ in, T
         ld(in + pz + rowm + x0, ym);
         ld(in + pz + rowp + x0, yp);
         const T a = __ldg(in + pz + row + xl), b = __ldg(in + pz + row + xr);
+        T xi[W];  // x0 and W are even: the thread's sites form whole pairs
+        const uint64_t k0 = (((uint64_t)z * N + y) * N + x0) >> 1;
+#pragma unroll
+        for (int j = 0; j < W; j += 2) gauss2<T>(k0 + j / 2, ctr1, seed, xi[j], xi[j + 1]);
         T o[W];
 #pragma unroll
         for (int j = 0; j < W; ++j) {
@@ -129,8 +142,7 @@ __global__ void __launch_bounds__(256) langevin_pass(const T *__restrict__ in, T
             const T right = j == W - 1 ? b : cu[j + 1];
             const T lap = (((left - c) + (right - c)) + ((ym[j] - c) + (yp[j] - c))) + ((zm[j] - c) + (zp[j] - c));
             const T drift = lap * inv_dx2 - m2 * c - half_lam * c * c * c;
-            const T xi = gauss<T>(((size_t)z * N + y) * N + x0 + j, ctr1, seed);
-            o[j] = (c + dt * drift) + amp * xi;
+            o[j] = (c + dt * drift) + amp * xi[j];
         }
 #pragma unroll
         for (int j = 0; j < W; ++j) {

@@ -454,6 +454,13 @@ def test_langevin_noise_is_unit_gaussian_and_independent():
     assert abs(np.mean(xi ** 4) - 3.0) < 0.1  # Gaussian kurtosis
     assert abs(np.corrcoef(xi.ravel(), xj.ravel())[0, 1]) < 5 / math.sqrt(n)
     assert np.array_equal(xi, o.langevin_noise(32, seed=5, step=0))
+    # the sites 2k, 2k+1 share one Box-Muller draw: uncorrelated, and their squared
+    # sum is -2 ln u1, exponential with mean 2 and variance 4 (a cosine reused for
+    # both sites would correlate them perfectly)
+    a, b = xi.ravel()[0::2], xi.ravel()[1::2]
+    assert abs(np.corrcoef(a, b)[0, 1]) < 5 / math.sqrt(n / 2)
+    r2 = a * a + b * b
+    assert abs(r2.mean() - 2.0) < 4 * 2.0 / math.sqrt(n / 2) and abs(r2.var() - 4.0) < 0.3
 
 
 def test_langevin_deterministic_relaxation_of_a_plane_wave():
