@@ -331,8 +331,8 @@ int tl_batch_step(tl_batch *batch, int n, double dt, tl_integrator integrator);
 void tl_batch_destroy(tl_batch *batch);
 
 /* Time candidate launch shapes of the fused pass on this lattice (both
- * kinds of tl_pass_config: z-planes per CTA from 4 to the whole lattice and
- * the tile rows of the streaming kernel, the warps of the TMA kernel) with
+ * kinds of tl_pass_config: z-planes per CTA from 4 to the whole lattice, the
+ * tile rows and CTA size of the streaming kernel, the warps of the TMA kernel) with
  * passes whose kick and drift coefficients are zero, which rewrite the state
  * unchanged, and keep the fastest.  Results are cached per (N, n_fields,
  * dtype, SM count) for the process and, if the environment variable

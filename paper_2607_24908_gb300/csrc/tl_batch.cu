@@ -352,16 +352,17 @@ extern "C" int tl_autotune(tl_lattice *L, double *best_ms_per_pass)
             return tl::set_geometry(L, it->second.t);
         }
     }
-    // candidates: the register-streaming pass with 256-thread CTAs (the shape
-    // the batched launch runs), tile rows of 32, 16 or 8 threads, and z-chunks
-    // from 4 planes to the whole lattice, plus the automatic choice; the TMA
-    // pass with 7 or 15 compute warps, the deepest ring that fits and the same
+    // candidates: the register-streaming pass with 256- or 512-thread CTAs
+    // (two or one per SM), tile rows of 32, 16 or 8 threads, and z-chunks from
+    // 4 planes to the whole lattice, plus the automatic choice; the TMA pass
+    // with 7 or 15 compute warps, the deepest ring that fits and the same
     // z-chunks
     std::vector<tl::PassTuning> cands;
     cands.push_back(tl::PassTuning{tl::kVariantLdg, 7, 0, 0, 0, 256, 0});
-    for (int txt : {32, 16, 8})
-        for (int zc = 4; zc <= L->N && zc <= 256; zc *= 2)
-            cands.push_back(tl::PassTuning{tl::kVariantLdg, 7, 0, zc, 0, 256, txt});
+    for (int threads : {256, 512})  // two or one CTAs per SM
+        for (int txt : {32, 16, 8})
+            for (int zc = 4; zc <= L->N && zc <= 256; zc *= 2)
+                cands.push_back(tl::PassTuning{tl::kVariantLdg, 7, 0, zc, 0, threads, txt});
     for (int cw : {7, 15}) {
         cands.push_back(tl::PassTuning{tl::kVariantTma, cw, 0, 0, 0, 256, 0});
         for (int zc = 4; zc <= L->N && zc <= 256; zc *= 2)
