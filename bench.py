@@ -304,12 +304,15 @@ def run_ours(args):
         for w in range(2):
             T.tl_set_state(lat.h, f, w, host[2 * f + w].numpy())
     T.tl_set_background(lat.h, E.a, E.b, False)
+    t1 = time.perf_counter()
     lat.step(args.steps, WL.dt, integ)
     E2 = lat.energies()
+    t2 = time.perf_counter()
     for f in range(WL.nf):
         for w in range(2):
             T.tl_get_state(lat.h, f, w, host[2 * f + w].numpy())
     t_e2e = time.perf_counter() - t0
+    args.e2e_phases = {"set_state_s": t1 - t0, "steps_and_energies_s": t2 - t1, "get_state_s": t0 + t_e2e - t2}
     t_e2e = max_over_ranks(t_e2e, ws, "cuda")
     state_bytes = 2 * WL.nf * sites * np.dtype(npd).itemsize
     lat.close()
@@ -345,7 +348,8 @@ def _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_ran
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": state_bytes / args.steps,
                     "d2h_bytes_per_step": (state_bytes + 136) / args.steps,
-                    "note": "state H2D once, K steps, energies + state D2H, per K-step job"},
+                    "note": "state H2D once, K steps, energies + state D2H, per K-step job",
+                    "phases": getattr(args, "e2e_phases", None)},
             "gpu_launches": launches,
             "clocks": clk,
             "physics": {"a": E.a, "hubble_resid": E.hubble_resid, "a_after_e2e": E2.a},
