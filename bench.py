@@ -66,16 +66,28 @@ def kernel_name(shape) -> str:
     return f"fused_pass_ldg<float,2> ({shape['threads']} threads)"
 
 
-def measured_traffic():
+def shape_tag(shape) -> str:
+    """The launch shape as written in the profile summary."""
+    if not shape:
+        return ""
+    if shape["kind"] == "tma":
+        return f"tma warps={shape['warps']} stages={shape['stages']} z_chunk={shape['z_chunk']}"
+    return f"stream threads={shape['threads']} tile_x={shape['tile_x']} z_chunk={shape['z_chunk']}"
+
+
+def measured_traffic(shape=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel source and launch shape (else None)."""
     try:
         txt = open(TRAFFIC_FILE).read()
     except OSError:
         return None
     h = re.search(r"kernel source sha256\[:16\]:\s*([0-9a-f]+)", txt)
     b = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
+    sh = re.search(r"launch shape of the capture:\s*(.+)", txt)
     if not h or not b or h.group(1) != kernel_hash():
+        return None
+    if shape is not None and (not sh or sh.group(1).strip() != shape_tag(shape)):
         return None
     return float(b.group(1))
 
@@ -343,7 +355,8 @@ def _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_ran
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
                          "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                         "traffic": measured_traffic() if N == WL.N else None, "algorithmic_bytes_per_launch": alg_bytes,
+                         "traffic": measured_traffic(getattr(args, "pass_shape", None)) if N == WL.N else None,
+                         "algorithmic_bytes_per_launch": alg_bytes,
                          "kernel": kernel_name(getattr(args, "pass_shape", None)), "ms_per_launch": ms_pass},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": state_bytes / args.steps,

@@ -48,17 +48,23 @@ thread_local char g_err[512] = "";
 
 tl::PassTuning tl::default_tuning(int N, int nf, int elem_bytes)
 {
-    const bool tma = elem_bytes == 4 && nf >= 2 && N >= 192;
-    tl::PassTuning t{tma ? tl::kVariantTma : tl::kVariantLdg, 7, 0, 0, 0, 256, 0};
+    (void)nf;
+    tl::PassTuning t{elem_bytes == 4 && N >= 192 ? tl::kVariantTma : tl::kVariantLdg, 7, 0, 0, 0, 256, 0};
+    // environment overrides (tuning experiments)
     const char *v = getenv("TL_PASS_VARIANT");
     if (v && strcmp(v, "tma") == 0) t.variant = tl::kVariantTma;
     if (v && strcmp(v, "ldg") == 0) t.variant = tl::kVariantLdg;
+    const char *cw = getenv("TL_BULK_WARPS"), *zc = getenv("TL_PASS_ZC");
+    if (t.variant == tl::kVariantTma) {  // measured: long z-chunks for the ring, 15 + 1 warps on large lattices
+        t.zc = N <= 192 ? 16 : 64;
+        t.cwarps = N >= 768 ? 15 : 7;
+    }
     if ((v = getenv("TL_PREFETCH"))) t.prefetch = atoi(v);
     if ((v = getenv("TL_LDG_THREADS"))) t.threads = atoi(v);
     if ((v = getenv("TL_LDG_TXT"))) t.txt = atoi(v);
-    if ((v = getenv("TL_BULK_WARPS"))) t.cwarps = atoi(v);
+    if (cw) t.cwarps = atoi(cw);
     if ((v = getenv("TL_BULK_STAGES"))) t.stages = atoi(v);
-    if ((v = getenv("TL_PASS_ZC"))) t.zc = atoi(v);
+    if (zc) t.zc = atoi(zc);
     return t;
 }
 

@@ -112,9 +112,10 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
 
 // Tuning from the environment (TL_PASS_VARIANT=ldg|bulk, TL_PREFETCH, TL_LDG_THREADS, TL_LDG_TXT,
 // TL_BULK_WARPS, TL_BULK_STAGES, TL_PASS_ZC), else the built-in defaults.
-// Launch shape a new lattice starts with: the TMA pass for FP32 with two or
-// more fields from N = 192 up, where it measured faster; the streaming pass
-// otherwise (FP64 is bound by FP64 arithmetic, one FP32 field by latency).
+// Launch shape a new lattice starts with: the TMA pass for FP32 from N = 192
+// up (z-chunks of 16 planes at 192, 64 above; 15 + 1 warps from N = 768),
+// where it measured faster; the streaming pass otherwise (FP64 is bound by
+// FP64 arithmetic, small lattices by latency).
 PassTuning default_tuning(int N, int nf, int elem_bytes);
 
 // One lattice of a batched (grouped) launch: its model, fields for this pass,

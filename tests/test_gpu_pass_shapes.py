@@ -87,11 +87,13 @@ def test_each_shape_against_oracle_expanding_fp64(shape):
 def test_default_shape_and_errors():
     with T.Lattice(192, 0.5, 2, "f32") as big, T.Lattice(128, 0.5, 2, "f32") as small:
         cfg = big.pass_config()
-        assert cfg["kind"] == "tma" and cfg["warps"] == 7 and 3 <= cfg["stages"] <= 8 and cfg["z_chunk"] >= 1
+        assert cfg["kind"] == "tma" and cfg["warps"] == 7 and 3 <= cfg["stages"] <= 8 and cfg["z_chunk"] == 16
         assert small.pass_config()["kind"] == "stream"
-        for nf, dtype in ((1, "f32"), (2, "f64")):  # one FP32 field, FP64: the streaming pass
-            with T.Lattice(256, 0.5, nf, dtype) as other:
-                assert other.pass_config()["kind"] == "stream"
+        with T.Lattice(256, 0.5, 1, "f32") as one:  # FP32 from 192: TMA, 64-plane chunks
+            c1 = one.pass_config()
+            assert (c1["kind"], c1["warps"], c1["z_chunk"]) == ("tma", 7, 64)
+        with T.Lattice(256, 0.5, 2, "f64") as f64:  # FP64: the streaming pass
+            assert f64.pass_config()["kind"] == "stream"
         bad = [dict(kind="tma", warps=8), dict(kind="tma", stages=2), dict(kind="tma", stages=9),
                dict(kind="tma", tile_x=16), dict(kind="stream", warps=7), dict(kind="stream", tile_x=12),
                dict(kind="stream", threads=128), dict(kind="stream", z_chunk=193)]
