@@ -84,13 +84,16 @@ typedef struct {
  * Rayleigh modulus, uniform phase, Hermitian pairs, drawn with Philox-2x64-10
  * (the paper's generator, Sec. 2) from counter (mode index, f) and key seed.
  * fluct_pi != 0 adds an independent draw with P = A omega_k/2 to pi_f
- * (counter (mode index, 8+f)), scaled by a0^(3-alpha). */
+ * (counter (mode index, 8+f)), scaled by a0^(3-alpha).  fixed_modulus != 0
+ * gives every mode the modulus sqrt(P(k)/L^3) exactly (random phase only)
+ * instead of the Rayleigh modulus; both have <|d(n)|^2> = P(k)/L^3. */
 typedef struct {
     double A;
     double meff2[TL_MAX_FIELDS];
     double phi0[TL_MAX_FIELDS];
     double pi0[TL_MAX_FIELDS];
     int fluct_pi;
+    int fixed_modulus;
 } tl_init_spec;
 
 /* Volume averages and background at the last integer time. */

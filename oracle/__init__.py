@@ -191,9 +191,10 @@ class InitSpec:
     0 < |n| < N/2 (k = kIR |n|) gets a complex amplitude with
     <|d(n)|^2> = P(k)/L^3, P = A/(2 omega_k), omega_k^2 = k^2 + meff2, so that
     <dphi^2> approximates the integral of P over d^3k/(2 pi)^3.  Modulus is
-    Rayleigh (sqrt(-ln u1)), phase 2 pi u2: a Gaussian field.  With
-    ``fluct_pi`` the momenta get an independent draw with P = A omega_k/2,
-    scaled by a0^(3-alpha).
+    Rayleigh (sqrt(-ln u1)), phase 2 pi u2: a Gaussian field; with
+    ``fixed_modulus`` every mode gets the modulus sqrt(P/L^3) exactly and a
+    random phase (same mean power).  With ``fluct_pi`` the momenta get an
+    independent draw with P = A omega_k/2, scaled by a0^(3-alpha).
     """
     A: float = 1e-10
     meff2: Sequence[float] = (3.0, 0.0, 0.0)
@@ -201,6 +202,7 @@ class InitSpec:
     pi0: Sequence[float] = (0.0, 0.0, 0.0)
     fluct_pi: bool = False
     a0: float = 1.0
+    fixed_modulus: bool = False
 
 
 def _mode_grid(N: int):
@@ -216,7 +218,7 @@ def _uniforms(words: np.ndarray):
     return u1, u2
 
 
-def gaussian_modes(N: int, kIR: float, power, seed: int, stream: int) -> np.ndarray:
+def gaussian_modes(N: int, kIR: float, power, seed: int, stream: int, fixed_modulus: bool = False) -> np.ndarray:
     """Complex Hermitian mode array d(n) (full N^3, numpy FFT order [z, y, x]).
 
     Each pair (n, -n) is drawn once, at the member that is canonical: nx > 0,
@@ -234,7 +236,7 @@ def gaussian_modes(N: int, kIR: float, power, seed: int, stream: int) -> np.ndar
     u1, u2 = _uniforms(words)
     L = 2.0 * math.pi / kIR
     P = power(kIR * r[live])
-    amp = np.sqrt(P / L ** 3) * np.sqrt(-np.log(u1))
+    amp = np.sqrt(P / L ** 3) * (1.0 if fixed_modulus else np.sqrt(-np.log(u1)))
     ph = 2.0 * math.pi * u2
     sgn = np.where(canon[live], 1.0, -1.0)
     d = np.zeros((N, N, N), dtype=np.complex128)
@@ -256,12 +258,14 @@ def init_fluctuations(p: Params, seed: int, spec: InitSpec):
     pi = np.empty((p.nf, N, N, N))
     for f in range(p.nf):
         m2 = spec.meff2[f]
-        d = gaussian_modes(N, p.kIR, lambda k: spec.A / (2.0 * np.sqrt(k * k + m2)), seed, f)
+        d = gaussian_modes(N, p.kIR, lambda k: spec.A / (2.0 * np.sqrt(k * k + m2)), seed, f,
+                           spec.fixed_modulus)
         phi[f] = spec.phi0[f] + modes_to_field(d)
         pi[f] = spec.pi0[f]
         if spec.fluct_pi:
             scale = spec.a0 ** (3.0 - p.alpha) if p.expanding else 1.0
-            dp = gaussian_modes(N, p.kIR, lambda k: spec.A * np.sqrt(k * k + m2) / 2.0, seed, 8 + f)
+            dp = gaussian_modes(N, p.kIR, lambda k: spec.A * np.sqrt(k * k + m2) / 2.0, seed, 8 + f,
+                                spec.fixed_modulus)
             pi[f] += scale * modes_to_field(dp)
     a0, b0 = 1.0, 0.0
     if p.expanding:

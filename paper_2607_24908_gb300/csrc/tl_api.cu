@@ -810,7 +810,7 @@ int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
             void *dst = L->buf[L->cur][which][f];
             if (fluct && spec->A > 0.0) {
                 cudaError_t ce = tl::launch_fill_modes(modes, N, L->kIR, spec->A, spec->meff2[f], which,
-                                                       seed, which == 0 ? (uint64_t)f : (uint64_t)(8 + f),
+                                                       spec->fixed_modulus ? 1 : 0, seed, which == 0 ? (uint64_t)f : (uint64_t)(8 + f),
                                                        L->sm_count, L->stream);
                 if (ce != cudaSuccess) { rc = fail(TL_ECUDA, "fill_modes: %s", cudaGetErrorString(ce)); break; }
                 cufftResult fr = cufftExecZ2D(plan, reinterpret_cast<cufftDoubleComplex *>(modes), real);

@@ -33,7 +33,7 @@ __device__ __forceinline__ int signed_mode(int i, int N) { return (i < N / 2) ? 
 
 // One entry of the half spectrum [iz][iy][ix], ix in [0, N/2].
 __global__ void fill_modes_kernel(double2 *modes, int N, double kIR, double A, double m2, int pi_spectrum,
-                                  uint64_t seed, uint64_t stream)
+                                  int fixed_modulus, uint64_t seed, uint64_t stream)
 {
     const int NH = N / 2 + 1;
     const size_t total = (size_t)N * N * NH;
@@ -58,7 +58,7 @@ __global__ void fill_modes_kernel(double2 *modes, int N, double kIR, double A, d
             const double om = sqrt(k * k + m2);
             const double P = pi_spectrum ? A * om / 2.0 : A / (2.0 * om);
             const double L = 2.0 * M_PI / kIR;
-            const double amp = sqrt(P / (L * L * L)) * sqrt(-log(u1));
+            const double amp = sqrt(P / (L * L * L)) * (fixed_modulus ? 1.0 : sqrt(-log(u1)));
             double s, c;
             sincos(2.0 * M_PI * u2, &s, &c);
             out = make_double2(amp * c, canon ? amp * s : -amp * s);
@@ -146,10 +146,11 @@ static unsigned grid_for(size_t n, int sm_count)
 }
 
 cudaError_t launch_fill_modes(double2 *modes, int N, double kIR, double A, double m2, int pi_spectrum,
-                              uint64_t seed, uint64_t stream, int sm_count, cudaStream_t s)
+                              int fixed_modulus, uint64_t seed, uint64_t stream, int sm_count, cudaStream_t s)
 {
     size_t total = (size_t)N * N * (N / 2 + 1);
-    fill_modes_kernel<<<grid_for(total, sm_count), 256, 0, s>>>(modes, N, kIR, A, m2, pi_spectrum, seed, stream);
+    fill_modes_kernel<<<grid_for(total, sm_count), 256, 0, s>>>(modes, N, kIR, A, m2, pi_spectrum, fixed_modulus,
+                                                                seed, stream);
     return cudaGetLastError();
 }
 

@@ -10,7 +10,7 @@ namespace tl {
 
 // Half-spectrum [N][N][N/2+1] of Hermitian Gaussian modes (see tl_init_spec).
 cudaError_t launch_fill_modes(double2 *modes, int N, double kIR, double A, double m2, int pi_spectrum,
-                              uint64_t seed, uint64_t stream, int sm_count, cudaStream_t s);
+                              int fixed_modulus, uint64_t seed, uint64_t stream, int sm_count, cudaStream_t s);
 // dst[pitched(i)] = (T)(base + scale * delta[i]) (delta may be NULL; delta dense).
 cudaError_t launch_assemble(int dtype, void *dst, const double *delta, size_t n, double base, double scale, int N,
                             long long P, long long PP, int sm_count, cudaStream_t s);

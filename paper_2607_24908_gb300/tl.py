@@ -45,7 +45,7 @@ class tl_potential(ctypes.Structure):
 class tl_init_spec(ctypes.Structure):
     _fields_ = [("A", ctypes.c_double), ("meff2", ctypes.c_double * MAX_FIELDS),
                 ("phi0", ctypes.c_double * MAX_FIELDS), ("pi0", ctypes.c_double * MAX_FIELDS),
-                ("fluct_pi", ctypes.c_int)]
+                ("fluct_pi", ctypes.c_int), ("fixed_modulus", ctypes.c_int)]
 
 
 class tl_langevin_params(ctypes.Structure):
@@ -195,8 +195,9 @@ def tl_set_potential(h, lam: float, q: float, m2: Sequence[float]):
     _check(lib().tl_set_potential(h, ctypes.byref(p)))
 
 
-def tl_init_fluctuations(h, seed: int, A: float, meff2, phi0, pi0=(0, 0, 0), fluct_pi: bool = False):
-    s = tl_init_spec(A, _f3(meff2), _f3(phi0), _f3(pi0), int(bool(fluct_pi)))
+def tl_init_fluctuations(h, seed: int, A: float, meff2, phi0, pi0=(0, 0, 0), fluct_pi: bool = False,
+                         fixed_modulus: bool = False):
+    s = tl_init_spec(A, _f3(meff2), _f3(phi0), _f3(pi0), int(bool(fluct_pi)), int(bool(fixed_modulus)))
     _check(lib().tl_init_fluctuations(h, ctypes.c_uint64(seed), ctypes.byref(s)))
 
 
@@ -452,8 +453,8 @@ class Lattice:
         tl_set_potential(self.h, lam, q, m2)
 
     def init_fluctuations(self, seed: int, A: float = 1e-10, meff2=(3.0, 0, 0), phi0=(1.0, 0, 0), pi0=(0, 0, 0),
-                          fluct_pi: bool = False):
-        tl_init_fluctuations(self.h, seed, A, meff2, phi0, pi0, fluct_pi)
+                          fluct_pi: bool = False, fixed_modulus: bool = False):
+        tl_init_fluctuations(self.h, seed, A, meff2, phi0, pi0, fluct_pi, fixed_modulus)
 
     def step(self, n: int, dt: float, integrator="verlet"):
         tl_step(self.h, n, dt, INTEGRATORS[integrator] if isinstance(integrator, str) else integrator)

@@ -139,15 +139,16 @@ def test_split_step_calls_match_single_call():
 
 # --- init and spectrum ------------------------------------------------------------------
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_init_fluctuations_two_fields_parity(dtype):
+@pytest.mark.parametrize("dtype,fixed", [("f64", False), ("f32", False), ("f64", True)])
+def test_init_fluctuations_two_fields_parity(dtype, fixed):
     """N = 48 (non-power-of-two FFT), two fields, momentum fluctuations on,
-    expanding: fields, b0 from the constraint."""
+    expanding: fields, b0 from the constraint (Rayleigh or fixed modulus)."""
     p = o.Params(N=48, nf=2, kIR=0.05, expanding=True, alpha=1.0, lam=1.0, q=100.0)
-    spec = o.InitSpec(A=1e-10, meff2=(3.0, 100.0, 0), phi0=(1.0, 0.0, 0), fluct_pi=True)
+    spec = o.InitSpec(A=1e-10, meff2=(3.0, 100.0, 0), phi0=(1.0, 0.0, 0), fluct_pi=True, fixed_modulus=fixed)
     ophi, opi, oa, ob = o.init_fluctuations(p, 77, spec)
     with make(p, dtype) as lat:
-        lat.init_fluctuations(77, A=1e-10, meff2=(3.0, 100.0, 0), phi0=(1.0, 0, 0), fluct_pi=True)
+        lat.init_fluctuations(77, A=1e-10, meff2=(3.0, 100.0, 0), phi0=(1.0, 0, 0), fluct_pi=True,
+                              fixed_modulus=fixed)
         gphi, gpi = lat.get_all()
         E = lat.energies()
     tol = 1e-9 if dtype == "f64" else 2e-2

@@ -370,6 +370,32 @@ def test_initial_field_spectrum_and_variance():
     assert P[0] < 1e-30
 
 
+def test_fixed_modulus_spectrum_is_exact():
+    """With a fixed modulus every live mode carries exactly |d(n)|^2 = P(k_n)/L^3, so the
+    measured shell spectrum of the field equals the shell mean of P to rounding and the
+    field variance equals sum_n P(k_n)/L^3 (no sampling scatter left to hide an error in
+    the power law, the cutoff or the normalisation); the phases stay random."""
+    N, A, m2 = 24, 1e-6, 3.0
+    p = o.Params(N=N, nf=1, kIR=0.5)
+    Pk = lambda k: A / (2.0 * np.sqrt(k * k + m2))
+    d = o.gaussian_modes(N, p.kIR, Pk, seed=4, stream=0, fixed_modulus=True)
+    n = np.rint(np.fft.fftfreq(N, 1.0 / N))
+    nz, ny, nx = np.meshgrid(n, n, n, indexing="ij")
+    r = np.sqrt(nx ** 2 + ny ** 2 + nz ** 2)
+    live = (r > 0) & (r < N / 2)
+    assert np.allclose(np.abs(d[live]) ** 2, Pk(p.kIR * r[live]) / p.L ** 3, rtol=1e-13, atol=0)
+    assert np.all(d[~live] == 0)
+    f = o.modes_to_field(d)
+    k, P, cnt = o.spectrum(p, f)
+    rr = r.ravel()
+    b = np.floor(rr + 0.5).astype(int)
+    expect = np.bincount(b, weights=Pk(p.kIR * rr) * live.ravel(), minlength=len(P)) / np.maximum(cnt, 1)
+    assert np.allclose(P[1:], expect[1:], rtol=1e-10, atol=1e-30)
+    assert abs(np.var(f) / (np.sum(Pk(p.kIR * r[live])) / p.L ** 3) - 1.0) < 1e-10
+    ph = np.angle(d[live & (nx > 0)])
+    assert abs(np.mean(np.cos(ph))) < 4 / math.sqrt(ph.size) and abs(np.mean(np.sin(ph))) < 4 / math.sqrt(ph.size)
+
+
 def test_init_fluctuations_two_fields_independent_and_b0():
     p = o.Params(N=16, nf=2, kIR=0.5, expanding=True, alpha=1.0, lam=1.0, q=100.0)
     spec = o.InitSpec(A=1e-10, meff2=(3.0, 100.0, 0), phi0=(1.0, 0.0, 0))
