@@ -672,7 +672,7 @@ def main():
                     choices=["step", "ensemble", "serve", "expanding256", "static32", "langevin", "su2"],
                     help="step: the 1024^3 fused step (default); ensemble: batched small lattices vs a plain loop; "
                          "serve: continuous batching of Poisson-arriving jobs vs a sequential loop")
-    ap.add_argument("--jobs", type=int, default=0, help="jobs for --mode ensemble (96) / serve (24)")
+    ap.add_argument("--jobs", type=int, default=0, help="jobs for --mode ensemble (96) / serve (16)")
     ap.add_argument("--ens-steps", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
