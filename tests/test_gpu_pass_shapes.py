@@ -137,3 +137,28 @@ def test_batch_moves_members_to_the_batch_shape():
         assert np.array_equal(p, rphi) and np.array_equal(q, rpi)
         assert np.array_equal(lat.energies().vector(), rE)
         lat.close()
+
+
+def test_ragged_at_scale_tma_default_equals_stream():
+    """N = 500, two FP32 fields: the default TMA shape has ragged tiles in every direction
+    (x tiles of 128 with a last one of 116 sites, y tiles of 7 rows with a last one of 3,
+    z-chunks of 64 planes with a last one of 52); two Verlet steps give bitwise the fields
+    of the streaming kernel."""
+    N, nf = 500, 2
+    rng = np.random.default_rng(17)
+    phi = (rng.standard_normal((nf, N, N, N), dtype=np.float32) * np.float32(1e-2)
+           + np.array([1.0, 0.0], np.float32)[:, None, None, None])
+    pi = rng.standard_normal((nf, N, N, N), dtype=np.float32) * np.float32(1e-2)
+    out = []
+    for shape in (None, dict(kind="stream")):
+        with T.Lattice(N, 0.1, nf, "f32") as lat:
+            if shape:
+                lat.set_pass_config(**shape)
+            else:
+                cfg = lat.pass_config()
+                assert cfg["kind"] == "tma" and cfg["z_chunk"] == 64
+            lat.set_potential(1.0, 10.0, (0.0, 0.2, 0.0))
+            lat.set_state(phi, pi)
+            lat.step(2, 0.01, "verlet")
+            out.append(lat.get_all())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
