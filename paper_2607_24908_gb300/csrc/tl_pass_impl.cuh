@@ -21,6 +21,8 @@
 #include <cuda.h>
 #include <math.h>
 
+#include <atomic>
+
 #include "tl_internal.cuh"
 
 namespace tl {
@@ -836,20 +838,39 @@ __global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Mo
     cta_reduce_finalize<NQ, sizeof(T) == 4>(accd, m, c, sc, slots, grid_bid(), grid_nblocks());
 }
 
+// The dynamic shared-memory limit of a kernel is a per-device attribute: raise
+// it once per device and kernel (thread-safe; a lower request needs no call).
+constexpr int kMaxDevices = 64;
+
+template <typename K>
+static cudaError_t ensure_smem_attribute(K kern, size_t smem, std::atomic<size_t> (*configured)[2], int slot)
+{
+    if (smem == 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::atomic<size_t> &done = configured[dev][slot];
+    if (smem <= done.load(std::memory_order_acquire)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    size_t cur = done.load(std::memory_order_relaxed);
+    while (smem > cur && !done.compare_exchange_weak(cur, smem, std::memory_order_release)) {
+    }
+    return cudaSuccess;
+}
+
 template <typename T, int NF, bool MEASURE>
 static cudaError_t launch_tma(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,
                               const TmaMaps &maps, Scalars *sc, double *slots, cudaStream_t s)
 {
     // 7 + 1 warps (two CTAs per SM) or 15 + 1 warps (one CTA per SM): 16
     // warps per SM, at most 4 per SM sub-partition, so 128 registers a thread
-    static size_t configured[2] = {0, 0};
+    static std::atomic<size_t> configured[kMaxDevices][2];
     const int big = g.cwarps > 7 ? 1 : 0;
     auto kern = big ? fused_pass_tma<T, NF, MEASURE, 512> : fused_pass_tma<T, NF, MEASURE, 256>;
-    if (g.smem > configured[big]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-        if (e != cudaSuccess) return e;
-        configured[big] = g.smem;
-    }
+    cudaError_t e = ensure_smem_attribute(kern, g.smem, configured, big);
+    if (e != cudaSuccess) return e;
     kern<<<g.grid, 32 * (g.cwarps + 1), g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, g.stages, g.lpad, maps, sc, slots);
     return cudaGetLastError();
 }
@@ -858,13 +879,10 @@ template <typename T, int NF, bool MEASURE, int D, int NT>
 static cudaError_t launch_ldg(const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g, Scalars *sc,
                               double *slots, cudaStream_t s)
 {
-    static size_t configured = 0;
+    static std::atomic<size_t> configured[kMaxDevices][2];
     auto kern = fused_pass_ldg<T, NF, MEASURE, D, NT>;
-    if (g.smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
-        if (e != cudaSuccess) return e;
-        configured = g.smem;
-    }
+    cudaError_t e = ensure_smem_attribute(kern, g.smem, configured, 0);
+    if (e != cudaSuccess) return e;
     kern<<<g.grid, NT, g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, sc, slots);
     return cudaGetLastError();
 }
