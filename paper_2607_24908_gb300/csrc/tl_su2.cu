@@ -90,77 +90,255 @@ __device__ __forceinline__ void sincos_t<float>(float a, float *s, float *c) { s
 template <>
 __device__ __forceinline__ void sincos_t<double>(double a, double *s, double *c) { sincos(a, s, c); }
 
-// One leapfrog step of site (x, y, z) (all three links).
+// The rotation of the drift, exp(i dt e.s) = cos(theta) + i f e.s with
+// theta = dt |e| and f = sin(theta) / |e| = dt sin(theta) / theta, from
+// q2 = |e|^2.  Small angles (theta^2 below kSmallTheta2, the common case: the
+// per-step angle is tiny) use the Taylor series of sin(theta)/theta and
+// cos(theta) in theta^2, truncated where the first omitted term is below half
+// an ulp of the result (FP32: theta < 1/2, terms to theta^8, first omitted
+// term < 3e-10; FP64: theta < 1/4, terms to theta^10 / theta^12, < 1e-17): no
+// square root, no division, no trigonometric call.  Larger angles take
+// sincos of theta.
 template <typename T>
-__device__ __forceinline__ void su2_site(const T *__restrict__ U, T *__restrict__ Uout, T *__restrict__ E, int N,
-                                         size_t n3, T dt, int x, int y, int z)
+constexpr T kSmallTheta2 = sizeof(T) == 4 ? (T)0.25 : (T)0.0625;
+
+template <typename T>
+__device__ __forceinline__ void drift_rotation(T q2, T dt, T *f, T *cs)
 {
-    const size_t s = ((size_t)z * N + y) * N + x;
-    // signed index steps to the periodic neighbours +mu and -mu (the wrap folded
-    // in; a step in one axis never changes the wrap of another)
-    const long long NN = (long long)N * N;
-    const long long up[3] = {x + 1 == N ? 1LL - N : 1LL, y + 1 == N ? (1LL - N) * N : (long long)N,
-                             z + 1 == N ? (1LL - N) * NN : NN};
-    const long long dn[3] = {x == 0 ? N - 1LL : -1LL, y == 0 ? (N - 1LL) * N : -(long long)N,
-                             z == 0 ? (N - 1LL) * NN : -NN};
-    Q<T> Ux[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) Ux[i] = ldU(U, n3, i, s);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        Q<T> S{0, 0, 0, 0};
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            if (j == i) continue;
-            const size_t xpi = s + up[i];
-            const size_t xpj = s + up[j];
-            const size_t xmj = s + dn[j];
-            const size_t xpimj = s + up[i] + dn[j];
-            // forward staple U_j(x+i) U_i(x+j)^+ U_j(x)^+
-            const Q<T> f = qmul(qmul(ldU(U, n3, j, xpi), qadj(ldU(U, n3, i, xpj))), qadj(Ux[j]));
-            // backward staple U_j(x+i-j)^+ U_i(x-j)^+ U_j(x-j)
-            const Q<T> Ujm = ldU(U, n3, j, xmj);
-            const Q<T> b = qmul(qmul(qadj(ldU(U, n3, j, xpimj)), qadj(ldU(U, n3, i, xmj))), Ujm);
-            S = qadd(S, qadd(f, b));
+    const T t2 = dt * dt * q2;
+    if (t2 < kSmallTheta2<T>) {
+        T sc, cc;
+        if (sizeof(T) == 4) {
+            // sin(t)/t = sum_k (-t^2)^k / (2k+1)!,  cos(t) = sum_k (-t^2)^k / (2k)!
+            sc = (T)(1.0 / 362880.0);
+            sc = sc * t2 - (T)(1.0 / 5040.0);
+            sc = sc * t2 + (T)(1.0 / 120.0);
+            sc = sc * t2 - (T)(1.0 / 6.0);
+            cc = (T)(1.0 / 40320.0);
+            cc = cc * t2 - (T)(1.0 / 720.0);
+            cc = cc * t2 + (T)(1.0 / 24.0);
+            cc = cc * t2 - (T)(1.0 / 2.0);
+        } else {
+            sc = (T)(-1.0 / 39916800.0);
+            sc = sc * t2 + (T)(1.0 / 362880.0);
+            sc = sc * t2 - (T)(1.0 / 5040.0);
+            sc = sc * t2 + (T)(1.0 / 120.0);
+            sc = sc * t2 - (T)(1.0 / 6.0);
+            cc = (T)(1.0 / 479001600.0);
+            cc = cc * t2 - (T)(1.0 / 3628800.0);
+            cc = cc * t2 + (T)(1.0 / 40320.0);
+            cc = cc * t2 - (T)(1.0 / 720.0);
+            cc = cc * t2 + (T)(1.0 / 24.0);
+            cc = cc * t2 - (T)(1.0 / 2.0);
         }
-        const Q<T> P = qmul(Ux[i], S);
-        T *e = E + (size_t)(3 * i) * n3 + s;
-        const T e1 = e[0] - (T)2 * dt * P.x;
-        const T e2 = e[n3] - (T)2 * dt * P.y;
-        const T e3 = e[2 * n3] - (T)2 * dt * P.z;
-        e[0] = e1;
-        e[n3] = e2;
-        e[2 * n3] = e3;
-        // drift: exp(i dt e.s) = cos(dt|e|) + i sin(dt|e|) e/|e|
-        const T nrm = sqrt(e1 * e1 + e2 * e2 + e3 * e3);
-        T sn, cs;
-        sincos_t<T>(dt * nrm, &sn, &cs);
-        const T f = nrm > (T)0 ? sn / nrm : dt;
-        Q<T> u = qmul(Q<T>{cs, f * e1, f * e2, f * e3}, Ux[i]);
-        if (sizeof(T) == 4) {  // FP32 storage: keep the link on the unit sphere
-            const T r = rsqrt(u.w * u.w + u.x * u.x + u.y * u.y + u.z * u.z);
-            u = Q<T>{u.w * r, u.x * r, u.y * r, u.z * r};
-        }
-        stU(Uout, n3, i, s, u);
+        *f = dt * (sc * t2 + (T)1);
+        *cs = cc * t2 + (T)1;
+    } else {
+        const T nrm = sqrt(q2);
+        T sn;
+        sincos_t<T>(dt * nrm, &sn, cs);
+        *f = sn / nrm;
     }
 }
 
-// CTAs of 32 x 8 site columns; each thread marches a chunk of z-planes, so the
-// tile's links of planes z-1, z and z+1 are reused from L1 by the staples of
-// the neighbouring threads and of the next plane (most neighbour links are
-// then L1 hits instead of L2 round trips).
+// Im(W^+ (0, v) W) for W = w + i u.s: the vector v rotated by the adjoint
+// action of W^+, (w^2 - |u|^2) v + 2 (u.v) u + 2 w (u x v) (the same value as
+// the two quaternion products, for any W).
+template <typename T>
+__device__ __forceinline__ void rot_adj(const Q<T> &W, T vx, T vy, T vz, T &ox, T &oy, T &oz)
+{
+    const T uv2 = (T)2 * (W.x * vx + W.y * vy + W.z * vz);
+    const T s = W.w * W.w - (W.x * W.x + W.y * W.y + W.z * W.z);
+    const T w2 = W.w + W.w;
+    const T cx = W.y * vz - W.z * vy, cy = W.z * vx - W.x * vz, cz = W.x * vy - W.y * vx;
+    ox = s * vx + uv2 * W.x + w2 * cx;
+    oy = s * vy + uv2 * W.y + w2 * cy;
+    oz = s * vz + uv2 * W.z + w2 * cz;
+}
+
+// One pass per step over CTAs of 32 x 8 site columns, each marching a chunk of
+// z-planes.  The force on U_i(x) is Im[U_i(x) S_i(x)] with the staples S of
+// Sec. 4; in terms of the plaquettes
+//   P_ij(x) = U_i(x) U_j(x+i) U_i(x+j)^+ U_j(x)^+,   V_ij = Im P_ij = -V_ji,
+// U_i f_ij(x) = P_ij(x) and U_i b_ij(x) = W^+ P_ij(x-j)^+ W with W = U_j(x-j), so
+//   Im[U_i S_i](x) = sum_{j != i} V_ij(x) - R(W^+) V_ij(x-j),
+// R(W^+) the rotation of rot_adj.  Each plaquette is then formed once per site
+// (three per site, instead of four staples per link) and shared through shared
+// memory: per plane, the CTA first forms V_xy, V_xz, V_yz of its tile plus the
+// -x / -y halo it needs, then updates its links; V_xz and V_yz of the previous
+// plane are kept for the -z terms.
+//
+// The link records of a plane's tile with a one-site halo, (kSu2Ty + 2) x
+// (kSu2Tx + 2) sites x 3 directions, are copied into a ring of shared-memory
+// stages with cp.async (16-byte chunks, addresses wrapped periodically by the
+// copying thread) one plane ahead of the compute.  Stage s holds plane z with
+// (z - z0 + 1) % 4 == s: planes z-1, z, z+1 are read while z+2 lands.
 constexpr int kSu2Tx = 32, kSu2Ty = 8;
+constexpr int kSu2Hx = kSu2Tx + 2, kSu2Hy = kSu2Ty + 2;  // link tile with its one-site halo
+constexpr int kSu2StageRecs = 3 * kSu2Hy * kSu2Hx;     // 1020 link records per plane
+constexpr int kSu2Stages = 4;
+constexpr int kSu2Px = kSu2Tx + 1, kSu2Py = kSu2Ty + 1;  // plaquette tile with the -x / -y halo
+constexpr int kSu2PlaqRecs = 3 * kSu2Py * kSu2Px;      // 891 per buffer (V_xy, V_xz, V_yz)
+constexpr int kSu2HaloJobs = 2 * kSu2Tx + 2 * kSu2Ty;   // row y0-1: V_xy, V_yz; column x0-1: V_xy, V_xz
 
 template <typename T>
-__global__ void __launch_bounds__(256) su2_pass(const T *__restrict__ U, T *__restrict__ Uout, T *__restrict__ E,
-                                                int N, int zc, T dt)
+struct alignas(4 * sizeof(T)) Rec {
+    T w, x, y, z;
+};
+
+template <typename T>
+constexpr size_t su2_tiled_smem()
 {
-    const int x = blockIdx.x * kSu2Tx + (int)(threadIdx.x % kSu2Tx);
-    const int y = blockIdx.y * kSu2Ty + (int)(threadIdx.x / kSu2Tx);
-    if (x >= N || y >= N) return;
+    return (size_t)(kSu2Stages * kSu2StageRecs + 2 * kSu2PlaqRecs) * sizeof(Rec<T>);
+}
+
+__device__ __forceinline__ void cp_async_cg16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
+    su2_pass(const T *__restrict__ U, T *__restrict__ Uout, T *__restrict__ E, int N, int zc, T dt)
+{
+    extern __shared__ __align__(16) unsigned char su2_raw[];
+    Rec<T> *ring = reinterpret_cast<Rec<T> *>(su2_raw);
+    Rec<T> *plaq = ring + kSu2Stages * kSu2StageRecs;
+    const int tid = threadIdx.x;
+    const int tx = tid % kSu2Tx, ty = tid / kSu2Tx;
+    const int x0 = blockIdx.x * kSu2Tx, y0 = blockIdx.y * kSu2Ty;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < N && y < N;
     const size_t n3 = (size_t)N * N * N;
+    const size_t NN = (size_t)N * N;
     const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, N);
-    for (int z = z0; z < z1; ++z) su2_site(U, Uout, E, N, n3, dt, x, y, z);
+
+    // this thread's copy chunks: chunk r of a stage is half (r % C) of record
+    // r / C = (i * Hy + ry) * Hx + rx; its source packed as wx | wy << 11 |
+    // i << 22 | half << 24 (N <= 1290 < 2^11)
+    constexpr int C = (int)sizeof(T) / 4;
+    constexpr int kChunks = kSu2StageRecs * C;
+    constexpr int kSlots = (kChunks + 255) / 256;
+    unsigned src[kSlots];
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k) {
+        const int r = tid + 256 * k;
+        const int rec = r / C, half = r % C;
+        const int i = rec / (kSu2Hy * kSu2Hx), q = rec % (kSu2Hy * kSu2Hx);
+        const int wx = (x0 - 1 + q % kSu2Hx + N) % N, wy = (y0 - 1 + q / kSu2Hx + N) % N;
+        src[k] = (unsigned)wx | (unsigned)wy << 11 | (unsigned)(i & 3) << 22 | (unsigned)half << 24;
+    }
+    auto copy_plane = [&](int z) {
+        const int zz = z < 0 ? z + N : (z >= N ? z - N : z);
+        unsigned char *st = reinterpret_cast<unsigned char *>(ring + ((z - z0 + 1) & (kSu2Stages - 1)) * kSu2StageRecs);
+        const T *Uz = U + (size_t)zz * NN * 4;
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k) {
+            const int r = tid + 256 * k;
+            const unsigned v = src[k];
+            const size_t rec = (size_t)((v >> 22) & 3u) * n3 + (size_t)((v >> 11) & 2047u) * N + (v & 2047u);
+            if (r < kChunks) cp_async_cg16(st + (size_t)r * 16, Uz + rec * 4 + (v >> 24) * (16 / sizeof(T)));
+        }
+        cp_async_commit();
+    };
+    // link i at tile position (rx, ry) of the plane with relative index zr = z - z0 + 1
+    auto link = [&](int i, int rx, int ry, int zr) -> Q<T> {
+        const Rec<T> v = ring[(zr & (kSu2Stages - 1)) * kSu2StageRecs + (i * kSu2Hy + ry) * kSu2Hx + rx];
+        return Q<T>{v.w, v.x, v.y, v.z};
+    };
+    // V_ij at tile position (rx, ry) of plane zr (i < j; reads planes zr and zr + 1)
+    auto plaq_im = [&](int i, int j, int rx, int ry, int zr) -> Rec<T> {
+        const Q<T> a = link(i, rx, ry, zr);
+        const Q<T> b = link(j, rx + (i == 0), ry + (i == 1), zr + (i == 2));
+        const Q<T> c = link(i, rx + (j == 0), ry + (j == 1), zr + (j == 2));
+        const Q<T> d = link(j, rx, ry, zr);
+        const Q<T> p = qmul(qmul(a, b), qmul(qadj(c), qadj(d)));
+        return Rec<T>{(T)0, p.x, p.y, p.z};
+    };
+    auto pidx = [](int buf, int k, int rx, int ry) { return buf * kSu2PlaqRecs + (k * kSu2Py + ry) * kSu2Px + rx; };
+    const int rx = tx + 1, ry = ty + 1;
+
+    copy_plane(z0 - 1);
+    copy_plane(z0);
+    copy_plane(z0 + 1);
+    cp_async_wait_all();
+    __syncthreads();
+    // V_xz, V_yz of plane z0 - 1 (relative index 0) for the first plane's -z terms
+    if (active) {
+        plaq[pidx(1, 1, rx, ry)] = plaq_im(0, 2, rx, ry, 0);
+        plaq[pidx(1, 2, rx, ry)] = plaq_im(1, 2, rx, ry, 0);
+    }
+    for (int z = z0; z < z1; ++z) {
+        const int zr = z - z0 + 1;
+        const int cur = (z - z0) & 1;
+        cp_async_wait_all();
+        __syncthreads();  // plane z+1 landed; the stage of plane z-2 and plaquette buffer cur are free
+        if (z + 2 <= z1) copy_plane(z + 2);
+        const size_t s = (size_t)z * NN + (size_t)y * N + x;
+        T eo[9];
+        Rec<T> V[3];
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) eo[c] = E[(size_t)c * n3 + s];
+            V[0] = plaq_im(0, 1, rx, ry, zr);
+            V[1] = plaq_im(0, 2, rx, ry, zr);
+            V[2] = plaq_im(1, 2, rx, ry, zr);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) plaq[pidx(cur, k, rx, ry)] = V[k];
+        }
+        if (tid < kSu2HaloJobs) {  // halo plaquettes: row y0-1 (V_xy, V_yz), column x0-1 (V_xy, V_xz)
+            const bool row = tid < 2 * kSu2Tx;
+            const int hx = row ? 1 + tid % kSu2Tx : 0;
+            const int hy = row ? 0 : 1 + (tid - 2 * kSu2Tx) % kSu2Ty;
+            const int k = row ? (tid < kSu2Tx ? 0 : 2) : (tid < 2 * kSu2Tx + kSu2Ty ? 0 : 1);
+            plaq[pidx(cur, k, hx, hy)] = k == 0   ? plaq_im(0, 1, hx, hy, zr)
+                                         : k == 1 ? plaq_im(0, 2, hx, hy, zr)
+                                                  : plaq_im(1, 2, hx, hy, zr);
+        }
+        __syncthreads();  // the plane's plaquettes are complete
+        if (!active) continue;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T Fx = 0, Fy = 0, Fz = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (j == i) continue;
+                const int k = i + j - 1;  // (0,1) -> 0, (0,2) -> 1, (1,2) -> 2
+                const T sg = i < j ? (T)1 : (T)-1;
+                // V_ij(x - j) and W = U_j(x - j)
+                const Rec<T> vn = j == 0   ? plaq[pidx(cur, k, rx - 1, ry)]
+                                  : j == 1 ? plaq[pidx(cur, k, rx, ry - 1)]
+                                           : plaq[pidx(cur ^ 1, k, rx, ry)];
+                const Q<T> W = j == 0 ? link(0, rx - 1, ry, zr) : j == 1 ? link(1, rx, ry - 1, zr) : link(2, rx, ry, zr - 1);
+                T ox, oy, oz;
+                rot_adj(W, vn.x, vn.y, vn.z, ox, oy, oz);
+                Fx += sg * (V[k].x - ox);
+                Fy += sg * (V[k].y - oy);
+                Fz += sg * (V[k].z - oz);
+            }
+            const T e1 = eo[3 * i] - (T)2 * dt * Fx;
+            const T e2 = eo[3 * i + 1] - (T)2 * dt * Fy;
+            const T e3 = eo[3 * i + 2] - (T)2 * dt * Fz;
+            T *ei = E + (size_t)(3 * i) * n3 + s;
+            ei[0] = e1;
+            ei[n3] = e2;
+            ei[2 * n3] = e3;
+            // drift: exp(i dt e.s) = cos(dt|e|) + i sin(dt|e|) e/|e|
+            T f, cs;
+            drift_rotation<T>(e1 * e1 + e2 * e2 + e3 * e3, dt, &f, &cs);
+            Q<T> u = qmul(Q<T>{cs, f * e1, f * e2, f * e3}, link(i, rx, ry, zr));
+            if (sizeof(T) == 4) {  // FP32 storage: keep the link on the unit sphere
+                const T r = rsqrt(u.w * u.w + u.x * u.x + u.y * u.y + u.z * u.z);
+                u = Q<T>{u.w * r, u.x * r, u.y * r, u.z * r};
+            }
+            stU(Uout, n3, i, s, u);
+        }
+    }
+    cp_async_wait_all();
 }
 
 // Per-CTA partial sums of |e|^2/2, 2(1 - Re P_ij) and |G|^2, and the CTA's
@@ -443,19 +621,36 @@ int tl_su2_step(tl_su2 *Y, int n, double dt)
     if (!Y->has_state) return tl::fail(TL_ESTATE, "no state");
     const int N = Y->N;
     const int gx = (N + kSu2Tx - 1) / kSu2Tx, gy = (N + kSu2Ty - 1) / kSu2Ty;
-    // z-chunk: as long as possible (more reuse) while the grid keeps ~8 CTAs per SM
+    const size_t smem = Y->dtype == TL_F32 ? su2_tiled_smem<float>() : su2_tiled_smem<double>();
+    int per_sm = 0;
+    if (Y->dtype == TL_F32) {
+        SU_CK(cudaFuncSetAttribute(su2_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SU_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, su2_pass<float>, 256, smem));
+    } else {
+        SU_CK(cudaFuncSetAttribute(su2_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SU_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, su2_pass<double>, 256, smem));
+    }
+    // z-chunk: minimise (waves of CTAs) x (planes per CTA + the ~3 planes of
+    // halo copies and the first plane's extra plaquettes), i.e. long chunks
+    // without a ragged last wave
+    const long slots = (long)(Y->sm_count > 0 ? Y->sm_count : 152) * (per_sm > 0 ? per_sm : 1);
     int zc = N;
-    while (zc > 1 && (long)gx * gy * ((N + zc - 1) / zc) < 8L * (Y->sm_count > 0 ? Y->sm_count : 152)) zc = (zc + 1) / 2;
+    long best = -1;
+    for (int c = N; c >= 1; --c) {
+        const long ctas = (long)gx * gy * ((N + c - 1) / c);
+        const long cost = (ctas + slots - 1) / slots * (long)(c + 3);
+        if (best < 0 || cost < best) best = cost, zc = c;
+    }
     const dim3 grid(gx, gy, (N + zc - 1) / zc);
     for (int k = 0; k < n; ++k) {
         if (Y->dtype == TL_F32)
-            su2_pass<float><<<grid, 256, 0, Y->stream>>>(static_cast<const float *>(Y->U[Y->cur]),
-                                                         static_cast<float *>(Y->U[Y->cur ^ 1]),
-                                                         static_cast<float *>(Y->E), N, zc, (float)dt);
+            su2_pass<float><<<grid, 256, smem, Y->stream>>>(static_cast<const float *>(Y->U[Y->cur]),
+                                                            static_cast<float *>(Y->U[Y->cur ^ 1]),
+                                                            static_cast<float *>(Y->E), N, zc, (float)dt);
         else
-            su2_pass<double><<<grid, 256, 0, Y->stream>>>(static_cast<const double *>(Y->U[Y->cur]),
-                                                          static_cast<double *>(Y->U[Y->cur ^ 1]),
-                                                          static_cast<double *>(Y->E), N, zc, dt);
+            su2_pass<double><<<grid, 256, smem, Y->stream>>>(static_cast<const double *>(Y->U[Y->cur]),
+                                                             static_cast<double *>(Y->U[Y->cur ^ 1]),
+                                                             static_cast<double *>(Y->E), N, zc, dt);
         SU_CK(cudaGetLastError());
         Y->cur ^= 1;
     }

@@ -33,6 +33,26 @@ def test_su2_leapfrog_matches_oracle(dtype, N, tol):
     assert abs(m[2] - np.max(np.sqrt(np.sum(G * G, axis=0)))) < max(tol, 1e-12) * 100
 
 
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_su2_large_rotation_angles_match_oracle(dtype, tol):
+    """dt = 0.25 with |e| ~ 2.4: per-step drift angles dt |e| on both sides of the
+    kernel's small-angle cut (series below, sincos above), against the oracle's sincos."""
+    N, dt, steps = 8, 0.25, 4
+    U0 = random_su2_links(N, seed=3, amp=0.6)
+    E0 = 1.5 * np.random.default_rng(2).standard_normal((3, 3, N, N, N))
+    theta = dt * np.sqrt(np.sum(E0 * E0, axis=1))
+    assert np.mean(theta < 0.25) > 0.02 and np.mean(theta > 0.5) > 0.3
+    npd = np.float32 if dtype == "f32" else np.float64
+    U0, E0 = U0.astype(npd), E0.astype(npd)
+    with T.SU2(N, dtype) as lat:
+        lat.set_state(U0, E0)
+        lat.step(steps, dt)
+        U, E = lat.get_state()
+    oU, oE = Y.step(U0.astype(np.float64), E0.astype(np.float64), dt, steps)
+    assert np.max(np.abs(U - oU)) < tol
+    assert np.max(np.abs(E - oE)) / np.max(np.abs(oE)) < tol
+
+
 def test_su2_gauss_law_and_energy_on_device():
     """From random links and E = 0, Gauss's law stays at rounding level; the
     energy measured with the leapfrog's half-step E deviates at O(dt), so the
