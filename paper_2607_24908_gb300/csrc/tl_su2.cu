@@ -164,21 +164,21 @@ __device__ __forceinline__ void rot_adj(const Q<T> &W, T vx, T vy, T vz, T &ox, 
 //   Im[U_i S_i](x) = sum_{j != i} V_ij(x) - R(W^+) V_ij(x-j),
 // R(W^+) the rotation of rot_adj.  Each plaquette is then formed once per site
 // (three per site, instead of four staples per link) and shared through shared
-// memory: per plane, the CTA first forms V_xy, V_xz, V_yz of its tile plus the
-// -x / -y halo it needs, then updates its links; V_xz and V_yz of the previous
-// plane are kept for the -z terms.
+// memory: V_xy, V_xz, V_yz of the CTA's tile plus the -x / -y halo it needs,
+// in three buffers (planes z-1, z, and z+1 being formed).
 //
 // The link records of a plane's tile with a one-site halo, (kSu2Ty + 2) x
 // (kSu2Tx + 2) sites x 3 directions, are copied into a ring of shared-memory
 // stages with cp.async (16-byte chunks, addresses wrapped periodically by the
-// copying thread) one plane ahead of the compute.  Stage s holds plane z with
-// (z - z0 + 1) % 4 == s: planes z-1, z, z+1 are read while z+2 lands.
+// copying thread) one plane ahead of their first use.  Stage s holds the
+// plane with relative index (z - z0 + 1) % 4 == s.
 constexpr int kSu2Tx = 32, kSu2Ty = 8;
 constexpr int kSu2Hx = kSu2Tx + 2, kSu2Hy = kSu2Ty + 2;  // link tile with its one-site halo
 constexpr int kSu2StageRecs = 3 * kSu2Hy * kSu2Hx;     // 1020 link records per plane
 constexpr int kSu2Stages = 4;
 constexpr int kSu2Px = kSu2Tx + 1, kSu2Py = kSu2Ty + 1;  // plaquette tile with the -x / -y halo
 constexpr int kSu2PlaqRecs = 3 * kSu2Py * kSu2Px;      // 891 per buffer (V_xy, V_xz, V_yz)
+constexpr int kSu2PlaqBufs = 3;                        // planes z-1 (read), z (read), z+1 (written)
 constexpr int kSu2HaloJobs = 2 * kSu2Tx + 2 * kSu2Ty;   // row y0-1: V_xy, V_yz; column x0-1: V_xy, V_xz
 
 template <typename T>
@@ -189,7 +189,7 @@ struct alignas(4 * sizeof(T)) Rec {
 template <typename T>
 constexpr size_t su2_tiled_smem()
 {
-    return (size_t)(kSu2Stages * kSu2StageRecs + 2 * kSu2PlaqRecs) * sizeof(Rec<T>);
+    return (size_t)(kSu2Stages * kSu2StageRecs + kSu2PlaqBufs * kSu2PlaqRecs) * sizeof(Rec<T>);
 }
 
 __device__ __forceinline__ void cp_async_cg16(void *dst, const void *src)
@@ -261,46 +261,67 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
     };
     auto pidx = [](int buf, int k, int rx, int ry) { return buf * kSu2PlaqRecs + (k * kSu2Py + ry) * kSu2Px + rx; };
     const int rx = tx + 1, ry = ty + 1;
-
-    copy_plane(z0 - 1);
-    copy_plane(z0);
-    copy_plane(z0 + 1);
-    cp_async_wait_all();
-    __syncthreads();
-    // V_xz, V_yz of plane z0 - 1 (relative index 0) for the first plane's -z terms
-    if (active) {
-        plaq[pidx(1, 1, rx, ry)] = plaq_im(0, 2, rx, ry, 0);
-        plaq[pidx(1, 2, rx, ry)] = plaq_im(1, 2, rx, ry, 0);
-    }
-    for (int z = z0; z < z1; ++z) {
-        const int zr = z - z0 + 1;
-        const int cur = (z - z0) & 1;
-        cp_async_wait_all();
-        __syncthreads();  // plane z+1 landed; the stage of plane z-2 and plaquette buffer cur are free
-        if (z + 2 <= z1) copy_plane(z + 2);
-        const size_t s = (size_t)z * NN + (size_t)y * N + x;
-        T eo[9];
-        Rec<T> V[3];
+    // plaquettes of plane zr (own site and the -x / -y halo) into buffer zr % 3
+    auto form_plaquettes = [&](int zr) {
+        const int b = zr % kSu2PlaqBufs;
         if (active) {
-#pragma unroll
-            for (int c = 0; c < 9; ++c) eo[c] = E[(size_t)c * n3 + s];
-            V[0] = plaq_im(0, 1, rx, ry, zr);
-            V[1] = plaq_im(0, 2, rx, ry, zr);
-            V[2] = plaq_im(1, 2, rx, ry, zr);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) plaq[pidx(cur, k, rx, ry)] = V[k];
+            plaq[pidx(b, 0, rx, ry)] = plaq_im(0, 1, rx, ry, zr);
+            plaq[pidx(b, 1, rx, ry)] = plaq_im(0, 2, rx, ry, zr);
+            plaq[pidx(b, 2, rx, ry)] = plaq_im(1, 2, rx, ry, zr);
         }
-        if (tid < kSu2HaloJobs) {  // halo plaquettes: row y0-1 (V_xy, V_yz), column x0-1 (V_xy, V_xz)
+        if (tid < kSu2HaloJobs) {  // row y0-1 (V_xy, V_yz), column x0-1 (V_xy, V_xz)
             const bool row = tid < 2 * kSu2Tx;
             const int hx = row ? 1 + tid % kSu2Tx : 0;
             const int hy = row ? 0 : 1 + (tid - 2 * kSu2Tx) % kSu2Ty;
             const int k = row ? (tid < kSu2Tx ? 0 : 2) : (tid < 2 * kSu2Tx + kSu2Ty ? 0 : 1);
-            plaq[pidx(cur, k, hx, hy)] = k == 0   ? plaq_im(0, 1, hx, hy, zr)
-                                         : k == 1 ? plaq_im(0, 2, hx, hy, zr)
-                                                  : plaq_im(1, 2, hx, hy, zr);
+            plaq[pidx(b, k, hx, hy)] = k == 0   ? plaq_im(0, 1, hx, hy, zr)
+                                       : k == 1 ? plaq_im(0, 2, hx, hy, zr)
+                                                : plaq_im(1, 2, hx, hy, zr);
         }
-        __syncthreads();  // the plane's plaquettes are complete
+    };
+
+    // Software pipeline, one barrier per plane: the interval of plane z forms
+    // the plaquettes of plane z+1 and then updates the links of plane z from
+    // the plaquettes of planes z and z-1 (formed in earlier intervals).  Ring
+    // stages hold planes z..z+2 while z+3 lands; U_z(x - z) is carried in
+    // registers from the previous plane, whose stage is being refilled.
+    copy_plane(z0 - 1);
+    copy_plane(z0);
+    copy_plane(z0 + 1);
+    copy_plane(z0 + 2);
+    cp_async_wait_all();
+    __syncthreads();
+    Q<T> uz_prev{0, 0, 0, 0};
+    if (active) {  // V_xz, V_yz of plane z0 - 1 (relative index 0) for the first plane's -z terms
+        plaq[pidx(0, 1, rx, ry)] = plaq_im(0, 2, rx, ry, 0);
+        plaq[pidx(0, 2, rx, ry)] = plaq_im(1, 2, rx, ry, 0);
+        uz_prev = link(2, rx, ry, 0);
+    }
+    form_plaquettes(1);
+    // the electric fields of a plane are loaded one plane ahead of their update
+    T eo[9], en[9];
+    const size_t s0 = (size_t)z0 * NN + (size_t)y * N + x;
+    if (active) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) eo[c] = E[(size_t)c * n3 + s0];
+    }
+    for (int z = z0; z < z1; ++z) {
+        const int zr = z - z0 + 1;
+        const int cur = zr % kSu2PlaqBufs, prev = (zr + kSu2PlaqBufs - 1) % kSu2PlaqBufs;
+        cp_async_wait_all();
+        __syncthreads();  // plaquettes of plane z complete, plane z+2 landed; the stage of z-1 and buffer (z+1) % 3 are free
+        if (z + 3 <= z1) copy_plane(z + 3);
+        const size_t s = (size_t)z * NN + (size_t)y * N + x;
+        if (active && z + 1 < z1) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) en[c] = E[(size_t)c * n3 + s + NN];
+        }
+        if (z + 1 < z1) form_plaquettes(zr + 1);
         if (!active) continue;
+        Rec<T> V[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) V[k] = plaq[pidx(cur, k, rx, ry)];
+        const Q<T> uz = link(2, rx, ry, zr);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             T Fx = 0, Fy = 0, Fz = 0;
@@ -312,8 +333,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
                 // V_ij(x - j) and W = U_j(x - j)
                 const Rec<T> vn = j == 0   ? plaq[pidx(cur, k, rx - 1, ry)]
                                   : j == 1 ? plaq[pidx(cur, k, rx, ry - 1)]
-                                           : plaq[pidx(cur ^ 1, k, rx, ry)];
-                const Q<T> W = j == 0 ? link(0, rx - 1, ry, zr) : j == 1 ? link(1, rx, ry - 1, zr) : link(2, rx, ry, zr - 1);
+                                           : plaq[pidx(prev, k, rx, ry)];
+                const Q<T> W = j == 0 ? link(0, rx - 1, ry, zr) : j == 1 ? link(1, rx, ry - 1, zr) : uz_prev;
                 T ox, oy, oz;
                 rot_adj(W, vn.x, vn.y, vn.z, ox, oy, oz);
                 Fx += sg * (V[k].x - ox);
@@ -330,13 +351,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
             // drift: exp(i dt e.s) = cos(dt|e|) + i sin(dt|e|) e/|e|
             T f, cs;
             drift_rotation<T>(e1 * e1 + e2 * e2 + e3 * e3, dt, &f, &cs);
-            Q<T> u = qmul(Q<T>{cs, f * e1, f * e2, f * e3}, link(i, rx, ry, zr));
+            Q<T> u = qmul(Q<T>{cs, f * e1, f * e2, f * e3}, i == 2 ? uz : link(i, rx, ry, zr));
             if (sizeof(T) == 4) {  // FP32 storage: keep the link on the unit sphere
                 const T r = rsqrt(u.w * u.w + u.x * u.x + u.y * u.y + u.z * u.z);
                 u = Q<T>{u.w * r, u.x * r, u.y * r, u.z * r};
             }
             stU(Uout, n3, i, s, u);
         }
+        uz_prev = uz;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) eo[c] = en[c];
     }
     cp_async_wait_all();
 }
