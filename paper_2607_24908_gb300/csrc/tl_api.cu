@@ -56,7 +56,7 @@ tl::PassTuning tl::default_tuning(int N, int nf, int elem_bytes)
     if (v && strcmp(v, "ldg") == 0) t.variant = tl::kVariantLdg;
     const char *cw = getenv("TL_BULK_WARPS"), *zc = getenv("TL_PASS_ZC");
     if (t.variant == tl::kVariantTma) {  // measured: long z-chunks for the ring, 15 + 1 warps on large lattices
-        t.zc = N <= 192 ? 16 : 64;
+        t.zc = N <= 192 ? 16 : (N >= 512 ? 72 : 64);
         t.cwarps = N >= 768 ? 15 : 7;
     }
     if ((v = getenv("TL_PREFETCH"))) t.prefetch = atoi(v);
