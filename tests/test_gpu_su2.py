@@ -11,9 +11,12 @@ from paper_2607_24908_gb300.workloads import random_su2_links
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("dtype,N,tol", [("f64", 8, 1e-12), ("f64", 12, 1e-12), ("f32", 10, 1e-5)])
+# N = 8-12 run z-chunks of one plane; N = 40 (FP32: 2-plane chunks, the last ragged) and N = 64
+# (FP64: 8-plane chunks) run the kernel's plane pipeline over several planes per CTA.
+@pytest.mark.parametrize("dtype,N,tol", [("f64", 8, 1e-12), ("f64", 12, 1e-12), ("f32", 10, 1e-5),
+                                         ("f32", 40, 1e-5), ("f64", 64, 1e-12)])
 def test_su2_leapfrog_matches_oracle(dtype, N, tol):
-    dt, steps = 0.05, 20
+    dt, steps = 0.05, 20 if N <= 40 else 6
     U0 = random_su2_links(N, seed=N, amp=0.6)
     rng = np.random.default_rng(1)
     E0 = 0.2 * rng.standard_normal((3, 3, N, N, N))
