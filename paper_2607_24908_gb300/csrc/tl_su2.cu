@@ -561,9 +561,10 @@ int tl_su2_create(tl_su2 **out, int N, tl_dtype dtype, void *cuda_stream)
         delete Y;
         return tl::fail(TL_ECUDA, "cudaMemGetInfo failed (no CUDA device?)");
     }
-    if (33 * n3 * Y->esz + (64u << 20) > free_b) {
+    const size_t need = 33 * n3 * Y->esz;  // two link buffers (12 values a site each) and the fields (9)
+    if (need + (64u << 20) > free_b) {
         delete Y;
-        return tl::fail(TL_ENOMEM, "SU(2) lattice needs %zu bytes", 33 * n3 * Y->esz);
+        return tl::fail(TL_ENOMEM, "SU(2) lattice needs %zu bytes", need);
     }
     int dev = 0;
     cudaGetDevice(&dev);
