@@ -141,19 +141,28 @@ __device__ __forceinline__ void drift_rotation(T q2, T dt, T *f, T *cs)
     }
 }
 
-// Im(W^+ (0, v) W) for W = w + i u.s: the vector v rotated by the adjoint
-// action of W^+, (w^2 - |u|^2) v + 2 (u.v) u + 2 w (u x v) (the same value as
-// the two quaternion products, for any W).
 template <typename T>
-__device__ __forceinline__ void rot_adj(const Q<T> &W, T vx, T vy, T vz, T &ox, T &oy, T &oz)
+struct alignas(4 * sizeof(T)) Rec {
+    T w, x, y, z;
+};
+
+__device__ __forceinline__ float fma_su(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_su(double a, double b, double c) { return fma(a, b, c); }
+
+// F += sg (V - R(W^+) v), with R(W^+) v = Im(W^+ (0, v) W) the vector v rotated
+// by the adjoint action of W^+.  For W = w + i u.s,
+//   R(W^+) v = (w^2 - |u|^2) v + 2 (u.v) u + 2 w (u x v),
+// which for a unit W (an SU(2) link) is v + 2 w (u x v) + 2 u x (u x v); that
+// form is accumulated here (two cross products and fused multiply-adds).
+template <typename T>
+__device__ __forceinline__ void add_force(const Q<T> &W, const Rec<T> &V, const Rec<T> &v, T sg, T &Fx, T &Fy, T &Fz)
 {
-    const T uv2 = (T)2 * (W.x * vx + W.y * vy + W.z * vz);
-    const T s = W.w * W.w - (W.x * W.x + W.y * W.y + W.z * W.z);
-    const T w2 = W.w + W.w;
-    const T cx = W.y * vz - W.z * vy, cy = W.z * vx - W.x * vz, cz = W.x * vy - W.y * vx;
-    ox = s * vx + uv2 * W.x + w2 * cx;
-    oy = s * vy + uv2 * W.y + w2 * cy;
-    oz = s * vz + uv2 * W.z + w2 * cz;
+    const T cx = W.y * v.z - W.z * v.y, cy = W.z * v.x - W.x * v.z, cz = W.x * v.y - W.y * v.x;
+    const T dx = W.y * cz - W.z * cy, dy = W.z * cx - W.x * cz, dz = W.x * cy - W.y * cx;
+    const T a = (T)-2 * sg * W.w, b = (T)-2 * sg;
+    Fx = fma_su(b, dx, fma_su(a, cx, Fx + sg * (V.x - v.x)));
+    Fy = fma_su(b, dy, fma_su(a, cy, Fy + sg * (V.y - v.y)));
+    Fz = fma_su(b, dz, fma_su(a, cz, Fz + sg * (V.z - v.z)));
 }
 
 // One pass per step over CTAs of 32 x 8 site columns, each marching a chunk of
@@ -162,7 +171,7 @@ __device__ __forceinline__ void rot_adj(const Q<T> &W, T vx, T vy, T vz, T &ox, 
 //   P_ij(x) = U_i(x) U_j(x+i) U_i(x+j)^+ U_j(x)^+,   V_ij = Im P_ij = -V_ji,
 // U_i f_ij(x) = P_ij(x) and U_i b_ij(x) = W^+ P_ij(x-j)^+ W with W = U_j(x-j), so
 //   Im[U_i S_i](x) = sum_{j != i} V_ij(x) - R(W^+) V_ij(x-j),
-// R(W^+) the rotation of rot_adj.  Each plaquette is then formed once per site
+// R(W^+) the rotation of add_force.  Each plaquette is then formed once per site
 // (three per site, instead of four staples per link) and shared through shared
 // memory: V_xy, V_xz, V_yz of the CTA's tile plus the -x / -y halo it needs,
 // in three buffers (planes z-1, z, and z+1 being formed).
@@ -180,11 +189,6 @@ constexpr int kSu2Px = kSu2Tx + 1, kSu2Py = kSu2Ty + 1;  // plaquette tile with 
 constexpr int kSu2PlaqRecs = 3 * kSu2Py * kSu2Px;      // 891 per buffer (V_xy, V_xz, V_yz)
 constexpr int kSu2PlaqBufs = 3;                        // planes z-1 (read), z (read), z+1 (written)
 constexpr int kSu2HaloJobs = 2 * kSu2Tx + 2 * kSu2Ty;   // row y0-1: V_xy, V_yz; column x0-1: V_xy, V_xz
-
-template <typename T>
-struct alignas(4 * sizeof(T)) Rec {
-    T w, x, y, z;
-};
 
 template <typename T>
 constexpr size_t su2_tiled_smem()
@@ -335,11 +339,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
                                   : j == 1 ? plaq[pidx(cur, k, rx, ry - 1)]
                                            : plaq[pidx(prev, k, rx, ry)];
                 const Q<T> W = j == 0 ? link(0, rx - 1, ry, zr) : j == 1 ? link(1, rx, ry - 1, zr) : uz_prev;
-                T ox, oy, oz;
-                rot_adj(W, vn.x, vn.y, vn.z, ox, oy, oz);
-                Fx += sg * (V[k].x - ox);
-                Fy += sg * (V[k].y - oy);
-                Fz += sg * (V[k].z - oz);
+                add_force(W, V[k], vn, sg, Fx, Fy, Fz);
             }
             const T e1 = eo[3 * i] - (T)2 * dt * Fx;
             const T e2 = eo[3 * i + 1] - (T)2 * dt * Fy;
