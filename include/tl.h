@@ -256,8 +256,8 @@ int tl_langevin_step(tl_lattice *lat, int n, double dt, const tl_langevin_params
  * (the paper's E+ = E - dt sum_j (P_ij - P_ij^+)), then drift
  * U_i(x) <- exp(dt E_i(x)) U_i(x) (closed-form exponential map), fused in one
  * pass per step.  FP32 links are renormalised to unit length after each drift.
- * The kick evaluates the staple sum through plaquettes and uses that the links
- * are unit quaternions: links given to tl_su2_set_state must be normalised
+ * The kick evaluates the staple sum through plaquettes, an identity that holds
+ * for unit quaternions: links given to tl_su2_set_state must be normalised
  * (to the precision of dtype); a deviation d of |U|^2 from 1 enters the force
  * at relative order d. */
 

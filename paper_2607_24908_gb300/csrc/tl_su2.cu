@@ -152,8 +152,10 @@ __device__ __forceinline__ double fma_su(double a, double b, double c) { return 
 // F += sg (V - R(W^+) v), with R(W^+) v = Im(W^+ (0, v) W) the vector v rotated
 // by the adjoint action of W^+.  For W = w + i u.s,
 //   R(W^+) v = (w^2 - |u|^2) v + 2 (u.v) u + 2 w (u x v),
-// which for a unit W (an SU(2) link) is v + 2 w (u x v) + 2 u x (u x v); that
-// form is accumulated here (two cross products and fused multiply-adds).
+// which for a unit W is v + 2 w (u x v) + 2 u x (u x v); that form is
+// accumulated here (two cross products and fused multiply-adds).  Links are
+// unit quaternions anyway: the plaquette form of the backward staple itself
+// uses W^+ W = 1.
 template <typename T>
 __device__ __forceinline__ void add_force(const Q<T> &W, const Rec<T> &V, const Rec<T> &v, T sg, T &Fx, T &Fy, T &Fz)
 {
@@ -169,7 +171,8 @@ __device__ __forceinline__ void add_force(const Q<T> &W, const Rec<T> &V, const 
 // z-planes.  The force on U_i(x) is Im[U_i(x) S_i(x)] with the staples S of
 // Sec. 4; in terms of the plaquettes
 //   P_ij(x) = U_i(x) U_j(x+i) U_i(x+j)^+ U_j(x)^+,   V_ij = Im P_ij = -V_ji,
-// U_i f_ij(x) = P_ij(x) and U_i b_ij(x) = W^+ P_ij(x-j)^+ W with W = U_j(x-j), so
+// U_i f_ij(x) = P_ij(x) and, for unit links, U_i b_ij(x) = W^+ P_ij(x-j)^+ W
+// with W = U_j(x-j), so
 //   Im[U_i S_i](x) = sum_{j != i} V_ij(x) - R(W^+) V_ij(x-j),
 // R(W^+) the rotation of add_force.  Each plaquette is then formed once per site
 // (three per site, instead of four staples per link) and shared through shared
