@@ -86,11 +86,11 @@ def _new_lattice(spec: JobSpec, stream: int) -> T.Lattice:
     return lat
 
 
-def _result(spec: JobSpec, lat: T.Lattice, admitted: float, t0: float) -> JobResult:
+def _result(spec: JobSpec, lat: T.Lattice, admitted: float, t0: float,
+            clock: Callable[[], float] = time.perf_counter) -> JobResult:
     E = lat.energies()
     _, P, _ = lat.spectrum(0, 0)
-    return JobResult(spec.job_id, spec.arrival, admitted, time.perf_counter() - t0, E.vector(), E.a, E.b,
-                     E.hubble_resid, P)
+    return JobResult(spec.job_id, spec.arrival, admitted, clock() - t0, E.vector(), E.a, E.b, E.hubble_resid, P)
 
 
 @dataclass
@@ -130,9 +130,10 @@ class _Lane:
 class Server:
     """Continuous batching over resident lattices (see the module docstring)."""
 
-    def __init__(self, budget_bytes: int, chunk: int = 100):
+    def __init__(self, budget_bytes: int, chunk: int = 100, clock: Callable[[], float] = time.perf_counter):
         self.budget = int(budget_bytes)
         self.chunk = int(chunk)
+        self.clock = clock
         self.lanes = {}  # (dtype, size class) -> _Lane, created with its stream on first use
         self.used = 0
 
@@ -176,7 +177,7 @@ class Server:
                     lane.batch.close()
                     lane.batch, lane.members = None, ()
                 for a in finished:
-                    done.append(_result(a.spec, a.lat, a.admitted, t0))
+                    done.append(_result(a.spec, a.lat, a.admitted, t0, self.clock))
                     a.lat.close()
                     self.used -= a.spec.budget_bytes()
             if not lane.jobs:
@@ -208,7 +209,7 @@ def serve(jobs: List[JobSpec], budget_bytes: int, chunk: int = 100,
           clock: Callable[[], float] = time.perf_counter):
     """Run ``jobs`` (sorted by arrival) through a continuous-batching server in
     real time.  Returns (results in completion order, makespan seconds)."""
-    srv = Server(budget_bytes, chunk)
+    srv = Server(budget_bytes, chunk, clock)
     pending = sorted(jobs, key=lambda j: j.arrival)
     for j in pending:
         if j.budget_bytes() > budget_bytes:
@@ -250,7 +251,7 @@ def run_alone(jobs: List[JobSpec], chunk: int = 100, clock: Callable[[], float] 
         lat = _new_lattice(spec, stream)
         for _ in range(spec.steps // chunk):
             lat.step(chunk, spec.dt, "verlet")
-        results.append(_result(spec, lat, admitted, t0))
+        results.append(_result(spec, lat, admitted, t0, clock))
         lat.close()
     return results, clock() - t0
 

@@ -153,6 +153,16 @@ def test_server_refuses_bad_jobs(fakes):
     srv.close()
 
 
+def test_results_are_stamped_with_the_callers_clock(fakes):
+    """Arrival, admission and finish times all come from the clock given to serve()."""
+    ticks = iter(range(10 ** 9))
+    clock = lambda: 1000.0 + next(ticks) * 1e-3  # noqa: E731  (a synthetic clock far from perf_counter)
+    jobs = _jobs()[:6]
+    results, makespan = S.serve(jobs, max(j.budget_bytes() for j in jobs) * 3, chunk=100, clock=clock)
+    for r in results:
+        assert 0.0 <= r.admitted <= r.finished <= makespan < 1000.0
+
+
 def test_run_alone_steps_each_job_in_chunks(fakes):
     jobs = _jobs()[:5]
     results, _ = S.run_alone(jobs, chunk=100)
