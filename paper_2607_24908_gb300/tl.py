@@ -2,8 +2,8 @@
 
 Functions keep the C names (``tl_lattice_create`` ...) and raise ``TLError``
 on a negative return code.  ``Lattice`` wraps one lattice handle.  Every step
-of the computation runs in libtl.so; if the library is missing this module
-raises at load time -- there is no CPU fallback.
+of the computation runs in libtl.so, loaded on the first call; if the library
+is missing that call raises ImportError -- there is no CPU fallback.
 """
 from __future__ import annotations
 
