@@ -83,3 +83,25 @@ def test_serving_job_generator_and_budget_arithmetic():
     assert srv.fits(jobs[0])
     srv.used = 1
     assert not srv.fits(jobs[0])
+
+
+def test_product_path_never_imports_or_links_the_oracle():
+    """The package (binding, serving loop, build script) imports nothing from oracle/,
+    and no kernel or header source includes a file from it."""
+    import ast
+    import glob
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2607_24908_gb300")
+    for path in glob.glob(os.path.join(pkg, "*.py")):
+        tree = ast.parse(open(path).read(), path)
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                assert not any(a.name.split(".")[0] == "oracle" for a in node.names), path
+            elif isinstance(node, ast.ImportFrom):
+                assert node.level > 0 or (node.module or "").split(".")[0] != "oracle", path
+    for path in glob.glob(os.path.join(pkg, "csrc", "*")) + glob.glob(os.path.join(root, "include", "*")):
+        for line in open(path, errors="replace"):
+            if line.lstrip().startswith("#include"):
+                assert "oracle" not in line and "tlo" not in line, (path, line)
+    build = open(os.path.join(pkg, "build.py")).read()
+    assert "oracle" not in build and "tlo.c" not in build
