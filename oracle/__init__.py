@@ -23,7 +23,9 @@ printed in the paper; the readings used are stated in the C file's header and
 in the functions below.
 
 Parity pins: see tests/test_oracle_pins.py.  ``philox2x64`` is parity
-unpinned against an external known-answer table; it is pinned statistically.
+unpinned against an external known-answer table (none is available offline);
+it is pinned to the published round definition by exact inversion of its ten
+rounds, and statistically.
 """
 from __future__ import annotations
 

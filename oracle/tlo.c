@@ -46,7 +46,7 @@
  * "Parallel random numbers: as easy as 1, 2, 3", SC'11), the generator the
  * paper names for its Gaussian random fields (Sec. 2).  Parity unpinned
  * against an external known-answer table (none is available offline); pinned
- * only statistically.
+ * to the published round definition by exact inversion, and statistically.
  *
  * Compiled with -O2 -ffp-contract=off so every product and sum is rounded as
  * written.

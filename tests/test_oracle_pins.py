@@ -455,6 +455,29 @@ def test_philox_uniform_statistics():
     assert len(np.unique(w[:, 0])) == n
 
 
+def test_philox_rounds_invert_under_the_published_definition():
+    """Salmon et al. (SC'11) define the Philox-2x64 round as (hi, lo) = M c0 (128-bit
+    product, M = 0xD2B74407B1CE6E93), c0 <- hi ^ k ^ c1, c1 <- lo, with the key bumped
+    by W = 0x9E3779B97F4A7C15 after each round.  M is odd, so a round inverts exactly:
+    c0 = lo M^-1 mod 2^64, then c1 = c0' ^ hi(M c0) ^ k.  Undoing ten such rounds on
+    the oracle's outputs (Python integers, independent of its C code) must give back
+    every input counter; a wrong constant, word order or key schedule would not."""
+    M, W, mask = 0xD2B74407B1CE6E93, 0x9E3779B97F4A7C15, (1 << 64) - 1
+    Minv = pow(M, -1, 1 << 64)
+    rng = np.random.default_rng(99)
+    c0s = rng.integers(0, 2 ** 63, size=64, dtype=np.uint64) * np.uint64(2) + np.uint64(1)
+    for c1, key in ((0, 0), ((1 << 63) + 17, 12345), (mask, mask)):
+        out = o.philox2x64(c0s, c1, key)
+        for i, c0 in enumerate(c0s):
+            x0, x1 = int(out[i, 0]), int(out[i, 1])
+            for r in reversed(range(10)):
+                k = (key + r * W) & mask
+                prev0 = (x1 * Minv) & mask
+                prev1 = x0 ^ ((M * prev0) >> 64) ^ k
+                x0, x1 = prev0, prev1
+            assert (x0, x1) == (int(c0), c1)
+
+
 # --- 14. site-local step equals the whole-lattice step -------------------------------
 
 def test_vv_step_at_sites_matches_full_step():
