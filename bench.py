@@ -79,7 +79,8 @@ def measured_traffic(shape=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source and launch shape (else None)."""
     try:
-        txt = open(TRAFFIC_FILE).read()
+        with open(TRAFFIC_FILE) as f:
+            txt = f.read()
     except OSError:
         return None
     h = re.search(r"kernel source sha256\[:16\]:\s*([0-9a-f]+)", txt)

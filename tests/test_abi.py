@@ -1,6 +1,7 @@
 """CPU checks of the boundary: libtl.so builds, loads without a GPU and
 exports every function include/tl.h declares; the binding covers them all."""
 import os
+import pathlib
 import re
 import subprocess
 
@@ -11,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def header_functions():
-    txt = open(os.path.join(ROOT, "include", "tl.h")).read()
+    txt = pathlib.Path(ROOT, "include", "tl.h").read_text()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(tl_[a-z0-9_]+)\s*\(", txt)))
 
@@ -93,15 +94,15 @@ def test_product_path_never_imports_or_links_the_oracle():
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     pkg = os.path.join(root, "paper_2607_24908_gb300")
     for path in glob.glob(os.path.join(pkg, "*.py")):
-        tree = ast.parse(open(path).read(), path)
+        tree = ast.parse(pathlib.Path(path).read_text(), path)
         for node in ast.walk(tree):
             if isinstance(node, ast.Import):
                 assert not any(a.name.split(".")[0] == "oracle" for a in node.names), path
             elif isinstance(node, ast.ImportFrom):
                 assert node.level > 0 or (node.module or "").split(".")[0] != "oracle", path
     for path in glob.glob(os.path.join(pkg, "csrc", "*")) + glob.glob(os.path.join(root, "include", "*")):
-        for line in open(path, errors="replace"):
+        for line in pathlib.Path(path).read_text(errors="replace").splitlines():
             if line.lstrip().startswith("#include"):
                 assert "oracle" not in line and "tlo" not in line, (path, line)
-    build = open(os.path.join(pkg, "build.py")).read()
+    build = pathlib.Path(pkg, "build.py").read_text()
     assert "oracle" not in build and "tlo.c" not in build

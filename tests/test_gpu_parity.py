@@ -249,9 +249,10 @@ def test_argument_errors():
 
 def _host_ram_gb():
     try:
-        for line in open("/proc/meminfo"):
-            if line.startswith("MemAvailable:"):
-                return int(line.split()[1]) / 2 ** 20
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
     except OSError:
         pass
     return 0.0
