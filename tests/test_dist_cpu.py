@@ -30,7 +30,7 @@ def json_lines(out: str):
 def test_replica_aggregation_gloo_world_size_2(tmp_path):
     r = torchrun([os.path.join("tests", "gloo_rank.py"), str(tmp_path)])
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = [json.load(open(tmp_path / f"rank{k}.json")) for k in range(2)]
+    lines = [json.loads((tmp_path / f"rank{k}.json").read_text()) for k in range(2)]
     assert [d["rank"] for d in lines] == [0, 1]
     for d in lines:
         assert d["ws"] == 2
