@@ -22,10 +22,10 @@ background, alpha time variable, Yoshida-4 and spectrum conventions are not
 printed in the paper; the readings used are stated in the C file's header and
 in the functions below.
 
-Parity pins: see tests/test_oracle_pins.py.  ``philox2x64`` is parity
-unpinned against an external known-answer table (none is available offline);
-it is pinned to the published round definition by exact inversion of its ten
-rounds, and statistically.
+Parity pins: see tests/test_oracle_pins.py and tests/test_golden.py.
+``philox2x64`` is pinned to the published known-answer vectors of
+Philox-2x64-10 (Random123's kat_vectors rows), to its round structure by exact
+inversion of its ten rounds, and statistically.
 """
 from __future__ import annotations
 

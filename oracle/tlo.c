@@ -44,9 +44,10 @@
  *
  * Random numbers: Philox-2x64 with 10 rounds (Salmon, Moraes, Dror, Shaw,
  * "Parallel random numbers: as easy as 1, 2, 3", SC'11), the generator the
- * paper names for its Gaussian random fields (Sec. 2).  Parity unpinned
- * against an external known-answer table (none is available offline); pinned
- * to the published round definition by exact inversion, and statistically.
+ * paper names for its Gaussian random fields (Sec. 2).  Pinned to the
+ * published known-answer vectors of Philox-2x64-10 (the Random123
+ * distribution's kat_vectors rows), to the round structure by exact
+ * inversion, and statistically.
  *
  * Compiled with -O2 -ffp-contract=off so every product and sum is rounded as
  * written.

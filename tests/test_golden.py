@@ -1,12 +1,19 @@
 """Stored expected values (tests/golden/).
 
+- philox2x64_10_kat.json: the published known-answer vectors of
+  Philox-2x64-10 (the Random123 distribution's kat_vectors rows, SC'11), the
+  generator the paper names for its Gaussian random fields (Sec. 2).  The
+  oracle's generator must reproduce them exactly: this pins its multiplier,
+  Weyl constant, word order and key schedule to a table from outside this
+  repository.
 - minimal_example_sec2_1.json: the one number the paper prints for a worked
   example (Sec. 2.1: the average of 2 plus a configuration-space Gaussian
   field on 128^3).  Its exact digits depend on the paper's own seeding of its
-  generator, which the paper does not define, so what is checked is our
-  reading of `average` (mean over the N^3 sites) and of the field (unit
-  variance per site): under it the printed value lies within 4 standard
-  errors of 2, and an average of 2 plus unit white noise on 128^3 does too.
+  generator, which the paper does not define.  This is a check of a reading,
+  not a pin of the oracle: under our reading of `average` (mean over the N^3
+  sites) and of the field (unit variance per site) the printed value lies
+  within 4 standard errors of 2, and an average of 2 plus unit white noise
+  on 128^3 does too.
 - oracle_cases.json: small seeded cases written by make_oracle_cases.py,
   which calls only oracle/; the oracle must keep reproducing them."""
 import json
@@ -23,7 +30,17 @@ def load(name):
         return json.load(fh)
 
 
-def test_paper_minimal_example_average():
+def test_philox2x64_10_known_answers():
+    import oracle as o
+    g = load("philox2x64_10_kat.json")
+    assert len(g["rows"]) == 3
+    for row in g["rows"]:
+        c0, c1 = (int(w, 16) for w in row["ctr"])
+        out = o.philox2x64(np.array([c0], dtype=np.uint64), c1, int(row["key"], 16))
+        assert (int(out[0, 0]), int(out[0, 1])) == tuple(int(w, 16) for w in row["out"]), row
+
+
+def test_reading_of_paper_minimal_example_average():
     g = load("minimal_example_sec2_1.json")
     N = g["lattice_N"]
     se = 1.0 / math.sqrt(N ** 3)  # standard error of the mean of N^3 unit-variance sites

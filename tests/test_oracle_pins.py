@@ -431,7 +431,7 @@ def test_spectrum_single_mode_closed_form_and_parseval():
     assert abs(k[1] - p.kIR * (6 + 12 * math.sqrt(2)) / 18) < 1e-15
 
 
-# --- 13. Philox-2x64-10: statistics only (parity unpinned against a KAT) -------------
+# --- 13. Philox-2x64-10: statistics and round structure (known answers: test_golden) --
 
 def test_philox_uniform_statistics():
     n = 200_000
@@ -461,7 +461,10 @@ def test_philox_rounds_invert_under_the_published_definition():
     by W = 0x9E3779B97F4A7C15 after each round.  M is odd, so a round inverts exactly:
     c0 = lo M^-1 mod 2^64, then c1 = c0' ^ hi(M c0) ^ k.  Undoing ten such rounds on
     the oracle's outputs (Python integers, independent of its C code) must give back
-    every input counter; a wrong constant, word order or key schedule would not."""
+    every input counter.  This pins the round structure (word order, key schedule,
+    which word is multiplied) but not the constants themselves, which are retyped
+    here; those are pinned by the published known-answer vectors
+    (tests/golden/philox2x64_10_kat.json, tests/test_golden.py)."""
     M, W, mask = 0xD2B74407B1CE6E93, 0x9E3779B97F4A7C15, (1 << 64) - 1
     Minv = pow(M, -1, 1 << 64)
     rng = np.random.default_rng(99)
