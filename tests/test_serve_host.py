@@ -1,7 +1,8 @@
 """The serving loop's host logic on the CPU: admission by budget in arrival
-order, lanes per precision and size class, reaping, batch rebuilds and
-clean-up, with the device calls (lattices, batches, streams, events) replaced
-by fakes that record what the server asks of them."""
+order, batched lanes per (precision, dt, integrator) and solo lanes for big
+jobs, the step size and integrator each job is advanced with, reaping, batch
+rebuilds and clean-up, with the device calls (lattices, batches, streams,
+events) replaced by fakes that record what the server asks of them."""
 import types
 
 import numpy as np
@@ -17,6 +18,7 @@ class FakeLattice:
     def __init__(self, N, kIR, nf, dtype, expanding, alpha, a0, fstar, stream=0):
         self.N, self.nf, self.dtype, self.stream = N, nf, dtype, stream
         self.steps, self.closed, self.in_batch, self.shape = 0, False, None, None
+        self.calls = []  # (n, dt, integrator) of every step this lattice took
         FakeLattice.created.append(self)
 
     def set_pass_config(self, **shape):
@@ -29,9 +31,10 @@ class FakeLattice:
     def init_fluctuations(self, seed, A, meff2, phi0):
         self.seed = seed
 
-    def step(self, n, dt, integ):  # the one-at-a-time loop
+    def step(self, n, dt, integ):  # a solo lane or the one-at-a-time loop
         assert not self.closed and self.in_batch is None
         self.steps += n
+        self.calls.append((n, dt, integ))
 
     def energies(self):
         assert not self.closed
@@ -59,6 +62,7 @@ class FakeBatch:
         for lat in self.lats:
             assert not lat.closed
             lat.steps += n
+            lat.calls.append((n, dt, integ))
 
     def close(self):
         for lat in self.lats:
@@ -93,6 +97,7 @@ def fakes(monkeypatch):
     import torch
     FakeLattice.created = []
     fake_T = types.SimpleNamespace(Lattice=FakeLattice, Batch=FakeBatch, DTYPES=realT.DTYPES,
+                                   INTEGRATORS=realT.INTEGRATORS,
                                    tl_state_bytes=realT.tl_state_bytes,
                                    batch_pass_config=lambda N, nf, dtype: {"kind": "stream", "z_chunk": min(N, 32)})
     monkeypatch.setattr(S, "T", fake_T)
@@ -116,9 +121,12 @@ def test_serve_loop_completes_every_job_within_budget(fakes, monkeypatch):
         orig_admit(self, spec, now)
         used_after_admit.append(self.used)
         admitted_ids.append(spec.job_id)
-        for key, lane in self.lanes.items():  # each lane holds one precision and one size class
+        for key, lane in self.lanes.items():  # batched lanes: one precision, dt, integrator; solo: one job
             for a in lane.jobs:
-                assert key == (a.spec.dtype, "small" if S.job_cost(a.spec) <= S.SMALL_COST else "big")
+                if S.is_batched(a.spec):
+                    assert key == ("batch", a.spec.dtype, a.spec.dt, a.spec.integrator)
+                else:
+                    assert key == ("solo", a.spec.job_id) and len(lane.jobs) == 1
 
     monkeypatch.setattr(S.Server, "admit", admit)
     results, _ = S.serve(jobs, budget, chunk=100)
@@ -131,7 +139,11 @@ def test_serve_loop_completes_every_job_within_budget(fakes, monkeypatch):
         assert r.admitted >= by_id[r.job_id].arrival - 1e-9 and r.latency >= 0
     assert len(FakeLattice.created) == len(jobs)
     assert all(lat.closed for lat in FakeLattice.created)
-    assert all(lat.shape["kind"] == "stream" for lat in FakeLattice.created)
+    # batched jobs start on the batch shape, big ones keep the library default
+    for lat in FakeLattice.created:
+        small = S.job_cost(types.SimpleNamespace(N=lat.N, n_fields=lat.nf, dtype=lat.dtype)) <= S.SMALL_COST
+        assert (lat.shape is not None and lat.shape["kind"] == "stream") if small else lat.shape is None
+    assert any(lat.shape is None for lat in FakeLattice.created)  # the mix has big jobs
 
 
 def test_tight_budget_serialises_and_still_finishes(fakes):
@@ -170,3 +182,58 @@ def test_run_alone_steps_each_job_in_chunks(fakes):
     for r, j in zip(results, sorted(jobs, key=lambda j: j.arrival)):
         assert r.energies[0] == j.steps
     assert all(lat.closed for lat in FakeLattice.created)
+
+
+def test_each_job_is_stepped_with_its_own_dt_and_integrator(fakes):
+    """Jobs with a non-default step size or integrator are never advanced with
+    another job's: lanes are keyed by them, and solo lanes use the job's own."""
+    base = _jobs()[:10]
+    jobs = []
+    for k, j in enumerate(base):
+        j.dt = (0.01, 0.004, 0.02)[k % 3]
+        j.integrator = ("verlet", "yoshida4", "leapfrog")[k % 3]
+        jobs.append(j)
+    results, _ = S.serve(jobs, max(j.budget_bytes() for j in jobs) * 4, chunk=100)
+    assert len(results) == len(jobs)
+    by_seed = {j.seed: j for j in jobs}
+    for lat in FakeLattice.created:
+        j = by_seed[lat.seed]
+        assert lat.calls and all(c == (100, j.dt, j.integrator) for c in lat.calls), (j.job_id, lat.calls)
+        assert lat.steps == j.steps
+    FakeLattice.created = []
+    alone, _ = S.run_alone(jobs, chunk=100)
+    for lat in FakeLattice.created:
+        j = by_seed[lat.seed]
+        assert all(c == (100, j.dt, j.integrator) for c in lat.calls)
+
+
+def test_run_alone_shapes(fakes):
+    """The plain loop runs every job on the library default ("default"); the
+    "served" form reproduces the server's shapes (batch shape for batched jobs)."""
+    jobs = _jobs()[:8]
+    S.run_alone(jobs, chunk=100)
+    assert all(lat.shape is None for lat in FakeLattice.created)
+    FakeLattice.created = []
+    S.run_alone(jobs, chunk=100, shape="served")
+    for lat, j in zip(FakeLattice.created, sorted(jobs, key=lambda j: j.arrival)):
+        assert (lat.shape is not None) == S.is_batched(j)
+    with pytest.raises(ValueError):
+        S.run_alone(jobs[:1], chunk=100, shape="tuned")
+
+
+def test_server_refuses_unknown_integrator_and_bad_dt(fakes):
+    srv = S.Server(budget_bytes=10 ** 12, chunk=100)
+    for kw in ({"integrator": "rk4"}, {"dt": 0.0}, {"dt": float("nan")}):
+        bad = S.JobSpec(job_id=7, N=32, n_fields=1, q=1.0, steps=100, dtype="f32", seed=1, **kw)
+        with pytest.raises(ValueError):
+            srv.admit(bad, 0.0)
+    srv.close()
+
+
+def test_lane_overlap_accounting():
+    log = [(("solo", 1), 0.0, 4.0), (("batch", "f32", 0.01, "verlet"), 1.0, 2.0),
+           (("batch", "f32", 0.01, "verlet"), 2.0, 3.0), (("solo", 2), 5.0, 6.0)]
+    o = S.lane_overlap(log, 8.0)
+    assert abs(o["any_lane_busy"] - 5.0 / 8.0) < 1e-12
+    assert abs(o["two_or_more_lanes_busy"] - 2.0 / 8.0) < 1e-12
+    assert o["busy_s_by_lane_kind"] == {"solo": 5.0, "batch-f32": 2.0}
