@@ -107,7 +107,10 @@ typedef struct {
 
 /* Create a lattice and allocate its device state (4 n_fields arrays of N^3
  * elements: phi and pi, ping-pong, plus O(grid) scratch for the fused
- * reductions).  N >= 8 and N % 4 == 0; 1 <= n_fields <= 3; kIR > 0;
+ * reductions).  Passage: Sec. 2, the memory toolbox of an N^3 box with one
+ * ghost layer (MemoryToolBox::makeShared) and the scalar fields living on it
+ * (Field<T, 3>, float or double); here phi and pi of every field are one
+ * device allocation owned by the lattice.  N >= 8 and N % 4 == 0; 1 <= n_fields <= 3; kIR > 0;
  * expansion may be NULL (static).  cuda_stream is a cudaStream_t (NULL: the
  * legacy default stream).  The lattice needs a potential
  * (tl_set_potential) and a state (tl_init_fluctuations or tl_set_state)
@@ -115,8 +118,8 @@ typedef struct {
 int tl_lattice_create(tl_lattice **out, int N, double kIR, int n_fields, tl_dtype dtype,
                       const tl_expansion *expansion, void *cuda_stream);
 
-/* As tl_lattice_create, but the 4 n_fields field arrays live in caller-owned
- * device memory: dev_ptrs[4 f + 0] phi_f (A), [4 f + 1] pi_f (A),
+/* As tl_lattice_create (Sec. 2, toolbox and fields), but the 4 n_fields
+ * field arrays live in caller-owned device memory: dev_ptrs[4 f + 0] phi_f (A), [4 f + 1] pi_f (A),
  * [4 f + 2] phi_f (B), [4 f + 3] pi_f (B); each holds the `elems` elements of
  * dtype that tl_array_layout gives (the padded layout), 16-byte aligned;
  * n_ptrs == 4 n_fields. */
@@ -124,10 +127,12 @@ int tl_lattice_create_with_buffers(tl_lattice **out, int N, double kIR, int n_fi
                                    const tl_expansion *expansion, void *cuda_stream,
                                    void *const *dev_ptrs, size_t n_ptrs);
 
-/* Device bytes tl_lattice_create would allocate for the field arrays. */
+/* Device bytes tl_lattice_create would allocate for the field arrays (the
+ * padded layout of tl_array_layout; no counterpart in the paper). */
 size_t tl_state_bytes(int N, int n_fields, tl_dtype dtype);
 
-/* Device layout of one field array of a lattice.  Every row carries W =
+/* Device layout of one field array of a lattice (Sec. 3.3: row-major on
+ * every device; Sec. 3.1 and Sec. 4: one ghost layer).  Every row carries W =
  * 16/sizeof ghost elements on each side (x in [-W, 0) and [N, N + W)) and
  * every z-plane one ghost row above and below: one-site ghost copies of the
  * periodic neighbours, kept current by every pass, so that a tile plus its
@@ -138,18 +143,32 @@ size_t tl_state_bytes(int N, int n_fields, tl_dtype dtype);
  * elems = N plane_pitch elements per array.  Any output may be NULL. */
 int tl_array_layout(int N, tl_dtype dtype, size_t *elems, size_t *row_pitch, size_t *plane_pitch, size_t *origin);
 
+/* Free a lattice and the device memory it owns (caller-owned buffers of
+ * tl_lattice_create_with_buffers are left alone) after synchronising its
+ * stream; NULL is a no-op, and so is a lattice still held by a tl_batch
+ * (destroy the batch first).  No counterpart in the paper (its toolbox is
+ * reference-counted). */
 void tl_lattice_destroy(tl_lattice *lat);
 
-/* Set the potential (may be changed between steps). */
+/* Set the potential (may be changed between steps).  Passage: Sec. 4, the
+ * quartic self-interaction (and mass term) in the kick of the phi^4
+ * benchmark; the two-field coupling q phi_0^2 phi_f^2/2 is the family the
+ * workloads need.  Errors: TL_EINVAL (NULL, non-finite coefficients). */
 int tl_set_potential(tl_lattice *lat, const tl_potential *pot);
 
-/* Draw the initial state (see tl_init_spec), set a = a0 and, when expanding,
+/* Passage: Sec. 2, Gaussian random fields drawn from Random123's counter-based
+ * Philox 2x64 in Fourier space (the field's Fourier view, Sec. 2 and
+ * Sec. 3.5); the spectrum A/(2 omega_k) is the workloads' vacuum spectrum.
+ * Draw the initial state (see tl_init_spec), set a = a0 and, when expanding,
  * b = a0^(1+alpha) sqrt(mu2 rho0/3) with rho0 the lattice-averaged K+G+V of
  * that state.  Uses cuFFT (c2r, FP64) and temporary device memory of about
  * 16 N^3 bytes.  Resets step and time to 0. */
 int tl_init_fluctuations(tl_lattice *lat, uint64_t seed, const tl_init_spec *spec);
 
-/* Advance n >= 0 steps of size dt (negative dt runs backwards).  The state
+/* Passage: Sec. 4, the kick-drift leapfrog of the phi^4 benchmark (kick
+ * pi += dt (Lap phi - dV/dphi), drift phi += dt pi, 7-point stencil), here
+ * with the expansion weights of the model above.
+ * Advance n >= 0 steps of size dt (negative dt runs backwards).  The state
  * stays resident; the call only enqueues work: n P + 1 fused passes (P = 1
  * for leapfrog/Verlet, 3 for Yoshida), each one kernel that drifts phi,
  * applies the Laplacian, dV/dphi and the expansion-weighted kick, and reduces
@@ -158,15 +177,21 @@ int tl_init_fluctuations(tl_lattice *lat, uint64_t seed, const tl_init_spec *spe
  * Errors: TL_EINVAL, TL_ESTATE, TL_ECUDA. */
 int tl_step(tl_lattice *lat, int n, double dt, tl_integrator integrator);
 
-/* Synchronise the lattice stream and return the energies at the current
+/* Passage: Sec. 2.1, the volume average of an expression (average(...));
+ * Sec. 3.2, the device reduction over a lattice (device::iteration::reduce).
+ * Synchronise the lattice stream and return the energies at the current
  * integer time (measured on the device if the state was set since the last
- * step). */
+ * step).  Errors: TL_EINVAL (NULL), TL_ESTATE (no state), TL_EUNSTABLE,
+ * TL_ETIMEOUT, TL_ECUDA. */
 int tl_energies(tl_lattice *lat, tl_energies_t *out);
 
-/* Number of spectrum bins for size N: ceil(sqrt(3) N/2) + 1. */
+/* Number of spectrum bins for size N: ceil(sqrt(3) N/2) + 1 (the shells of
+ * tl_spectrum). */
 int tl_spectrum_bins(int N);
 
-/* Binned power spectrum of phi_field (which = 0) or pi_field (which = 1):
+/* Passage: Sec. 2, a field's Fourier-space view (inFourierSpace), and
+ * Sec. 3.5, DFTs used for measurements such as power spectra.
+ * Binned power spectrum of phi_field (which = 0) or pi_field (which = 1):
  * d(n) = N^-3 sum_x f(x) exp(-i k.x), bin b = floor(|n| + 1/2),
  * P_b = L^3 mean_{n in b} |d(n)|^2, k_b = kIR mean_{n in b} |n|, count_b =
  * modes in the bin (all N^3 modes, both members of each pair).  Host arrays
@@ -174,25 +199,33 @@ int tl_spectrum_bins(int N);
  * FP64 atomics (reproducible to rounding, not bitwise).  Synchronises. */
 int tl_spectrum(tl_lattice *lat, int field, int which, int nbins, double *k, double *P, int64_t *count);
 
-/* Copy phi_field (which = 0) or pi_field (which = 1) at the current integer
+/* Passage: Sec. 3.3, the row-major layout of a field ([z][y][x], x fastest,
+ * ghosts stripped); used for checkpoints and tests.
+ * Copy phi_field (which = 0) or pi_field (which = 1) at the current integer
  * time to host memory of bytes = N^3 * element size ([z][y][x], x fastest).
  * Synchronises.  TL_EUNSTABLE if the evolution went non-finite. */
 int tl_get_state(tl_lattice *lat, int field, int which, void *host, size_t bytes);
 
-/* Overwrite phi_field or pi_field from host memory (same layout and size as
+/* Passage: Sec. 3.3, as tl_get_state (assignment of a field from host data;
+ * the ghost copies are refilled on the device).
+ * Overwrite phi_field or pi_field from host memory (same layout and size as
  * tl_get_state).  Resets step and time to 0; the energies are re-measured
  * on demand.  Call tl_set_background afterwards when expanding. */
 int tl_set_state(tl_lattice *lat, int field, int which, const void *host, size_t bytes);
 
-/* Set the scale factor a and a' = b; from_constraint != 0 ignores b and sets
+/* No counterpart in the paper (its benchmarks run in a static box): the
+ * background of the FLRW model above.
+ * Set the scale factor a and a' = b; from_constraint != 0 ignores b and sets
  * b = a^(1+alpha) sqrt(mu2 rho/3) from the current state's energies. */
 int tl_set_background(tl_lattice *lat, double a, double b, int from_constraint);
 
-/* Device address of element (0, 0, 0) of phi_field / pi_field of the current
+/* No counterpart in the paper (zero-copy access for callers on the device).
+ * Device address of element (0, 0, 0) of phi_field / pi_field of the current
  * state (padded layout, see tl_array_layout; valid until the next tl_step). */
 int tl_state_device_ptr(tl_lattice *lat, int field, int which, void **dev_ptr);
 
-/* The caller has written every phi_f and pi_f of the current state directly on
+/* No counterpart in the paper (pairs with tl_state_device_ptr).
+ * The caller has written every phi_f and pi_f of the current state directly on
  * the device (through tl_state_device_ptr or its own buffers of
  * tl_lattice_create_with_buffers, interior sites in the padded layout): refresh
  * their ghost copies and take them as the state, like tl_set_state of every
@@ -368,7 +401,8 @@ int tl_get_pass_config(const tl_lattice *lat, tl_pass_config *cfg);
  * cuda_stream.  Errors: TL_EINVAL (NULL), TL_ENOMEM, TL_ECUDA. */
 int tl_probe_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s, void *cuda_stream);
 
-/* Message for the last error on this thread ("" if none). */
+/* Message for the last error on this thread ("" if none); no counterpart in
+ * the paper. */
 const char *tl_last_error(void);
 
 #ifdef __cplusplus
