@@ -168,6 +168,8 @@ template <typename T, int NF>
 struct Coefs {
     T drift, wlx, wv, kdt, hdt, lam, q;
     T m2[NF];
+    T qlam, hq;  // lambda/4, q/2 (the potential's own coefficients, FP64 form)
+    T hm2[NF];   // m2/2
 };
 
 template <typename T, int NF>
@@ -182,7 +184,12 @@ __device__ __forceinline__ Coefs<T, NF> make_coefs(const Model &m, const PassCoe
     k.lam = (T)m.lambda;
     k.q = (T)m.q;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) k.m2[f] = (T)m.m2[f];
+    for (int f = 0; f < NF; ++f) {
+        k.m2[f] = (T)m.m2[f];
+        k.hm2[f] = (T)(0.5 * m.m2[f]);
+    }
+    k.qlam = (T)(0.25 * m.lambda);
+    k.hq = (T)(0.5 * m.q);
     return k;
 }
 
@@ -193,12 +200,62 @@ __device__ __forceinline__ Coefs<T, NF> make_coefs(const Model &m, const PassCoe
 // exact), dV/dphi, the kick, and the K/G/V sums at the evaluation time.
 // cu/zm/zp: phi at z, z-1, z+1; ym/yp: rows y-1, y+1; xl/xr: the sites left of
 // element 0 and right of element W-1; pc: stored pi at z.
+//
+// FP64 (bound by the FP64 pipe) takes the same quantities with fewer FP64
+// operations: the Laplacian as the neighbour sum minus 6 phi; the potential and
+// its derivative in factored form, phi (m2 + lambda phi^2) and
+// phi^2 (m2/2 + lambda phi^2/4); and the gradient energy by summation by
+// parts, which on a periodic lattice is exact: sum_x sum_i (phi(x+i) - phi(x))^2
+// = -sum_x phi(x) (sum_i [phi(x+i) + phi(x-i)] - 6 phi(x)), so each site adds
+// -phi times the Laplacian it has already formed (one fma instead of three
+// differences and three squares).  The lattice-wide sums are the same
+// numbers up to rounding; per site the terms differ.
 template <typename T, int NF, int W>
 __device__ __forceinline__ void site_update(const Coefs<T, NF> &k, const T (&cu)[NF][W], const T (&zm)[NF][W],
                                             const T (&zp)[NF][W], const T (&ym)[NF][W], const T (&yp)[NF][W],
                                             const T (&xl)[NF], const T (&xr)[NF], const T (&pc)[NF][W],
                                             T (&pnew)[NF][W], T (&acc)[2 * NF + 1])
 {
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            T v[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) v[f] = cu[f][j];
+            const T v02 = v[0] * v[0];
+            T dv[NF];
+            T Vs;
+            if constexpr (NF > 1) {
+                T others = (T)0, mo = (T)0;  // sum_{f>0} phi_f^2 and sum_{f>0} m2_f phi_f^2/2
+#pragma unroll
+                for (int f = 1; f < NF; ++f) {
+                    const T vf2 = v[f] * v[f];
+                    others += vf2;
+                    mo = fma_t(k.hm2[f], vf2, mo);
+                    dv[f] = v[f] * fma_t(k.q, v02, k.m2[f]);
+                }
+                dv[0] = v[0] * fma_t(k.q, others, fma_t(k.lam, v02, k.m2[0]));
+                Vs = fma_t(k.hq * v02, others, fma_t(v02, fma_t(k.qlam, v02, k.hm2[0]), mo));
+            } else {
+                dv[0] = v[0] * fma_t(k.lam, v02, k.m2[0]);
+                Vs = v02 * fma_t(k.qlam, v02, k.hm2[0]);
+            }
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const T cc = v[f];
+                const T left = (j == 0) ? xl[f] : cu[f][j - 1];
+                const T right = (j == W - 1) ? xr[f] : cu[f][j + 1];
+                const T lap = fma_t((T)-6, cc, ((left + right) + (ym[f][j] + yp[f][j])) + (zm[f][j] + zp[f][j]));
+                const T F = fma_t(k.wlx, lap, -k.wv * dv[f]);
+                const T pint = fma_t(k.hdt, F, pc[f][j]);
+                pnew[f][j] = fma_t(k.kdt, F, pc[f][j]);
+                acc[f] = fma_t(pint, pint, acc[f]);
+                acc[NF + f] = fma_t(-cc, lap, acc[NF + f]);
+            }
+            acc[2 * NF] += Vs;
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         T v[NF];
@@ -226,16 +283,9 @@ __device__ __forceinline__ void site_update(const Coefs<T, NF> &k, const T (&cu)
             const T left = (j == 0) ? xl[f] : cu[f][j - 1];
             const T right = (j == W - 1) ? xr[f] : cu[f][j + 1];
             const T dxp = right - cc, dyp = yp[f][j] - cc, dzp = zp[f][j] - cc;
-            T lap;
-            if constexpr (sizeof(T) == 8) {
-                // FP64: the neighbour sum minus 6 phi (fewer FP64-pipe operations; the
-                // differences below are only needed for the gradient energy)
-                lap = fma_t((T)-6, cc, ((left + right) + (ym[f][j] + yp[f][j])) + (zm[f][j] + zp[f][j]));
-            } else {
-                // FP32: differences first, so the small gradients stay exact
-                const T dxm = left - cc, dym = ym[f][j] - cc, dzm = zm[f][j] - cc;
-                lap = ((dxm + dxp) + (dym + dyp)) + (dzm + dzp);
-            }
+            // FP32: differences first, so the small gradients stay exact
+            const T dxm = left - cc, dym = ym[f][j] - cc, dzm = zm[f][j] - cc;
+            const T lap = ((dxm + dxp) + (dym + dyp)) + (dzm + dzp);
             const T F = k.wlx * lap - k.wv * dv[f];
             const T pint = fma_t(k.hdt, F, pc[f][j]);
             pnew[f][j] = fma_t(k.kdt, F, pc[f][j]);
