@@ -344,29 +344,58 @@ typedef struct {
 typedef struct tl_batch tl_batch; /* opaque */
 
 /* Group n existing lattices (same dtype; any N, n_fields, potential,
- * background) into a batch that tl_batch_step advances together.  Each
- * lattice is moved to the batch launch shape (tl_batch_pass_config) if it is
- * not on it, and keeps it afterwards; a batch step is bitwise tl_step of the
- * lattice alone on that shape.  The
+ * background) into a batch that tl_batch_step advances together (a lattice
+ * belongs to at most one batch at a time).  Each lattice is moved to the
+ * batch launch shape of its size (tl_batch_pass_config) if it is not on it,
+ * and keeps it afterwards; a batch step is bitwise tl_step of the lattice
+ * alone on that shape.  The batch's launch options are those
+ * tl_batch_autotune found for the same composition (multiset of N, fields,
+ * dtype) earlier in the process or in TL_TUNE_FILE, else the defaults.  The
  * lattices stay owned by the caller and cannot be destroyed or autotuned
  * while the batch exists; their own calls (tl_energies, tl_get_state,
  * tl_spectrum ...) keep working between batch steps.  cuda_stream: the
- * stream the batch runs on.  Errors: TL_EINVAL, TL_ENOMEM, TL_ECUDA. */
+ * stream the batch runs on.  No counterpart in the paper (Sec. 3.2's foreach
+ * over one lattice, here over many).  Errors: TL_EINVAL, TL_ENOMEM, TL_ECUDA. */
 int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_stream);
 
-/* The launch shape tl_batch_create gives a lattice of this size: the
- * TL_PASS_STREAM kernel with 256-thread CTAs and z-chunks of min(N, 32)
- * planes.  Set it with tl_set_pass_config on a lattice that should step alone
- * bitwise like its batched twin.  Errors: TL_EINVAL. */
+/* The launch shape tl_batch_create gives a lattice of this size on the
+ * current device: the TL_PASS_STREAM kernel with 256-thread CTAs, with the
+ * z-chunk and tile row width tl_batch_autotune measured for (N, n_fields,
+ * dtype, SM count) if it has, else z-chunks of min(N, 32) planes.  Set it
+ * with tl_set_pass_config on a lattice that should step alone bitwise like
+ * its batched twin.  Errors: TL_EINVAL. */
 int tl_batch_pass_config(int N, int n_fields, tl_dtype dtype, tl_pass_config *out);
 
 /* Advance every lattice of the batch by n steps of size dt, as tl_step
  * would, with one persistent launch per pass and per field count (each
  * launch walks all lattices' CTA tiles), the whole pass sequence captured
- * once as a CUDA graph per (n, dt, integrator) and replayed.  Each lattice
- * keeps its own launch geometry and reduction order, so its results are
- * bitwise those of tl_step on it alone.  Enqueues only. */
+ * once as a CUDA graph per (n, dt, integrator) and replayed; with the
+ * "split" option the field-count groups are independent branches of that
+ * graph, so their launches overlap on the device.  Each lattice keeps its
+ * own launch geometry and reduction order, so its results are bitwise those
+ * of tl_step on it alone.  Enqueues only. */
 int tl_batch_step(tl_batch *batch, int n, double dt, tl_integrator integrator);
+
+/* Choose the batch's launch shapes by measurement: for each class of members
+ * (same N and n_fields), largest total work first, time the z-chunks 4 ... N
+ * and tile row widths of the streaming kernel with the other classes held,
+ * keep the fastest (one coordinate-descent sweep); then the batch-level
+ * options (per-thread prefetch ring, field-count groups as graph branches,
+ * persistent grid split by work).  Each candidate is timed as CUDA-graph
+ * replays of the whole batch's grouped passes with zero kick and drift
+ * coefficients, which rewrite every state unchanged.  The members keep the
+ * chosen shapes; the shapes (per N, n_fields, dtype, SM count) and the
+ * options (per composition) are cached for later tl_batch_create calls in
+ * the process and appended to TL_TUNE_FILE when that names a file.
+ * best_ms_per_pass (may be NULL): the winner's time per grouped pass.
+ * Synchronises.  No counterpart in the paper.  Errors: TL_EINVAL, TL_ESTATE,
+ * TL_ECUDA. */
+int tl_batch_autotune(tl_batch *batch, double *best_ms_per_pass);
+
+/* The batch's launch options: prefetch (0 or 3 planes), split (field-count
+ * groups as independent graph branches, 0/1), share (persistent grid split
+ * among the groups by work, 0/1); any output may be NULL. */
+int tl_batch_get_options(const tl_batch *batch, int *prefetch, int *split, int *share);
 
 void tl_batch_destroy(tl_batch *batch);
 

@@ -16,6 +16,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -35,6 +36,17 @@ using tl::PassCoef;
         if (e_ != cudaSuccess) return tl::fail(TL_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));          \
     } while (0)
 
+namespace {
+
+// Launch options of a batch's grouped passes (the same for every member).
+struct BatchOpts {
+    int prefetch = 0;  // 0: plain streaming tiles; 3: per-thread cp.async ring three planes ahead
+    int split = 1;     // field-count groups as independent branches of the graph (else one chain)
+    int share = 0;     // 0: each group's persistent grid is 2 CTAs x SMs; 1: that grid split by work
+};
+
+}  // namespace
+
 struct tl_batch {
     struct Group {
         int nf = 0;
@@ -42,14 +54,19 @@ struct tl_batch {
         BatchJob *d_jobs[2] = {nullptr, nullptr}; // even / odd passes of a call
         unsigned *d_first = nullptr;          // first item of each job
         unsigned total = 0;                   // items (CTA tiles) over all jobs
+        double work = 0.0;                    // sites x fields of its lattices
         int grid = 0;                         // persistent CTAs
+        cudaStream_t branch = nullptr;        // capture stream of its graph branch (group 0: the capture stream)
+        cudaEvent_t done = nullptr;           // end of its branch
     };
     std::vector<tl_lattice *> lats;
     std::vector<Group> groups;
     int dtype = 0;
     int sm_count = 0;
+    BatchOpts opts;
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;
+    cudaEvent_t fork = nullptr;
     // graph of the last (n, dt, integrator)
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -95,22 +112,72 @@ int upload_jobs(tl_batch *B)
     return TL_OK;
 }
 
-int build_graph(tl_batch *B, int n, double dt, int integrator)
+// Item layout of every group from its members' current launch geometry, and
+// the persistent grid of each group's launch under the batch's options.
+int refresh_groups(tl_batch *B)
 {
-    std::vector<PassCoef> passes;
-    if (!tl::pass_schedule(n, dt, integrator, passes)) return tl::fail(TL_EINVAL, "unknown integrator %d", integrator);
-    if (B->exec) cudaGraphExecDestroy(B->exec);
-    if (B->graph) cudaGraphDestroy(B->graph);
-    B->exec = nullptr;
-    B->graph = nullptr;
+    const int per_sm = 2;  // the grouped kernel's register budget allows two CTAs per SM
+    const long full = (long)B->sm_count * per_sm;
+    double all = 0.0;
+    for (auto &g : B->groups) all += g.work;
+    std::vector<unsigned> first;
+    for (auto &g : B->groups) {
+        first.clear();
+        g.total = 0;
+        for (int i : g.idx) {
+            first.push_back(g.total);
+            g.total += B->lats[i]->geom.nblocks;
+        }
+        long want = full;
+        if (B->opts.share && B->groups.size() > 1 && all > 0.0) {
+            want = (long)(full * (g.work / all) + 0.5);
+            if (want < B->sm_count / 4) want = B->sm_count / 4 > 0 ? B->sm_count / 4 : 1;
+        }
+        g.grid = (int)((long)g.total < want ? (long)g.total : want);
+        if (g.grid < 1) g.grid = 1;
+        TB_CK(cudaMemcpyAsync(g.d_first, first.data(), first.size() * sizeof(unsigned), cudaMemcpyHostToDevice,
+                              B->stream));
+        TB_CK(cudaStreamSynchronize(B->stream));  // `first` is reused for the next group
+    }
+    return TL_OK;
+}
+
+// Capture `passes` over every group into an executable graph: each group's
+// passes form one chain on its own capture stream (a branch forked from and
+// joined back into the batch's capture stream) when opts.split is set, so the
+// groups' launches overlap on the device; else one chain of all groups.
+int capture_passes(tl_batch *B, const std::vector<PassCoef> &passes, cudaGraph_t *graph_out,
+                   cudaGraphExec_t *exec_out)
+{
+    *graph_out = nullptr;
+    *exec_out = nullptr;
     TB_CK(cudaStreamBeginCapture(B->capture, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (size_t p = 0; p < passes.size() && e == cudaSuccess; ++p)
-        for (auto &g : B->groups) {
-            e = tl::launch_group(B->dtype, g.nf, g.d_jobs[p & 1], g.d_first, (int)g.idx.size(), g.total, passes[p],
-                                 g.grid, B->capture);
-            if (e != cudaSuccess) break;
+    const bool split = B->opts.split && B->groups.size() > 1;
+    if (split) {
+        e = cudaEventRecord(B->fork, B->capture);
+        for (size_t gi = 1; gi < B->groups.size() && e == cudaSuccess; ++gi)
+            e = cudaStreamWaitEvent(B->groups[gi].branch, B->fork, 0);
+    }
+    if (split) {
+        for (size_t gi = 0; gi < B->groups.size() && e == cudaSuccess; ++gi) {
+            auto &g = B->groups[gi];
+            cudaStream_t s = gi == 0 ? B->capture : g.branch;
+            for (size_t p = 0; p < passes.size() && e == cudaSuccess; ++p)
+                e = tl::launch_group(B->dtype, g.nf, B->opts.prefetch, g.d_jobs[p & 1], g.d_first, (int)g.idx.size(),
+                                     g.total, passes[p], g.grid, s);
+            if (gi > 0 && e == cudaSuccess) e = cudaEventRecord(g.done, s);
         }
+        for (size_t gi = 1; gi < B->groups.size() && e == cudaSuccess; ++gi)
+            e = cudaStreamWaitEvent(B->capture, B->groups[gi].done, 0);
+    } else {
+        for (size_t p = 0; p < passes.size() && e == cudaSuccess; ++p)
+            for (auto &g : B->groups) {
+                e = tl::launch_group(B->dtype, g.nf, B->opts.prefetch, g.d_jobs[p & 1], g.d_first,
+                                     (int)g.idx.size(), g.total, passes[p], g.grid, B->capture);
+                if (e != cudaSuccess) break;
+            }
+    }
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(B->capture, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -123,24 +190,75 @@ int build_graph(tl_batch *B, int n, double dt, int integrator)
         cudaGraphDestroy(graph);
         return tl::fail(TL_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
     }
-    B->graph = graph;
-    B->exec = exec;
+    *graph_out = graph;
+    *exec_out = exec;
+    return TL_OK;
+}
+
+void drop_graph(tl_batch *B)
+{
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+    B->g_n = -1;
+}
+
+int build_graph(tl_batch *B, int n, double dt, int integrator)
+{
+    std::vector<PassCoef> passes;
+    if (!tl::pass_schedule(n, dt, integrator, passes)) return tl::fail(TL_EINVAL, "unknown integrator %d", integrator);
+    drop_graph(B);
+    int rc = capture_passes(B, passes, &B->graph, &B->exec);
+    if (rc) return rc;
     B->g_n = n;
     B->g_dt = dt;
     B->g_integ = integrator;
     return TL_OK;
 }
 
-}  // namespace
+// ---- batch launch shapes ------------------------------------------------------
+// A member's shape in a batch: the register-streaming tiles with 256-thread
+// CTAs (what the grouped kernel runs).  Untuned, z-chunks of 32 planes (the
+// whole lattice below that), so that each (lattice, tile) item of the grouped
+// launch carries enough planes to amortise its fixed costs (locating the job,
+// the coefficient set-up, the FP64 reduction of its sums); tl_batch_autotune
+// replaces this rule by measured shapes per (N, fields, dtype, SMs), and the
+// batch-level options per batch composition.
 
-namespace {
+typedef std::tuple<int, int, int, int> ClassKey;  // N, fields, dtype, SMs
+std::mutex g_batch_mu;
+std::map<ClassKey, tl::PassTuning> g_batch_shapes;
+std::map<std::string, BatchOpts> g_batch_opts;  // composition signature -> options
 
-// The launch shape of batch members: the register-streaming tiles with
-// 256-thread CTAs (what the grouped kernel runs) and z-chunks of 32 planes
-// (the whole lattice below that), so that each (lattice, tile) item of the
-// grouped launch carries enough planes to amortise its fixed costs (locating
-// the job, the coefficient set-up, the FP64 reduction of its sums).
-tl::PassTuning batch_tuning(int N) { return tl::PassTuning{tl::kVariantLdg, 7, 0, N < 32 ? N : 32, 0, 256, 0}; }
+tl::PassTuning batch_rule(int N) { return tl::PassTuning{tl::kVariantLdg, 7, 0, N < 32 ? N : 32, 0, 256, 0}; }
+
+void ensure_tune_loaded();  // TL_TUNE_FILE, read once (autotuner section below)
+
+tl::PassTuning batch_tuning(int N, int nf, int dtype, int sms)
+{
+    ensure_tune_loaded();
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    auto it = g_batch_shapes.find(ClassKey(N, nf, dtype, sms));
+    return it != g_batch_shapes.end() ? it->second : batch_rule(N);
+}
+
+std::string composition(const std::vector<tl_lattice *> &lats)
+{
+    std::map<std::tuple<int, int, int>, int> cnt;
+    for (tl_lattice *L : lats) cnt[std::make_tuple(L->N, L->nf, (int)L->dtype)]++;
+    std::string s = std::to_string(lats.empty() ? 0 : lats[0]->sm_count);
+    for (auto &kv : cnt)
+        s += ":" + std::to_string(std::get<0>(kv.first)) + "x" + std::to_string(std::get<1>(kv.first)) + "x" +
+             std::to_string(std::get<2>(kv.first)) + "=" + std::to_string(kv.second);
+    return s;
+}
+
+bool same_shape(const tl::PassTuning &a, const tl::PassTuning &b)
+{
+    return a.variant == b.variant && a.threads == b.threads && a.zc == b.zc && a.txt == b.txt &&
+           a.prefetch == b.prefetch;
+}
 
 }  // namespace
 
@@ -153,8 +271,12 @@ int tl_batch_pass_config(int N, int n_fields, tl_dtype dtype, tl_pass_config *ou
     if (N < 8 || N % 4 != 0 || N > 2048 || n_fields < 1 || n_fields > TL_MAX_FIELDS ||
         (dtype != TL_F32 && dtype != TL_F64))
         return tl::fail(TL_EINVAL, "bad lattice shape");
-    const tl::PassTuning t = batch_tuning(N);
-    *out = tl_pass_config{TL_PASS_STREAM, 0, 0, t.zc, 0, t.threads};
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        sms = 0;
+    const tl::PassTuning t = batch_tuning(N, n_fields, (int)dtype, sms);
+    *out = tl_pass_config{TL_PASS_STREAM, 0, 0, t.zc, t.txt, t.threads};
     return TL_OK;
 }
 
@@ -166,18 +288,9 @@ int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_s
     for (int i = 0; i < n; ++i) {
         if (!lats[i]) return tl::fail(TL_EINVAL, "lattice %d is NULL", i);
         if (lats[i]->dtype != lats[0]->dtype) return tl::fail(TL_EINVAL, "all lattices of a batch share one dtype");
+        if (lats[i]->batch_refs > 0) return tl::fail(TL_EINVAL, "lattice %d is already in a batch", i);
         for (int k = 0; k < i; ++k)
             if (lats[k] == lats[i]) return tl::fail(TL_EINVAL, "lattice %d appears twice", i);
-    }
-    // members move to the batch shape (and keep it afterwards)
-    for (int i = 0; i < n; ++i) {
-        tl_lattice *L = lats[i];
-        const tl::PassTuning t = batch_tuning(L->N);
-        if (L->tuning.variant != t.variant || L->tuning.threads != t.threads || L->tuning.zc != t.zc ||
-            L->tuning.txt != t.txt || L->tuning.prefetch != t.prefetch) {
-            int rc = tl::set_geometry(L, t);
-            if (rc) return rc;
-        }
     }
     tl_batch *B = new (std::nothrow) tl_batch();
     if (!B) return tl::fail(TL_ENOMEM, "host allocation failed");
@@ -185,31 +298,56 @@ int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_s
     B->dtype = (int)lats[0]->dtype;
     B->stream = static_cast<cudaStream_t>(cuda_stream);
     B->sm_count = lats[0]->sm_count;
+    ensure_tune_loaded();
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        auto it = g_batch_opts.find(composition(B->lats));
+        if (it != g_batch_opts.end()) B->opts = it->second;
+    }
+    // environment override of the options (tuning experiments): "prefetch,split,share"
+    if (const char *v = getenv("TL_BATCH_OPTIONS")) {
+        int pf = 0, sp = 1, sh = 0;
+        if (sscanf(v, "%d,%d,%d", &pf, &sp, &sh) == 3 && (pf == 0 || pf == 3) && (sp == 0 || sp == 1) &&
+            (sh == 0 || sh == 1))
+            B->opts = BatchOpts{pf, sp, sh};
+    }
+    // members move to the batch shape (and keep it afterwards); every member
+    // of a batch runs with the batch's prefetch option
+    for (int i = 0; i < n; ++i) {
+        tl_lattice *L = lats[i];
+        tl::PassTuning t = batch_tuning(L->N, L->nf, (int)L->dtype, L->sm_count);
+        t.prefetch = B->opts.prefetch;
+        if (!same_shape(L->tuning, t)) {
+            int rc = tl::set_geometry(L, t);
+            if (rc) {
+                delete B;
+                return rc;
+            }
+        }
+    }
     int rc = TL_OK;
     cudaError_t e = cudaStreamCreateWithFlags(&B->capture, cudaStreamNonBlocking);
-    if (e != cudaSuccess) rc = tl::fail(TL_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) rc = tl::fail(TL_ECUDA, "stream/event creation: %s", cudaGetErrorString(e));
     for (int nf = 1; nf <= TL_MAX_FIELDS && rc == TL_OK; ++nf) {
         tl_batch::Group g;
         g.nf = nf;
-        std::vector<unsigned> first;
         for (int i = 0; i < n; ++i)
             if (lats[i]->nf == nf) {
                 g.idx.push_back(i);
-                first.push_back(g.total);
-                g.total += lats[i]->geom.nblocks;
+                g.work += (double)lats[i]->N * lats[i]->N * lats[i]->N * nf;
             }
         if (g.idx.empty()) continue;
-        const int per_sm = 2;  // the grouped kernel's register budget allows two CTAs per SM
-        const long want = (long)B->sm_count * per_sm;
-        g.grid = (int)((long)g.total < want ? (long)g.total : want);
         const size_t jb = g.idx.size() * sizeof(BatchJob);
         if ((e = cudaMalloc(&g.d_jobs[0], jb)) != cudaSuccess || (e = cudaMalloc(&g.d_jobs[1], jb)) != cudaSuccess ||
-            (e = cudaMalloc(&g.d_first, first.size() * sizeof(unsigned))) != cudaSuccess ||
-            (e = cudaMemcpy(g.d_first, first.data(), first.size() * sizeof(unsigned), cudaMemcpyHostToDevice)) !=
-                cudaSuccess)
+            (e = cudaMalloc(&g.d_first, g.idx.size() * sizeof(unsigned))) != cudaSuccess)
             rc = tl::fail(TL_ENOMEM, "batch descriptors: %s", cudaGetErrorString(e));
+        if (rc == TL_OK && ((e = cudaStreamCreateWithFlags(&g.branch, cudaStreamNonBlocking)) != cudaSuccess ||
+                            (e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming)) != cudaSuccess))
+            rc = tl::fail(TL_ECUDA, "stream/event creation: %s", cudaGetErrorString(e));
         B->groups.push_back(g);
     }
+    if (rc == TL_OK) rc = refresh_groups(B);
     if (rc) {
         tl_batch_destroy(B);
         return rc;
@@ -223,18 +361,36 @@ void tl_batch_destroy(tl_batch *B)
 {
     if (!B) return;
     cudaStreamSynchronize(B->stream);
-    if (B->exec) cudaGraphExecDestroy(B->exec);
-    if (B->graph) cudaGraphDestroy(B->graph);
+    drop_graph(B);
     for (auto &g : B->groups) {
         cudaFree(g.d_jobs[0]);
         cudaFree(g.d_jobs[1]);
         cudaFree(g.d_first);
+        if (g.branch) cudaStreamDestroy(g.branch);
+        if (g.done) cudaEventDestroy(g.done);
     }
+    if (B->fork) cudaEventDestroy(B->fork);
     if (B->capture) cudaStreamDestroy(B->capture);
     for (tl_lattice *L : B->lats)
         if (L->batch_refs > 0) L->batch_refs--;
     delete B;
 }
+
+namespace {
+
+int check_members(tl_batch *B)
+{
+    for (tl_lattice *L : B->lats) {
+        if (!L->has_pot || !L->has_state) return tl::fail(TL_ESTATE, "every lattice needs a potential and a state");
+        if (L->dtype != (tl_dtype)B->dtype) return tl::fail(TL_EINVAL, "dtype changed");
+    }
+    // the lattices' own streams must be done with earlier work before the batch stream runs
+    for (tl_lattice *L : B->lats)
+        if (L->stream != B->stream) TB_CK(cudaStreamSynchronize(L->stream));
+    return TL_OK;
+}
+
+}  // namespace
 
 int tl_batch_step(tl_batch *B, int n, double dt, tl_integrator integrator)
 {
@@ -242,15 +398,10 @@ int tl_batch_step(tl_batch *B, int n, double dt, tl_integrator integrator)
     if (!B) return tl::fail(TL_EINVAL, "NULL batch");
     if (n < 0) return tl::fail(TL_EINVAL, "n must be >= 0");
     if (!isfinite(dt) || dt == 0.0) return tl::fail(TL_EINVAL, "dt must be finite and nonzero");
-    for (tl_lattice *L : B->lats) {
-        if (!L->has_pot || !L->has_state) return tl::fail(TL_ESTATE, "every lattice needs a potential and a state");
-        if (L->dtype != (tl_dtype)B->dtype) return tl::fail(TL_EINVAL, "dtype changed");
-    }
+    int rc = check_members(B);
+    if (rc) return rc;
     if (n == 0) return TL_OK;
-    // the lattices' own streams must be done with earlier work before the batch stream runs
-    for (tl_lattice *L : B->lats)
-        if (L->stream != B->stream) TB_CK(cudaStreamSynchronize(L->stream));
-    int rc = upload_jobs(B);
+    rc = upload_jobs(B);
     if (rc) return rc;
     if (!(B->exec && B->g_n == n && B->g_dt == dt && B->g_integ == (int)integrator)) {
         rc = build_graph(B, n, dt, (int)integrator);
@@ -296,6 +447,14 @@ const char *const kTuneFmt =
     "{\"N\": %d, \"fields\": %d, \"dtype\": %d, \"sms\": %d, \"variant\": %d, \"warps\": %d, "
     "\"stages\": %d, \"z_chunk\": %d, \"prefetch\": %d, \"threads\": %d, \"tile_x\": %d, \"ms\": %lf}";
 
+// Batch entries (tl_batch_autotune): one member shape per (N, fields, dtype,
+// SMs), and the launch options of one batch composition.
+const char *const kBatchShapeFmt =
+    "{\"batch_shape\": {\"N\": %d, \"fields\": %d, \"dtype\": %d, \"sms\": %d, \"z_chunk\": %d, "
+    "\"tile_x\": %d, \"prefetch\": %d}}";
+const char *const kBatchOptsFmt = "{\"batch_options\": {\"prefetch\": %d, \"split\": %d, \"share\": %d, "
+                                  "\"composition\": \"%255[^\"]\"}}";
+
 void load_tune_file()
 {
     g_tune_loaded = true;
@@ -305,6 +464,25 @@ void load_tune_file()
     if (!f) return;
     char line[512];
     while (fgets(line, sizeof line, f)) {
+        {
+            int N, nf, dt, sms, zc, txt, pf, sp, sh;
+            char comp[256];
+            if (sscanf(line, kBatchShapeFmt, &N, &nf, &dt, &sms, &zc, &txt, &pf) == 7) {
+                if (N >= 8 && nf >= 1 && nf <= TL_MAX_FIELDS && (dt == 0 || dt == 1) && zc >= 1 && zc <= N &&
+                    (txt == 0 || txt == 8 || txt == 16 || txt == 32) && (pf == 0 || pf == 3)) {
+                    std::lock_guard<std::mutex> lk(g_batch_mu);
+                    g_batch_shapes[ClassKey(N, nf, dt, sms)] = tl::PassTuning{tl::kVariantLdg, 7, 0, zc, pf, 256, txt};
+                }
+                continue;
+            }
+            if (sscanf(line, kBatchOptsFmt, &pf, &sp, &sh, comp) == 4) {
+                if ((pf == 0 || pf == 3) && (sp == 0 || sp == 1) && (sh == 0 || sh == 1)) {
+                    std::lock_guard<std::mutex> lk(g_batch_mu);
+                    g_batch_opts[comp] = BatchOpts{pf, sp, sh};
+                }
+                continue;
+            }
+        }
         int N, nf, dt, sms, var, cw, st, zc, pf, th, txt;
         double ms;
         if (sscanf(line, kTuneFmt, &N, &nf, &dt, &sms, &var, &cw, &st, &zc, &pf, &th, &txt, &ms) != 12) continue;
@@ -316,6 +494,12 @@ void load_tune_file()
         g_tune[TuneKey(N, nf, dt, sms)] = TuneVal{t, ms};
     }
     fclose(f);
+}
+
+void ensure_tune_loaded()
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune_loaded) load_tune_file();
 }
 
 void save_tune_entry(const TuneKey &k, const TuneVal &v)
@@ -411,5 +595,190 @@ extern "C" int tl_autotune(tl_lattice *L, double *best_ms_per_pass)
         save_tune_entry(key, TuneVal{best_t, best});
     }
     if (best_ms_per_pass) *best_ms_per_pass = best;
+    return TL_OK;
+}
+
+// ---- batch autotuner ------------------------------------------------------------
+
+namespace {
+
+void append_tune_line(const char *line)
+{
+    const char *path = getenv("TL_TUNE_FILE");
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fputs(line, f);
+    fputs("\n", f);
+    fclose(f);
+}
+
+// Average time of one grouped identity pass over the whole batch (ms): passes
+// with zero kick and drift coefficients rewrite every state unchanged; an
+// even number of them leaves each lattice's buffers where they started.
+int time_identity(tl_batch *B, cudaEvent_t e0, cudaEvent_t e1, double *ms_out)
+{
+    int rc = refresh_groups(B);
+    if (rc) return rc;
+    rc = upload_jobs(B);
+    if (rc) return rc;
+    const int reps = 6;
+    std::vector<PassCoef> passes(reps, PassCoef{});
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    rc = capture_passes(B, passes, &graph, &exec);
+    if (rc) return rc;
+    cudaError_t e = cudaGraphLaunch(exec, B->stream);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, B->stream);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaGraphLaunch(exec, B->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, B->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return tl::fail(TL_ECUDA, "batch autotune: %s", cudaGetErrorString(e));
+    *ms_out = ms / (2.0 * reps);
+    return TL_OK;
+}
+
+}  // namespace
+
+extern "C" int tl_batch_autotune(tl_batch *B, double *best_ms_per_pass)
+{
+    tl::set_error(TL_OK, "", "");
+    if (!B) return tl::fail(TL_EINVAL, "NULL batch");
+    int rc = check_members(B);
+    if (rc) return rc;
+    ensure_tune_loaded();
+    drop_graph(B);
+    // classes of members: (N, fields), largest total work first
+    struct Cls {
+        int N, nf;
+        double work;
+        std::vector<tl_lattice *> members;
+        tl::PassTuning t;
+    };
+    std::vector<Cls> cls;
+    for (tl_lattice *L : B->lats) {
+        Cls *c = nullptr;
+        for (auto &k : cls)
+            if (k.N == L->N && k.nf == L->nf) c = &k;
+        if (!c) {
+            cls.push_back(Cls{L->N, L->nf, 0.0, {}, L->tuning});
+            c = &cls.back();
+        }
+        c->members.push_back(L);
+        c->work += (double)L->N * L->N * L->N * L->nf;
+    }
+    std::sort(cls.begin(), cls.end(), [](const Cls &a, const Cls &b) { return a.work > b.work; });
+    auto apply = [&](Cls &c, const tl::PassTuning &t) -> int {
+        for (tl_lattice *L : c.members) {
+            int r = tl::set_geometry(L, t);
+            if (r) return r;
+        }
+        return TL_OK;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TB_CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return tl::fail(TL_ECUDA, "cudaEventCreate failed");
+    }
+    double best = 0.0;
+    rc = time_identity(B, e0, e1, &best);
+    // coordinate descent, one sweep: each class's z-chunk and tile row width
+    // with the others held at their current best
+    for (size_t ci = 0; ci < cls.size() && rc == TL_OK; ++ci) {
+        Cls &c = cls[ci];
+        const int per_row = c.N / (B->dtype == TL_F64 ? 2 : 4);
+        std::vector<tl::PassTuning> cands;
+        for (int txt : {0, 16, 8}) {
+            if (txt && txt >= per_row) continue;  // the same tile as txt = 0
+            for (int zc : {4, 8, 16, 32, 64, 128, c.N}) {
+                if (zc > c.N) continue;
+                tl::PassTuning t{tl::kVariantLdg, 7, 0, zc, B->opts.prefetch, 256, txt};
+                bool dup = same_shape(t, c.t);
+                for (auto &o : cands) dup = dup || same_shape(o, t);
+                if (!dup) cands.push_back(t);
+            }
+        }
+        for (const auto &t : cands) {
+            const tl::PassTuning keep = c.t;
+            if ((rc = apply(c, t))) break;
+            double ms = 0.0;
+            if ((rc = time_identity(B, e0, e1, &ms))) break;
+            if (ms < best) {
+                best = ms;
+                c.t = t;
+            } else if ((rc = apply(c, keep))) {
+                break;
+            }
+        }
+    }
+    // batch-level options: prefetch ring, independent branches, grid split
+    if (rc == TL_OK) {
+        const BatchOpts start = B->opts;
+        BatchOpts best_o = start;
+        for (int pf : {0, 3})
+            for (int sp : {1, 0})
+                for (int sh : {0, 1}) {
+                    if (rc) break;
+                    BatchOpts o{pf, sp, sh};
+                    if (o.prefetch == start.prefetch && o.split == start.split && o.share == start.share) continue;
+                    if (B->groups.size() < 2 && (sp == 0 || sh == 1)) continue;  // no effect with one group
+                    B->opts = o;
+                    for (auto &c : cls) {
+                        c.t.prefetch = pf;
+                        if ((rc = apply(c, c.t))) break;
+                    }
+                    if (rc) break;
+                    double ms = 0.0;
+                    if ((rc = time_identity(B, e0, e1, &ms))) break;
+                    if (ms < best) {
+                        best = ms;
+                        best_o = o;
+                    }
+                }
+        if (rc == TL_OK) {
+            B->opts = best_o;
+            for (auto &c : cls) {
+                c.t.prefetch = best_o.prefetch;
+                if ((rc = apply(c, c.t))) break;
+            }
+        }
+        if (rc == TL_OK) rc = refresh_groups(B);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        for (auto &c : cls) g_batch_shapes[ClassKey(c.N, c.nf, B->dtype, B->sm_count)] = c.t;
+        g_batch_opts[composition(B->lats)] = B->opts;
+    }
+    char buf[512];
+    for (auto &c : cls) {
+        snprintf(buf, sizeof buf, kBatchShapeFmt, c.N, c.nf, B->dtype, B->sm_count, c.t.zc, c.t.txt, c.t.prefetch);
+        append_tune_line(buf);
+    }
+    const std::string comp = composition(B->lats);
+    if (comp.size() < 255) {
+        snprintf(buf, sizeof buf, "{\"batch_options\": {\"prefetch\": %d, \"split\": %d, \"share\": %d, "
+                                  "\"composition\": \"%s\"}}",
+                 B->opts.prefetch, B->opts.split, B->opts.share, comp.c_str());
+        append_tune_line(buf);
+    }
+    if (best_ms_per_pass) *best_ms_per_pass = best;
+    return TL_OK;
+}
+
+extern "C" int tl_batch_get_options(const tl_batch *B, int *prefetch, int *split, int *share)
+{
+    tl::set_error(TL_OK, "", "");
+    if (!B) return tl::fail(TL_EINVAL, "NULL batch");
+    if (prefetch) *prefetch = B->opts.prefetch;
+    if (split) *split = B->opts.split;
+    if (share) *share = B->opts.share;
     return TL_OK;
 }

@@ -130,9 +130,11 @@ struct BatchJob {
 };
 
 // Enqueue one grouped pass over every job (all with n_fields == nf) as a
-// persistent launch of `grid` CTAs walking the (job, tile) items.
-cudaError_t launch_group(int dtype, int nf, const BatchJob *jobs, const unsigned *first_item, int njobs,
-                         unsigned total, const PassCoef &c, int grid, cudaStream_t s);
+// persistent launch of `grid` CTAs of 256 threads walking the (job, tile)
+// items; prefetch > 0 runs the variant whose threads prefetch their words
+// three planes ahead (cp.async), the same arithmetic.
+cudaError_t launch_group(int dtype, int nf, int prefetch, const BatchJob *jobs, const unsigned *first_item,
+                         int njobs, unsigned total, const PassCoef &c, int grid, cudaStream_t s);
 
 // Enqueue one fused pass (measure_only: energies of the stored state, no writes).
 cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,

@@ -121,16 +121,16 @@ cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const Pa
                            : launch_pass_f64(m, fp, c, g, sc, slots, measure_only, s, maps);
 }
 
-cudaError_t launch_group_f32(int nf, const BatchJob *jobs, const unsigned *first_item, int njobs, unsigned total,
-                             const PassCoef &c, int grid, cudaStream_t s);
-cudaError_t launch_group_f64(int nf, const BatchJob *jobs, const unsigned *first_item, int njobs, unsigned total,
-                             const PassCoef &c, int grid, cudaStream_t s);
+cudaError_t launch_group_f32(int nf, int prefetch, const BatchJob *jobs, const unsigned *first_item, int njobs,
+                             unsigned total, const PassCoef &c, int grid, cudaStream_t s);
+cudaError_t launch_group_f64(int nf, int prefetch, const BatchJob *jobs, const unsigned *first_item, int njobs,
+                             unsigned total, const PassCoef &c, int grid, cudaStream_t s);
 
-cudaError_t launch_group(int dtype, int nf, const BatchJob *jobs, const unsigned *first_item, int njobs,
-                         unsigned total, const PassCoef &c, int grid, cudaStream_t s)
+cudaError_t launch_group(int dtype, int nf, int prefetch, const BatchJob *jobs, const unsigned *first_item,
+                         int njobs, unsigned total, const PassCoef &c, int grid, cudaStream_t s)
 {
-    return dtype == TL_F32 ? launch_group_f32(nf, jobs, first_item, njobs, total, c, grid, s)
-                           : launch_group_f64(nf, jobs, first_item, njobs, total, c, grid, s);
+    return dtype == TL_F32 ? launch_group_f32(nf, prefetch, jobs, first_item, njobs, total, c, grid, s)
+                           : launch_group_f64(nf, prefetch, jobs, first_item, njobs, total, c, grid, s);
 }
 
 // Refresh the ghost copies of one array (layout in tl_internal.cuh): the W

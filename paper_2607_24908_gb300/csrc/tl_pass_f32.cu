@@ -15,18 +15,15 @@ cudaError_t launch_pass_f32(const Model &m, const FieldPtrs &fp, const PassCoef 
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_group_f32(int nf, const BatchJob *jobs, const unsigned *first_item, int njobs, unsigned total,
-                              const PassCoef &c, int grid, cudaStream_t s)
+cudaError_t launch_group_f32(int nf, int prefetch, const BatchJob *jobs, const unsigned *first_item, int njobs,
+                              unsigned total, const PassCoef &c, int grid, cudaStream_t s)
 {
-    // the staged job table (see fused_pass_group)
-    const size_t smem = njobs <= kGroupStagedJobs ? (size_t)njobs * sizeof(unsigned) : 0;
     switch (nf) {
-    case 1: fused_pass_group<float, 1><<<grid, 256, smem, s>>>(jobs, first_item, njobs, total, c); break;
-    case 2: fused_pass_group<float, 2><<<grid, 256, smem, s>>>(jobs, first_item, njobs, total, c); break;
-    case 3: fused_pass_group<float, 3><<<grid, 256, smem, s>>>(jobs, first_item, njobs, total, c); break;
-    default: return cudaErrorInvalidValue;
+    case 1: return launch_group_t<float, 1>(prefetch, jobs, first_item, njobs, total, c, grid, s);
+    case 2: return launch_group_t<float, 2>(prefetch, jobs, first_item, njobs, total, c, grid, s);
+    case 3: return launch_group_t<float, 3>(prefetch, jobs, first_item, njobs, total, c, grid, s);
     }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace tl

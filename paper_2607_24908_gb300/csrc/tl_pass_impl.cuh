@@ -598,13 +598,27 @@ __global__ void __launch_bounds__(NT, 512 / NT) fused_pass_ldg(Model m, FieldPtr
 // The job table (first item of each job) is staged in shared memory once per
 // CTA when it fits (kGroupStagedJobs entries), so locating an item's job is a
 // binary search in shared memory rather than a chain of dependent global loads.
+// D > 0: each thread prefetches its words D planes ahead with cp.async into a
+// per-thread ring placed after the staged table (group_smem_bytes).
 constexpr int kGroupStagedJobs = 8192;
 
-template <typename T, int NF>
-__global__ void __launch_bounds__(256, 2) fused_pass_group(const BatchJob *jobs, const unsigned *first_item, int njobs,
+__host__ __device__ constexpr size_t group_table_bytes(int njobs)
+{
+    return njobs <= kGroupStagedJobs ? ((size_t)njobs * sizeof(unsigned) + 15) / 16 * 16 : 0;
+}
+__host__ __device__ constexpr size_t group_smem_bytes(int njobs, int nf, int D)
+{
+    return group_table_bytes(njobs) + (size_t)D * nf * 2 * 256 * 16;
+}
+
+template <typename T, int NF, int D>
+__global__ void __launch_bounds__(256, 2) fused_pass_group(const BatchJob *__restrict__ jobs,
+                                                           const unsigned *__restrict__ first_item, int njobs,
                                                            unsigned total, PassCoef c)
 {
-    extern __shared__ unsigned s_first[];
+    extern __shared__ __align__(16) unsigned char g_smem[];
+    unsigned *s_first = reinterpret_cast<unsigned *>(g_smem);
+    unsigned char *ring = g_smem + group_table_bytes(njobs);
     const bool staged = njobs <= kGroupStagedJobs;
     if (staged) {
         for (int i = threadIdx.x; i < njobs; i += blockDim.x) s_first[i] = __ldg(first_item + i);
@@ -623,8 +637,36 @@ __global__ void __launch_bounds__(256, 2) fused_pass_group(const BatchJob *jobs,
         const int bx = (int)(local % (unsigned)j.gx);
         const int by = (int)((local / (unsigned)j.gx) % (unsigned)j.gy);
         const int bz = (int)(local / ((unsigned)j.gx * (unsigned)j.gy));
-        ldg_tile<T, NF, false, 0>(j.m, j.fp, c, j.txt, j.ty, j.zc, bx, by, bz, local, j.nblocks, j.sc, j.slots, nullptr);
+        ldg_tile<T, NF, false, D>(j.m, j.fp, c, j.txt, j.ty, j.zc, bx, by, bz, local, j.nblocks, j.sc, j.slots, ring);
     }
+}
+
+// Enqueue one grouped pass (see launch_group).
+template <typename T, int NF>
+static cudaError_t launch_group_t(int prefetch, const BatchJob *jobs, const unsigned *first_item, int njobs,
+                                  unsigned total, const PassCoef &c, int grid, cudaStream_t s)
+{
+    const int D = prefetch > 0 ? 3 : 0;
+    const size_t smem = group_smem_bytes(njobs, NF, D);
+    auto kern = D ? fused_pass_group<T, NF, 3> : fused_pass_group<T, NF, 0>;
+    if (smem > 48 * 1024) {
+        // the opt-in limit for this kernel (per device, set once; an equal or smaller request needs nothing)
+        static std::atomic<size_t> configured[64][2];
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        std::atomic<size_t> &done = configured[dev][D ? 1 : 0];
+        if (smem > done.load(std::memory_order_acquire)) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            size_t cur = done.load(std::memory_order_relaxed);
+            while (smem > cur && !done.compare_exchange_weak(cur, smem, std::memory_order_release)) {
+            }
+        }
+    }
+    kern<<<grid, 256, smem, s>>>(jobs, first_item, njobs, total, c);
+    return cudaGetLastError();
 }
 
 // ---- PTX helpers for asynchronous copies ---------------------------------------

@@ -104,6 +104,9 @@ _SIGS = {
                                        ctypes.c_void_p]),
     "tl_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
     "tl_batch_destroy": (None, [ctypes.c_void_p]),
+    "tl_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "tl_batch_get_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "tl_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tl_set_pass_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_pass_config)]),
     "tl_commit_state": (ctypes.c_int, [ctypes.c_void_p]),
@@ -331,6 +334,18 @@ def tl_batch_destroy(b):
     lib().tl_batch_destroy(b)
 
 
+def tl_batch_autotune(b) -> float:
+    ms = ctypes.c_double()
+    _check(lib().tl_batch_autotune(b, ctypes.byref(ms)))
+    return ms.value
+
+
+def tl_batch_get_options(b) -> dict:
+    v = [ctypes.c_int() for _ in range(3)]
+    _check(lib().tl_batch_get_options(b, *[ctypes.byref(x) for x in v]))
+    return {"prefetch": v[0].value, "split": v[1].value, "share": v[2].value}
+
+
 def tl_autotune(h) -> float:
     ms = ctypes.c_double()
     _check(lib().tl_autotune(h, ctypes.byref(ms)))
@@ -383,6 +398,14 @@ class Batch:
 
     def step(self, n: int, dt: float, integrator="verlet"):
         tl_batch_step(self.b, n, dt, INTEGRATORS[integrator] if isinstance(integrator, str) else integrator)
+
+    def autotune(self) -> float:
+        """Choose the members' batch shapes and the batch options by
+        measurement (see tl_batch_autotune); returns ms per grouped pass."""
+        return tl_batch_autotune(self.b)
+
+    def options(self) -> dict:
+        return tl_batch_get_options(self.b)
 
     def close(self):
         if getattr(self, "b", None):

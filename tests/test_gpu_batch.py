@@ -1,4 +1,4 @@
-"""Batched ensembles (tl_batch_*) and the autotuner on the GPU.
+"""Batched ensembles (tl_batch_*) and the autotuners on the GPU.
 
 A batch advances lattices of uneven N, 1-2 fields, different couplings,
 backgrounds and seeds with one persistent launch per pass (per field count)
@@ -167,4 +167,63 @@ def test_ensemble_recipe_fp32_batch_against_oracle():
         tol = f32_pi_tol(p, steps + 1, float(np.max(np.abs(ophi))), float(np.max(np.abs(opi))))
         assert normwise(pi, opi) < tol, (job, normwise(pi, opi), tol)
         assert abs(E.a - oa) / oa < 1e-5 and abs(E.b - ob) / ob < 1e-5, job
+        lat.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_batch_autotune_keeps_state_and_steps_bitwise_like_each_member_alone(dtype, tmp_path, monkeypatch):
+    """tl_batch_autotune times member shapes and batch options with identity passes: it leaves
+    every state untouched; the tuned batch then steps each member bitwise like tl_step on the
+    member alone on its tuned shape (tl_batch_pass_config reports it); the shapes and options
+    go to the cache file; and FP64 members still match the oracle to 1e-12."""
+    monkeypatch.setenv("TL_TUNE_FILE", str(tmp_path / "tune.txt"))
+    dt, steps = 0.01, 12
+    # the shapes the members start on (their b0 from the constraint is reduced under them)
+    before = {(N, nf): T.batch_pass_config(N, nf, dtype) for N, nf, _, _, _ in JOBS}
+    lats, inputs = [], []
+    for N, nf, q, ex, seed in JOBS:
+        lat = make(N, nf, q, ex, dtype)
+        inputs.append(fill(lat, N, nf, seed, dtype))
+        lats.append(lat)
+    E0 = [lat.energies() for lat in lats]
+    with T.Batch(lats) as b:
+        ms = b.autotune()
+        assert ms > 0
+        opts = b.options()
+        assert opts["prefetch"] in (0, 3) and opts["split"] in (0, 1) and opts["share"] in (0, 1)
+        for lat, (phi0, pi0), e0 in zip(lats, inputs, E0):
+            phi, pi = lat.get_all()
+            assert np.array_equal(phi, phi0) and np.array_equal(pi, pi0)
+            e1 = lat.energies()
+            assert e1.a == e0.a and e1.b == e0.b
+        b.step(steps, dt, "verlet")
+    recs = [json.loads(line) for line in (tmp_path / "tune.txt").read_text().strip().splitlines()]
+    shapes = {(r["batch_shape"]["N"], r["batch_shape"]["fields"]): r["batch_shape"] for r in recs
+              if "batch_shape" in r}
+    assert set(shapes) == {(N, nf) for N, nf, _, _, _ in JOBS}
+    assert sum("batch_options" in r for r in recs) == 1
+    for lat, (N, nf, q, ex, seed), (phi0, pi0) in zip(lats, JOBS, inputs):
+        cfg = T.batch_pass_config(N, nf, dtype)
+        assert cfg["z_chunk"] == shapes[(N, nf)]["z_chunk"] == lat.pass_config()["z_chunk"]
+        # the twin replays the member's history: state and b0 on the starting shape, then the tuned one
+        twin = T.Lattice(N, 0.5, nf, dtype, ex, 1.0, 1.0, 1.0)
+        twin.set_pass_config(**before[(N, nf)])
+        twin.set_potential(1.0, q, (0.0, 0.1, 0.0))
+        fill(twin, N, nf, seed, dtype)
+        twin.set_pass_config(**cfg)
+        twin.step(steps, dt, "verlet")
+        phi, pi = lat.get_all()
+        tphi, tpi = twin.get_all()
+        E, tE = lat.energies(), twin.energies()
+        assert np.array_equal(phi, tphi) and np.array_equal(pi, tpi), (N, nf)
+        assert np.array_equal(E.vector(), tE.vector()) and E.a == tE.a and E.b == tE.b
+        twin.close()
+        if dtype == "f64":
+            p = o.Params(N=N, nf=nf, kIR=0.5, expanding=ex, alpha=1.0, lam=1.0, q=q, m2=(0.0, 0.1, 0.0))
+            b0 = math.sqrt(float(np.sum(o.energies(p, phi0, pi0, 1.0))) / 3.0) if ex else 0.0
+            ophi, opi, oa, ob = o.run(p, phi0, pi0, 1.0, b0, dt, steps, o.VERLET)
+            assert np.max(np.abs(phi - ophi)) / np.max(np.abs(ophi)) < 1e-12
+            assert np.max(np.abs(pi - opi)) / np.max(np.abs(opi)) < 1e-12
+            if ex:
+                assert abs(E.a - oa) / oa < 1e-12 and abs(E.b - ob) / ob < 1e-12
         lat.close()
