@@ -249,7 +249,10 @@ int tl_commit_state(tl_lattice *lat);
  * every GPU loading the library holds until exit) with room for 16384 CTA
  * partial sums, enough for N <= 1024 in both precisions; larger lattices get
  * TL_EINVAL.  The first call on each device looks up the array's address
- * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, so make
+ * that call before any stream capture; a device reset (cudaDeviceReset, or a
+ * reset of the primary context) invalidates the kept address, and later calls
+ * on that device are then invalid.  All calls
  * share the array: calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.
  * Errors: TL_EINVAL, TL_ECUDA, TL_EUNSTABLE (non-finite energies). */

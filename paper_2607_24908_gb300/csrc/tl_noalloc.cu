@@ -19,11 +19,31 @@
 namespace {
 
 // Scratch capacity: the scalar block plus kMaxSlotBlocks CTA slots of
-// kMaxQ doubles.  16384 slots cover every lattice up to 1024^3 in both
-// precisions with the default launch geometry.
+// kMaxQ doubles.
 constexpr size_t kMaxSlotBlocks = 16384;
 constexpr size_t kScalarsBytes = (sizeof(tl::Scalars) + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kScalarsBytes + kMaxSlotBlocks * tl::kMaxQ * sizeof(double);
+
+// The pass shape of this entry point, fixed here so that its CTA count does
+// not follow the library's default shapes: the register-streaming kernel with
+// 256-thread CTAs and 32 threads along x (tiles of 32 W x 8 sites, W = 4 FP32
+// or 2 FP64 sites per thread), z-chunks of 256 planes from N = 512 up and the
+// automatic z-chunk below (at most 128 planes, so at most
+// ceil(N/(32 W)) ceil(N/8) ceil(N/128) <= 2048 CTAs for N < 512).
+constexpr int kZChunkLarge = 256;
+
+tl::PassTuning noalloc_tuning(int N)
+{
+    return tl::PassTuning{tl::kVariantLdg, 7, 0, N >= 512 ? kZChunkLarge : 0, 0, 256, 32};
+}
+
+constexpr size_t large_blocks(int N, int W)
+{
+    return (size_t)((N / W + 31) / 32) * (size_t)((N + 7) / 8) * (size_t)((N + kZChunkLarge - 1) / kZChunkLarge);
+}
+// every lattice up to 1024^3 fits the scratch in both precisions (4096 and 8192 CTAs)
+static_assert(large_blocks(1024, 4) <= kMaxSlotBlocks && large_blocks(1024, 2) <= kMaxSlotBlocks,
+              "the static scratch must hold the CTA slots of a 1024^3 lattice");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -73,10 +93,8 @@ extern "C" int tl_energies_noalloc(int N, double kIR, int n_fields, tl_dtype dty
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(TL_ECUDA, "device query: ", cudaGetErrorString(e));
-    tl::PassTuning tune = tl::default_tuning(N, n_fields, dtype == TL_F32 ? 4 : 8);
-    tune.variant = tl::kVariantLdg;  // dense caller arrays have no ghost layer for tiled copies
-    tune.prefetch = 0;
-    const tl::PassGeom g = tl::pass_geometry(N, dtype == TL_F32 ? 4 : 8, sms, n_fields, tune);
+    // dense caller arrays have no ghost layer for tiled copies: the streaming kernel
+    const tl::PassGeom g = tl::pass_geometry(N, dtype == TL_F32 ? 4 : 8, sms, n_fields, noalloc_tuning(N));
     if (g.nblocks > kMaxSlotBlocks)
         return fail(TL_EINVAL, "lattice needs more reduction slots than the static scratch holds (max 16384 CTAs)");
 
