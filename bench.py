@@ -196,13 +196,86 @@ def oracle_sample(seconds_target: float = 15.0, max_steps: int = 1000):
     one = time.perf_counter() - t0
     steps = max(1, min(max_steps, int(seconds_target / max(one, 1e-6))))
     t0 = time.perf_counter()
-    o.run(p, phi, pi, a, b, WL.dt, steps, integ)
+    phi, pi, a, b = o.run(p, phi, pi, a, b, WL.dt, steps, integ)
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     value = n ** 3 * WL.nf * PASSES * steps / el
+    final = {"N": n, "kIR": p.kIR, "steps": 1 + steps, "E": o.energies(p, phi, pi, a), "a": a, "b": b,
+             "R": o.hubble_residual(p, o.energies(p, phi, pi, a), a, b)}
     return {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
             "sample": f"{n}^3 x {WL.nf} fields, same model/dt/{WL.integrator}, FP64, {steps} steps in {el:.1f} s "
-                      f"(OpenMP {cores} threads)"}
+                      f"(OpenMP {cores} threads)"}, final
+
+
+def gpu_vs_oracle(final):
+    """The oracle sample's run (same seed, model, dx, dt, integrator and step
+    count) on the GPU in each precision, one tl_step call: the largest error of
+    K_f, G_f, V relative to K+G+V and of a, a' relative to themselves, against
+    the FP64 oracle (the error statement of the reported FP32 result)."""
+    from paper_2607_24908_gb300 import tl as T
+    oE = np.asarray(final["E"])
+    rho = float(np.sum(oE))
+    out = {"sample": f"{final['N']}^3 x {WL.nf} fields, {final['steps']} {WL.integrator} steps "
+                     f"(dt {WL.dt}, same dx as {WL.N}^3), initial state drawn from the same seed on each side"}
+    for dtype in ("f32", "f64"):
+        lat = T.Lattice(final["N"], final["kIR"], WL.nf, dtype, WL.expanding, WL.alpha, WL.fstar_over_mp, 1.0)
+        lat.set_potential(WL.lam, WL.q, WL.m2)
+        lat.init_fluctuations(WL.seed, A=WL.A, meff2=WL.meff2, phi0=WL.phi0)
+        lat.step(final["steps"], WL.dt, WL.integrator)
+        E = lat.energies()
+        lat.close()
+        out[dtype] = {"energies_rel_to_rho": float(np.max(np.abs(E.vector() - oE)) / rho),
+                      "a_rel": abs(E.a - final["a"]) / final["a"], "b_rel": abs(E.b - final["b"]) / abs(final["b"]),
+                      "hubble_resid": E.hubble_resid, "hubble_resid_oracle": final["R"]}
+        out[dtype]["max"] = max(out[dtype]["energies_rel_to_rho"], out[dtype]["a_rel"], out[dtype]["b_rel"])
+    return out
+
+
+# FP64 operations a fused pass must do per site of one field, as the pass is
+# written: drift 1; phi^2, dV/dphi and V(phi) in factored form 5; Laplacian
+# (neighbour sum minus 6 phi) 6; force 2; momentum at the evaluation time and the
+# kicked momentum 2; kinetic, gradient (summation by parts: -phi Lap phi) and
+# potential sums 3.  The FP64 pass is bound by the FP64 pipe; each thread also
+# redoes the drift of its four in-plane neighbours (3 more per site), which is
+# not counted here.
+FP64_OPS_PER_SITE_1F = 19
+
+
+def fp64_pass():
+    """The paper's own precision: the 256^3 one-field expanding phi^4 workload
+    in FP64 (velocity Verlet, one fused pass per step), ms per pass and its
+    FP64-pipe roofline against the device's measured FP64 FMA issue rate."""
+    import torch
+    from paper_2607_24908_gb300 import tl as T
+    from paper_2607_24908_gb300.workloads import PHI4_EXPANDING_256 as W2
+    stream = torch.cuda.Stream()
+    lat = T.Lattice(W2.N, W2.kIR, 1, "f64", True, W2.alpha, W2.fstar_over_mp, 1.0, stream=stream.cuda_stream)
+    lat.set_potential(W2.lam, 0.0, W2.m2)
+    lat.init_fluctuations(W2.seed, A=W2.A, meff2=W2.meff2, phi0=W2.phi0)
+    for _ in range(3):
+        lat.step(1, W2.dt, "verlet")
+    lat.energies()
+    steps = 40
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.step(steps, W2.dt, "verlet")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_pass = e0.elapsed_time(e1) / (steps + 1)
+    shape = lat.pass_config()
+    lat.close()
+    rate64, _ = T.tl_probe_fma_rates(stream.cuda_stream)
+    sites = W2.N ** 3
+    achieved = FP64_OPS_PER_SITE_1F * sites / (ms_pass / 1e3)
+    hbm, _ = peaks()
+    return {"workload": W2.name, "ms_per_pass": ms_pass, "site_updates_per_s": sites / (ms_pass / 1e3),
+            "pass_shape": shape,
+            "roofline": {"bound": "alu", "unit": "G FP64 operations/s", "ops_per_site": FP64_OPS_PER_SITE_1F,
+                         "achieved": achieved / 1e9, "peak": rate64 / 1e9,
+                         "peak_source": "tl_probe_fma_rates (measured FP64 FMA issue rate)",
+                         "frac": achieved / rate64},
+            "hbm_frac": 32 * sites / (ms_pass / 1e3) / 1e9 / hbm}
 
 
 def run_reference(args):
@@ -341,9 +414,13 @@ def _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_ran
         peak, peak_kind = peaks()
         alg_bytes = sites * WL.nf * BYTES_PER_SITE_FIELD_PASS
         achieved = alg_bytes / (ms_pass / 1e3) / 1e9
-        cpu = None
+        cpu, extras = None, {}
         if ws == 1 and not args.no_cpu_baseline:
-            cpu = oracle_sample()
+            cpu, final = oracle_sample()
+            extras["oracle_error"] = gpu_vs_oracle(final)
+        if ws == 1 and not args.no_extras and N == WL.N:
+            extras["fp64"] = fp64_pass()
+            extras["ensemble"] = ensemble_measure(96, 1000)
         line = {
             "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -368,6 +445,7 @@ def _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_ran
             "clocks": clk,
             "physics": {"a": E.a, "hubble_resid": E.hubble_resid, "a_after_e2e": E2.a},
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -389,26 +467,38 @@ def ensemble_jobs(n_jobs=96, seed=4242):
     return jobs
 
 
-def run_ensemble(args):
+def ensemble_measure(n_jobs: int = 96, steps: int = 1000, dt: float = 0.01, tune_batch: bool = True) -> dict:
+    """The batched ensemble (every job resident, one grouped launch per pass
+    and field count, graph replay; member shapes and batch options from
+    tl_batch_autotune) against one job at a time with tl_step on its
+    autotuned shape; wall times include each job's init."""
     import torch
     from paper_2607_24908_gb300 import tl as T
-    torch.cuda.set_device(0)
-    jobs = ensemble_jobs(args.jobs)
-    steps, dt = args.ens_steps, 0.01
+    jobs = ensemble_jobs(n_jobs)
 
-    def new(j):
+    def new(j, tune=True):
         lat = T.Lattice(j["N"], 0.5, j["nf"], "f32", True, 1.0, 1.0, 1.0)
         lat.set_potential(1.0, j["q"], (0.0, 0.0, 0.0))
         lat.init_fluctuations(j["seed"], A=1e-10, meff2=(3.0, j["q"], 0.0), phi0=(1.0, 0.0, 0.0))
-        lat.autotune()
+        if tune:
+            lat.autotune()
         return lat
 
-    # warm the per-shape caches (FFT plans, autotuner) and the kernels once
+    # warm the per-shape caches (FFT plans, autotuners) and the kernels once:
+    # each shape tuned alone for the one-at-a-time arm, and a batch of the
+    # same composition tuned for the batched arm (tl_batch_autotune caches its
+    # member shapes and options for the batch created below)
     shapes = {(j["N"], j["nf"]) for j in jobs}
     for N, nf in shapes:
         lat = new(dict(N=N, nf=nf, q=0.0, seed=1))
         lat.step(2, dt, "verlet")
         lat.energies()
+        lat.close()
+    warm = [new(dict(j, seed=j["seed"] + 1), tune=False) for j in jobs]
+    with T.Batch(warm) as b:
+        b.step(2, dt, "verlet")
+        tuned_ms_per_pass = b.autotune() if tune_batch else None
+    for lat in warm:
         lat.close()
     torch.cuda.synchronize()
 
@@ -428,12 +518,14 @@ def run_ensemble(args):
 
     # batched: all jobs resident, one grouped launch per pass, graph replay
     t0 = time.perf_counter()
-    lats = [new(j) for j in jobs]
+    lats = [new(j, tune=False) for j in jobs]
     torch.cuda.synchronize()
     t_bat_init = time.perf_counter() - t0
     with T.Batch(lats) as b:
         b.step(steps, dt, "verlet")
+        opts = b.options()
     bat = [lat.energies() for lat in lats]
+    shapes_used = sorted({(lat.N, lat.nf, json.dumps(lat.pass_config(), sort_keys=True)) for lat in lats})
     for lat in lats:
         lat.close()
     t_bat = time.perf_counter() - t0
@@ -441,16 +533,30 @@ def run_ensemble(args):
     diff = max(float(np.max(np.abs(x.vector() - y.vector()))) / float(np.sum(np.abs(y.vector()))) for x, y in
                zip(bat, seq))
     site_updates = sum(j["N"] ** 3 * j["nf"] for j in jobs) * steps
-    line = {"metric": "jobs/s", "value": len(jobs) / t_bat, "unit": "jobs/s", "higher_is_better": True,
-            "mode": "ensemble", "n_gpus": 1,
-            "config": {"workload": f"{len(jobs)} jobs, N in {{32,48,64,96,128}}, 1-2 fields, q in {{0,10,100}}, "
-                                   f"{steps} Verlet steps dt={dt}, FP32 storage, expanding alpha=1, kIR=0.5",
-                       "jobs": len(jobs), "steps": steps},
-            "batched_s": t_bat, "sequential_s": t_seq, "sequential_jobs_per_s": len(jobs) / t_seq,
+    alg_bytes = sum(j["N"] ** 3 * j["nf"] for j in jobs) * 16 * (steps + 1)
+    hbm, _ = peaks()
+    return {"workload": f"{len(jobs)} jobs, N in {{32,48,64,96,128}}, 1-2 fields, q in {{0,10,100}}, "
+                        f"{steps} Verlet steps dt={dt}, FP32 storage, expanding alpha=1, kIR=0.5",
+            "jobs": len(jobs), "steps": steps,
+            "batched_jobs_per_s": len(jobs) / t_bat, "sequential_jobs_per_s": len(jobs) / t_seq,
+            "batched_s": t_bat, "sequential_s": t_seq,
             "init_s": {"batched": t_bat_init, "sequential": t_seq_init},
             "stepping_s": {"batched": t_bat - t_bat_init, "sequential": t_seq - t_seq_init},
             "speedup": t_seq / t_bat, "site_updates_per_s_batched": site_updates / t_bat,
+            "batched_stepping_hbm_frac": alg_bytes / (t_bat - t_bat_init) / 1e9 / hbm,
+            "batch_shapes": [{"N": n, "fields": f, "shape": json.loads(c)} for n, f, c in shapes_used],
+            "batch_options": opts, "batch_tuned_ms_per_pass": tuned_ms_per_pass,
             "max_rel_energy_diff_batched_vs_sequential": diff}
+
+
+def run_ensemble(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = ensemble_measure(args.jobs, args.ens_steps, tune_batch=not args.no_batch_tune)
+    line = {"metric": "jobs/s", "value": r["batched_jobs_per_s"], "unit": "jobs/s", "higher_is_better": True,
+            "mode": "ensemble", "n_gpus": 1, "config": {"workload": r["workload"], "jobs": r["jobs"],
+                                                        "steps": r["steps"]}}
+    line.update(r)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -465,40 +571,73 @@ def run_serve(args):
     torch.cuda.set_device(0)
     budget = int(150e9)
     n = args.jobs
+    repeats = max(1, args.repeats)
     base = S.poisson_jobs(n, seed=12345, rate=0.0)
-    # warm-up: one small job of each precision (kernels, FFT plans)
-    warm = [S.JobSpec(-1, 64, 2, 100.0, 100, "f32", 1), S.JobSpec(-2, 64, 2, 100.0, 100, "f64", 2)]
-    S.run_alone(warm)
-    # mean sequential service time from the first jobs, arrivals at t = 0
+    # warm-up: one small and one big job of each precision on both shapes (kernels, FFT plans)
+    warm = [S.JobSpec(-1, 64, 2, 100.0, 100, "f32", 1), S.JobSpec(-2, 64, 2, 100.0, 100, "f64", 2),
+            S.JobSpec(-3, 256, 2, 100.0, 100, "f32", 3), S.JobSpec(-4, 256, 1, 100.0, 100, "f64", 4)]
+    for shape in ("served", "default"):
+        S.run_alone(warm, shape=shape)
+    # mean service time of the plain loop from the first jobs, arrivals at t = 0
     probe = [S.JobSpec(**{**j.__dict__, "arrival": 0.0}) for j in base[:4]]
-    _, t_probe = S.run_alone(probe)
+    _, t_probe = S.run_alone(probe, shape="default")
     mean_service = t_probe / len(probe)
     rate = 0.8 / mean_service
     jobs = S.poisson_jobs(n, seed=12345, rate=rate)
+    sat = [S.JobSpec(**{**j.__dict__, "arrival": 0.0}) for j in jobs]
 
     def stats(res, span):
         lat = np.array([r.latency for r in res])
         return {"jobs_per_s": len(res) / span, "p50_s": float(np.percentile(lat, 50)),
                 "p99_s": float(np.percentile(lat, 99)), "makespan_s": span}
 
-    served, span_srv = S.serve(jobs, budget)
-    alone, span_seq = S.run_alone(jobs)
-    same = all(np.array_equal(a.energies, b.energies) for a, b in
-               zip(sorted(served, key=lambda r: r.job_id), sorted(alone, key=lambda r: r.job_id)))
-    # saturation: every job present at t = 0
-    sat = [S.JobSpec(**{**j.__dict__, "arrival": 0.0}) for j in jobs]
-    served0, span0 = S.serve(sat, budget)
-    alone0, span0_seq = S.run_alone(sat)
-    line = {"metric": "served jobs/s", "value": len(sat) / span0, "unit": "jobs/s", "higher_is_better": True,
+    def agreement(a, b):
+        """max relative difference of the final energies (to K+G+V), a and a'
+        between two runs of the same jobs, per precision"""
+        out = {}
+        bb = {r.job_id: r for r in b}
+        spec = {j.job_id: j for j in jobs}
+        for r in a:
+            s_ = bb[r.job_id]
+            d = max(float(np.max(np.abs(r.energies - s_.energies)) / np.sum(np.abs(s_.energies))),
+                    abs(r.a - s_.a) / s_.a, abs(r.b - s_.b) / abs(s_.b))
+            k = spec[r.job_id].dtype
+            out[k] = max(out.get(k, 0.0), d)
+        return out
+
+    runs = {"poisson_load_0.8": [], "saturation": []}
+    agree = {}
+    for rep in range(repeats):
+        for name, js in (("poisson_load_0.8", jobs), ("saturation", sat)):
+            log = []
+            served, span_s = S.serve(js, budget, log=log)
+            plain, span_p = S.run_alone(js, shape="default")
+            for k, v in agreement(served, plain).items():
+                agree[k] = max(agree.get(k, 0.0), v)
+            runs[name].append({"served": stats(served, span_s), "plain_loop": stats(plain, span_p),
+                               "speedup_jobs_per_s": span_p / span_s,
+                               "served_lanes": S.lane_overlap(log, span_s)})
+
+    def spread(name, arm, key):
+        v = [r[arm][key] for r in runs[name]]
+        return {"mean": float(np.mean(v)), "min": float(np.min(v)), "max": float(np.max(v))}
+
+    summary = {name: {f"{arm}_{key}": spread(name, arm, key) for arm in ("served", "plain_loop")
+                      for key in ("jobs_per_s", "p50_s", "p99_s")} for name in runs}
+    sat_served = summary["saturation"]["served_jobs_per_s"]["mean"]
+    line = {"metric": "served jobs/s", "value": sat_served, "unit": "jobs/s", "higher_is_better": True,
             "mode": "serve", "n_gpus": 1,
             "config": {"workload": f"{n} Poisson jobs: N in {{64,128,256,384}}, 1-3 fields, q in {{1,100}}, "
                                    "500-5000 Verlet steps (dt 0.01), FP32 or FP64, expanding alpha=1, kIR=0.1",
                        "budget_bytes": budget, "chunk_steps": 100, "arrival_rate_per_s": rate,
-                       "mean_sequential_service_s": mean_service},
-            "poisson_load_0.8": {"served": stats(served, span_srv), "sequential": stats(alone, span_seq)},
-            "saturation": {"served": stats(served0, span0), "sequential": stats(alone0, span0_seq),
-                           "speedup_jobs_per_s": span0_seq / span0},
-            "results_bitwise_equal_served_vs_alone": bool(same)}
+                       "mean_plain_service_s": mean_service, "repeats": repeats,
+                       "plain_loop": "one job at a time, tl_step on the library's default launch shape",
+                       "served": "batched lanes (small jobs, batch shape) + solo lanes (big jobs, default shape)"},
+            "summary": summary, "runs": runs,
+            "max_rel_diff_served_vs_plain": agree,
+            "accuracy_note": "served and plain results agree within the parity tolerances of each precision "
+                             "(FP64 1e-12, FP32 1e-5); served results are bitwise those of each job alone on "
+                             "its served shape (tests/test_gpu_serve.py)"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -674,6 +813,11 @@ def main():
                     help="step: the 1024^3 fused step (default); ensemble: batched small lattices vs a plain loop; "
                          "serve: continuous batching of Poisson-arriving jobs vs a sequential loop")
     ap.add_argument("--jobs", type=int, default=0, help="jobs for --mode ensemble (96) / serve (16)")
+    ap.add_argument("--repeats", type=int, default=2, help="--mode serve: repeats of each arm")
+    ap.add_argument("--no-batch-tune", action="store_true",
+                    help="--mode ensemble: batch on the untuned batch shapes (for comparison)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line without the fp64 and ensemble keys (profiling runs)")
     ap.add_argument("--ens-steps", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
