@@ -532,6 +532,9 @@ def ensemble_measure(n_jobs: int = 96, steps: int = 1000, dt: float = 0.01, tune
 
     diff = max(float(np.max(np.abs(x.vector() - y.vector()))) / float(np.sum(np.abs(y.vector()))) for x, y in
                zip(bat, seq))
+    # the batched FP32 results against the FP64 oracle, on the cheapest jobs
+    err = oracle_job_errors([(j["N"], j["nf"], j["q"], j["seed"], 0.5, dt, steps, "verlet", E.vector(), E.a, E.b)
+                             for j, E in zip(jobs, bat)])
     site_updates = sum(j["N"] ** 3 * j["nf"] for j in jobs) * steps
     alg_bytes = sum(j["N"] ** 3 * j["nf"] for j in jobs) * 16 * (steps + 1)
     hbm, _ = peaks()
@@ -546,7 +549,35 @@ def ensemble_measure(n_jobs: int = 96, steps: int = 1000, dt: float = 0.01, tune
             "batched_stepping_hbm_frac": alg_bytes / (t_bat - t_bat_init) / 1e9 / hbm,
             "batch_shapes": [{"N": n, "fields": f, "shape": json.loads(c)} for n, f, c in shapes_used],
             "batch_options": opts, "batch_tuned_ms_per_pass": tuned_ms_per_pass,
-            "max_rel_energy_diff_batched_vs_sequential": diff}
+            "max_rel_energy_diff_batched_vs_sequential": diff,
+            "oracle_error_fp32_batched": err}
+
+
+def oracle_job_errors(cases, max_cases: int = 4):
+    """Error of GPU results against the FP64 oracle on a bounded sample of
+    jobs: each case (N, fields, q, seed, kIR, dt, steps, integrator, GPU
+    energies [K.., G.., V], a, a') is rerun by the oracle from the same seed
+    (Philox drawn from its definition on the CPU side), cheapest first.
+    Returns the largest errors (energies relative to K+G+V; a, a' relative)."""
+    import oracle as o
+    integ = {"leapfrog": o.LEAPFROG, "verlet": o.VERLET, "yoshida4": o.YOSHIDA4}
+    cases = sorted(cases, key=lambda c: c[0] ** 3 * c[1] * c[6])[:max_cases]
+    worst = {"energies_rel_to_rho": 0.0, "a_rel": 0.0, "b_rel": 0.0}
+    sample = []
+    for N, nf, q, seed, kIR, dt, steps, integrator, E, a, b in cases:
+        p = o.Params(N=N, nf=nf, kIR=kIR, expanding=True, alpha=1.0, lam=1.0, q=q)
+        spec = o.InitSpec(A=1e-10, meff2=(3.0,) + (q,) * (nf - 1), phi0=(1.0, 0.0, 0.0))
+        phi, pi, a0, b0 = o.init_fluctuations(p, seed, spec)
+        ophi, opi, oa, ob = o.run(p, phi, pi, a0, b0, dt, steps, integ[integrator])
+        oE = o.energies(p, ophi, opi, oa)
+        worst["energies_rel_to_rho"] = max(worst["energies_rel_to_rho"],
+                                           float(np.max(np.abs(np.asarray(E) - oE)) / np.sum(oE)))
+        worst["a_rel"] = max(worst["a_rel"], abs(a - oa) / oa)
+        worst["b_rel"] = max(worst["b_rel"], abs(b - ob) / abs(ob))
+        sample.append(f"{N}^3x{nf} {steps} {integrator}")
+    worst["max"] = max(worst["energies_rel_to_rho"], worst["a_rel"], worst["b_rel"])
+    worst["sample"] = ", ".join(sample)
+    return worst
 
 
 def run_ensemble(args):
@@ -607,10 +638,12 @@ def run_serve(args):
 
     runs = {"poisson_load_0.8": [], "saturation": []}
     agree = {}
+    served_last = None
     for rep in range(repeats):
         for name, js in (("poisson_load_0.8", jobs), ("saturation", sat)):
             log = []
             served, span_s = S.serve(js, budget, log=log)
+            served_last = served
             plain, span_p = S.run_alone(js, shape="default")
             for k, v in agreement(served, plain).items():
                 agree[k] = max(agree.get(k, 0.0), v)
@@ -625,6 +658,14 @@ def run_serve(args):
     summary = {name: {f"{arm}_{key}": spread(name, arm, key) for arm in ("served", "plain_loop")
                       for key in ("jobs_per_s", "p50_s", "p99_s")} for name in runs}
     sat_served = summary["saturation"]["served_jobs_per_s"]["mean"]
+    spec = {j.job_id: j for j in jobs}
+    oerr = {}
+    for dt_ in ("f32", "f64"):
+        cases = [(spec[r.job_id].N, spec[r.job_id].n_fields, spec[r.job_id].q, spec[r.job_id].seed,
+                  spec[r.job_id].kIR, spec[r.job_id].dt, spec[r.job_id].steps, spec[r.job_id].integrator,
+                  r.energies, r.a, r.b) for r in served_last if spec[r.job_id].dtype == dt_]
+        if cases:
+            oerr[dt_] = oracle_job_errors(cases, max_cases=1)
     line = {"metric": "served jobs/s", "value": sat_served, "unit": "jobs/s", "higher_is_better": True,
             "mode": "serve", "n_gpus": 1,
             "config": {"workload": f"{n} Poisson jobs: N in {{64,128,256,384}}, 1-3 fields, q in {{1,100}}, "
@@ -635,6 +676,7 @@ def run_serve(args):
                        "served": "batched lanes (small jobs, batch shape) + solo lanes (big jobs, default shape)"},
             "summary": summary, "runs": runs,
             "max_rel_diff_served_vs_plain": agree,
+            "oracle_error_served": oerr,
             "accuracy_note": "served and plain results agree within the parity tolerances of each precision "
                              "(FP64 1e-12, FP32 1e-5); served results are bitwise those of each job alone on "
                              "its served shape (tests/test_gpu_serve.py)"}
