@@ -382,6 +382,8 @@ int tl::set_geometry(tl_lattice *L, const PassTuning &t)
     return TL_OK;
 }
 
+int tl::lattice_tma_maps(tl_lattice *L) { return ensure_tma_maps(L); }
+
 void tl::invalidate_launches(tl_lattice *L)
 {
     for (auto &g : L->graphs)

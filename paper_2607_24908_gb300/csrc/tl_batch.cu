@@ -48,19 +48,27 @@ struct BatchOpts {
 }  // namespace
 
 struct tl_batch {
+    // Lattices of one field count and one kernel variant, advanced by one
+    // grouped launch per pass.
     struct Group {
         int nf = 0;
+        int variant = tl::kVariantLdg;        // the members' kernel: register streaming or TMA
         std::vector<int> idx;                 // lattices of this group
         BatchJob *d_jobs[2] = {nullptr, nullptr}; // even / odd passes of a call
         unsigned *d_first = nullptr;          // first item of each job
+        tl::TmaMaps *d_maps = nullptr;        // TMA: tensor maps of each member, both buffer parities
         unsigned total = 0;                   // items (CTA tiles) over all jobs
         double work = 0.0;                    // sites x fields of its lattices
-        int grid = 0;                         // persistent CTAs
+        int grid = 0;                         // CTAs (persistent for streaming, one per item for TMA)
+        int stages = 0;                       // TMA: ring stages
+        size_t smem = 0;                      // TMA: dynamic shared memory per CTA
         cudaStream_t branch = nullptr;        // capture stream of its graph branch (group 0: the capture stream)
         cudaEvent_t done = nullptr;           // end of its branch
     };
     std::vector<tl_lattice *> lats;
     std::vector<Group> groups;
+    std::vector<cudaStream_t> branch_pool;    // branch streams and join events, reused by group rebuilds
+    std::vector<cudaEvent_t> event_pool;
     int dtype = 0;
     int sm_count = 0;
     BatchOpts opts;
@@ -82,7 +90,7 @@ int upload_jobs(tl_batch *B)
     for (auto &g : B->groups) {
         for (int parity = 0; parity < 2; ++parity) {
             B->h_jobs.clear();
-            for (int i : g.idx) {
+            for (const int &i : g.idx) {
                 tl_lattice *L = B->lats[i];
                 const int in = L->cur ^ parity;
                 BatchJob j{};
@@ -101,6 +109,8 @@ int upload_jobs(tl_batch *B)
                 j.gx = (int)L->geom.grid.x;
                 j.gy = (int)L->geom.grid.y;
                 j.nblocks = L->geom.nblocks;
+                j.lpad = L->geom.lpad;
+                j.maps = g.d_maps ? g.d_maps + 2 * (&i - g.idx.data()) + in : nullptr;
                 B->h_jobs.push_back(j);
             }
             TB_CK(cudaMemcpyAsync(g.d_jobs[parity], B->h_jobs.data(), B->h_jobs.size() * sizeof(BatchJob),
@@ -128,18 +138,101 @@ int refresh_groups(tl_batch *B)
             first.push_back(g.total);
             g.total += B->lats[i]->geom.nblocks;
         }
-        long want = full;
-        if (B->opts.share && B->groups.size() > 1 && all > 0.0) {
-            want = (long)(full * (g.work / all) + 0.5);
-            if (want < B->sm_count / 4) want = B->sm_count / 4 > 0 ? B->sm_count / 4 : 1;
+        if (g.variant == tl::kVariantTma) {
+            // one CTA per item; the ring as deep as two CTAs per SM allow for the
+            // largest box among the members; each member's tensor maps (both
+            // buffer parities) copied to device memory for the kernel to read
+            int wmax = 0, hmax = 0;
+            std::vector<tl::TmaMaps> maps;
+            for (int i : g.idx) {
+                tl_lattice *L = B->lats[i];
+                const int W = (int)(16 / L->esz);
+                wmax = std::max(wmax, L->geom.txt * W + 2 * W);
+                hmax = std::max(hmax, L->geom.ty + 2);
+                int rc = tl::lattice_tma_maps(L);
+                if (rc) return rc;
+                maps.push_back(L->maps[0]);
+                maps.push_back(L->maps[1]);
+            }
+            const int esz = B->dtype == TL_F64 ? 8 : 4;
+            int S = 8;
+            while (S > 3 && tl::tma_group_smem(esz, g.nf, S, wmax, hmax) > 113u * 1024u) --S;
+            g.stages = S;
+            g.smem = tl::tma_group_smem(esz, g.nf, S, wmax, hmax);
+            g.grid = (int)g.total;
+            TB_CK(cudaMemcpyAsync(g.d_maps, maps.data(), maps.size() * sizeof(tl::TmaMaps), cudaMemcpyHostToDevice,
+                                  B->stream));
+        } else {
+            long want = full;
+            if (B->opts.share && B->groups.size() > 1 && all > 0.0) {
+                want = (long)(full * (g.work / all) + 0.5);
+                if (want < B->sm_count / 4) want = B->sm_count / 4 > 0 ? B->sm_count / 4 : 1;
+            }
+            g.grid = (int)((long)g.total < want ? (long)g.total : want);
+            if (g.grid < 1) g.grid = 1;
         }
-        g.grid = (int)((long)g.total < want ? (long)g.total : want);
-        if (g.grid < 1) g.grid = 1;
         TB_CK(cudaMemcpyAsync(g.d_first, first.data(), first.size() * sizeof(unsigned), cudaMemcpyHostToDevice,
                               B->stream));
-        TB_CK(cudaStreamSynchronize(B->stream));  // `first` is reused for the next group
+        TB_CK(cudaStreamSynchronize(B->stream));  // `first` and `maps` are reused for the next group
     }
     return TL_OK;
+}
+
+void free_groups(tl_batch *B)
+{
+    for (auto &g : B->groups) {
+        cudaFree(g.d_jobs[0]);
+        cudaFree(g.d_jobs[1]);
+        cudaFree(g.d_first);
+        cudaFree(g.d_maps);
+    }
+    B->groups.clear();
+}
+
+// Partition the members into groups by field count and kernel variant (the
+// variant each member's launch shape names) and allocate their descriptors;
+// branch streams and join events come from the batch's pools.
+int build_groups(tl_batch *B)
+{
+    free_groups(B);
+    const int n = (int)B->lats.size();
+    for (int nf = 1; nf <= TL_MAX_FIELDS; ++nf)
+        for (int variant : {tl::kVariantLdg, tl::kVariantTma}) {
+            tl_batch::Group g;
+            g.nf = nf;
+            g.variant = variant;
+            for (int i = 0; i < n; ++i)
+                if (B->lats[i]->nf == nf && B->lats[i]->tuning.variant == variant) {
+                    g.idx.push_back(i);
+                    g.work += (double)B->lats[i]->N * B->lats[i]->N * B->lats[i]->N * nf;
+                }
+            if (g.idx.empty()) continue;
+            B->groups.push_back(g);
+        }
+    cudaError_t e = cudaSuccess;
+    for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+        auto &g = B->groups[gi];
+        const size_t jb = g.idx.size() * sizeof(BatchJob);
+        if ((e = cudaMalloc(&g.d_jobs[0], jb)) != cudaSuccess || (e = cudaMalloc(&g.d_jobs[1], jb)) != cudaSuccess ||
+            (e = cudaMalloc(&g.d_first, g.idx.size() * sizeof(unsigned))) != cudaSuccess ||
+            (g.variant == tl::kVariantTma &&
+             (e = cudaMalloc(&g.d_maps, 2 * g.idx.size() * sizeof(tl::TmaMaps))) != cudaSuccess))
+            return tl::fail(TL_ENOMEM, "batch descriptors: %s", cudaGetErrorString(e));
+        while (B->branch_pool.size() <= gi) {
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev = nullptr;
+            if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+                if (st) cudaStreamDestroy(st);
+                return tl::fail(TL_ECUDA, "stream/event creation: %s", cudaGetErrorString(e));
+            }
+            B->branch_pool.push_back(st);
+            B->event_pool.push_back(ev);
+        }
+        g.branch = B->branch_pool[gi];
+        g.done = B->event_pool[gi];
+    }
+    return refresh_groups(B);
 }
 
 // Capture `passes` over every group into an executable graph: each group's
@@ -164,8 +257,8 @@ int capture_passes(tl_batch *B, const std::vector<PassCoef> &passes, cudaGraph_t
             auto &g = B->groups[gi];
             cudaStream_t s = gi == 0 ? B->capture : g.branch;
             for (size_t p = 0; p < passes.size() && e == cudaSuccess; ++p)
-                e = tl::launch_group(B->dtype, g.nf, B->opts.prefetch, g.d_jobs[p & 1], g.d_first, (int)g.idx.size(),
-                                     g.total, passes[p], g.grid, s);
+                e = tl::launch_group(B->dtype, g.nf, g.variant, B->opts.prefetch, g.stages, g.smem, g.d_jobs[p & 1],
+                                     g.d_first, (int)g.idx.size(), g.total, passes[p], g.grid, s);
             if (gi > 0 && e == cudaSuccess) e = cudaEventRecord(g.done, s);
         }
         for (size_t gi = 1; gi < B->groups.size() && e == cudaSuccess; ++gi)
@@ -173,8 +266,8 @@ int capture_passes(tl_batch *B, const std::vector<PassCoef> &passes, cudaGraph_t
     } else {
         for (size_t p = 0; p < passes.size() && e == cudaSuccess; ++p)
             for (auto &g : B->groups) {
-                e = tl::launch_group(B->dtype, g.nf, B->opts.prefetch, g.d_jobs[p & 1], g.d_first,
-                                     (int)g.idx.size(), g.total, passes[p], g.grid, B->capture);
+                e = tl::launch_group(B->dtype, g.nf, g.variant, B->opts.prefetch, g.stages, g.smem, g.d_jobs[p & 1],
+                                     g.d_first, (int)g.idx.size(), g.total, passes[p], g.grid, B->capture);
                 if (e != cudaSuccess) break;
             }
     }
@@ -256,8 +349,9 @@ std::string composition(const std::vector<tl_lattice *> &lats)
 
 bool same_shape(const tl::PassTuning &a, const tl::PassTuning &b)
 {
-    return a.variant == b.variant && a.threads == b.threads && a.zc == b.zc && a.txt == b.txt &&
-           a.prefetch == b.prefetch;
+    if (a.variant != b.variant || a.zc != b.zc) return false;
+    if (a.variant == tl::kVariantTma) return a.cwarps == b.cwarps;
+    return a.threads == b.threads && a.txt == b.txt && a.prefetch == b.prefetch;
 }
 
 }  // namespace
@@ -276,7 +370,10 @@ int tl_batch_pass_config(int N, int n_fields, tl_dtype dtype, tl_pass_config *ou
                                                   cudaSuccess)
         sms = 0;
     const tl::PassTuning t = batch_tuning(N, n_fields, (int)dtype, sms);
-    *out = tl_pass_config{TL_PASS_STREAM, 0, 0, t.zc, t.txt, t.threads};
+    if (t.variant == tl::kVariantTma)
+        *out = tl_pass_config{TL_PASS_TMA, t.cwarps, 0, t.zc, 0, 0};
+    else
+        *out = tl_pass_config{TL_PASS_STREAM, 0, 0, t.zc, t.txt, t.threads};
     return TL_OK;
 }
 
@@ -316,7 +413,7 @@ int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_s
     for (int i = 0; i < n; ++i) {
         tl_lattice *L = lats[i];
         tl::PassTuning t = batch_tuning(L->N, L->nf, (int)L->dtype, L->sm_count);
-        t.prefetch = B->opts.prefetch;
+        if (t.variant == tl::kVariantLdg) t.prefetch = B->opts.prefetch;
         if (!same_shape(L->tuning, t)) {
             int rc = tl::set_geometry(L, t);
             if (rc) {
@@ -329,25 +426,7 @@ int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_s
     cudaError_t e = cudaStreamCreateWithFlags(&B->capture, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
     if (e != cudaSuccess) rc = tl::fail(TL_ECUDA, "stream/event creation: %s", cudaGetErrorString(e));
-    for (int nf = 1; nf <= TL_MAX_FIELDS && rc == TL_OK; ++nf) {
-        tl_batch::Group g;
-        g.nf = nf;
-        for (int i = 0; i < n; ++i)
-            if (lats[i]->nf == nf) {
-                g.idx.push_back(i);
-                g.work += (double)lats[i]->N * lats[i]->N * lats[i]->N * nf;
-            }
-        if (g.idx.empty()) continue;
-        const size_t jb = g.idx.size() * sizeof(BatchJob);
-        if ((e = cudaMalloc(&g.d_jobs[0], jb)) != cudaSuccess || (e = cudaMalloc(&g.d_jobs[1], jb)) != cudaSuccess ||
-            (e = cudaMalloc(&g.d_first, g.idx.size() * sizeof(unsigned))) != cudaSuccess)
-            rc = tl::fail(TL_ENOMEM, "batch descriptors: %s", cudaGetErrorString(e));
-        if (rc == TL_OK && ((e = cudaStreamCreateWithFlags(&g.branch, cudaStreamNonBlocking)) != cudaSuccess ||
-                            (e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming)) != cudaSuccess))
-            rc = tl::fail(TL_ECUDA, "stream/event creation: %s", cudaGetErrorString(e));
-        B->groups.push_back(g);
-    }
-    if (rc == TL_OK) rc = refresh_groups(B);
+    if (rc == TL_OK) rc = build_groups(B);
     if (rc) {
         tl_batch_destroy(B);
         return rc;
@@ -362,13 +441,9 @@ void tl_batch_destroy(tl_batch *B)
     if (!B) return;
     cudaStreamSynchronize(B->stream);
     drop_graph(B);
-    for (auto &g : B->groups) {
-        cudaFree(g.d_jobs[0]);
-        cudaFree(g.d_jobs[1]);
-        cudaFree(g.d_first);
-        if (g.branch) cudaStreamDestroy(g.branch);
-        if (g.done) cudaEventDestroy(g.done);
-    }
+    free_groups(B);
+    for (cudaStream_t st : B->branch_pool) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : B->event_pool) cudaEventDestroy(ev);
     if (B->fork) cudaEventDestroy(B->fork);
     if (B->capture) cudaStreamDestroy(B->capture);
     for (tl_lattice *L : B->lats)
@@ -450,8 +525,8 @@ const char *const kTuneFmt =
 // Batch entries (tl_batch_autotune): one member shape per (N, fields, dtype,
 // SMs), and the launch options of one batch composition.
 const char *const kBatchShapeFmt =
-    "{\"batch_shape\": {\"N\": %d, \"fields\": %d, \"dtype\": %d, \"sms\": %d, \"z_chunk\": %d, "
-    "\"tile_x\": %d, \"prefetch\": %d}}";
+    "{\"batch_shape\": {\"N\": %d, \"fields\": %d, \"dtype\": %d, \"sms\": %d, \"variant\": %d, "
+    "\"z_chunk\": %d, \"tile_x\": %d, \"prefetch\": %d}}";
 const char *const kBatchOptsFmt = "{\"batch_options\": {\"prefetch\": %d, \"split\": %d, \"share\": %d, "
                                   "\"composition\": \"%255[^\"]\"}}";
 
@@ -465,13 +540,16 @@ void load_tune_file()
     char line[512];
     while (fgets(line, sizeof line, f)) {
         {
-            int N, nf, dt, sms, zc, txt, pf, sp, sh;
+            int N, nf, dt, sms, var, zc, txt, pf, sp, sh;
             char comp[256];
-            if (sscanf(line, kBatchShapeFmt, &N, &nf, &dt, &sms, &zc, &txt, &pf) == 7) {
+            if (sscanf(line, kBatchShapeFmt, &N, &nf, &dt, &sms, &var, &zc, &txt, &pf) == 8) {
                 if (N >= 8 && nf >= 1 && nf <= TL_MAX_FIELDS && (dt == 0 || dt == 1) && zc >= 1 && zc <= N &&
+                    (var == tl::kVariantLdg || var == tl::kVariantTma) &&
                     (txt == 0 || txt == 8 || txt == 16 || txt == 32) && (pf == 0 || pf == 3)) {
                     std::lock_guard<std::mutex> lk(g_batch_mu);
-                    g_batch_shapes[ClassKey(N, nf, dt, sms)] = tl::PassTuning{tl::kVariantLdg, 7, 0, zc, pf, 256, txt};
+                    g_batch_shapes[ClassKey(N, nf, dt, sms)] =
+                        var == tl::kVariantTma ? tl::PassTuning{tl::kVariantTma, 7, 0, zc, 0, 256, 0}
+                                               : tl::PassTuning{tl::kVariantLdg, 7, 0, zc, pf, 256, txt};
                 }
                 continue;
             }
@@ -618,7 +696,7 @@ void append_tune_line(const char *line)
 // even number of them leaves each lattice's buffers where they started.
 int time_identity(tl_batch *B, cudaEvent_t e0, cudaEvent_t e1, double *ms_out)
 {
-    int rc = refresh_groups(B);
+    int rc = build_groups(B);  // members may have changed kernel variant
     if (rc) return rc;
     rc = upload_jobs(B);
     if (rc) return rc;
@@ -628,17 +706,23 @@ int time_identity(tl_batch *B, cudaEvent_t e0, cudaEvent_t e1, double *ms_out)
     cudaGraphExec_t exec = nullptr;
     rc = capture_passes(B, passes, &graph, &exec);
     if (rc) return rc;
-    cudaError_t e = cudaGraphLaunch(exec, B->stream);  // warm-up
-    if (e == cudaSuccess) e = cudaEventRecord(e0, B->stream);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaGraphLaunch(exec, B->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, B->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    // warm-up, then the best of three timings of two replays each (single
+    // timings of sub-millisecond replays vary by several percent)
+    cudaError_t e = cudaGraphLaunch(exec, B->stream);
+    float best = 0.f;
+    for (int t = 0; t < 3 && e == cudaSuccess; ++t) {
+        if (e == cudaSuccess) e = cudaEventRecord(e0, B->stream);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaGraphLaunch(exec, B->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, B->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (t == 0 || ms < best)) best = ms;
+    }
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return tl::fail(TL_ECUDA, "batch autotune: %s", cudaGetErrorString(e));
-    *ms_out = ms / (2.0 * reps);
+    *ms_out = best / (2.0 * reps);
     return TL_OK;
 }
 
@@ -703,6 +787,14 @@ extern "C" int tl_batch_autotune(tl_batch *B, double *best_ms_per_pass)
                 if (!dup) cands.push_back(t);
             }
         }
+        // the TMA pass (7 + 1 warps, one CTA per item of the grouped launch)
+        for (int zc : {8, 16, 32, 64, c.N}) {
+            if (zc > c.N) continue;
+            tl::PassTuning t{tl::kVariantTma, 7, 0, zc, 0, 256, 0};
+            bool dup = same_shape(t, c.t);
+            for (auto &o : cands) dup = dup || same_shape(o, t);
+            if (!dup) cands.push_back(t);
+        }
         for (const auto &t : cands) {
             const tl::PassTuning keep = c.t;
             if ((rc = apply(c, t))) break;
@@ -729,7 +821,7 @@ extern "C" int tl_batch_autotune(tl_batch *B, double *best_ms_per_pass)
                     if (B->groups.size() < 2 && (sp == 0 || sh == 1)) continue;  // no effect with one group
                     B->opts = o;
                     for (auto &c : cls) {
-                        c.t.prefetch = pf;
+                        if (c.t.variant == tl::kVariantLdg) c.t.prefetch = pf;
                         if ((rc = apply(c, c.t))) break;
                     }
                     if (rc) break;
@@ -743,11 +835,11 @@ extern "C" int tl_batch_autotune(tl_batch *B, double *best_ms_per_pass)
         if (rc == TL_OK) {
             B->opts = best_o;
             for (auto &c : cls) {
-                c.t.prefetch = best_o.prefetch;
+                if (c.t.variant == tl::kVariantLdg) c.t.prefetch = best_o.prefetch;
                 if ((rc = apply(c, c.t))) break;
             }
         }
-        if (rc == TL_OK) rc = refresh_groups(B);
+        if (rc == TL_OK) rc = build_groups(B);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -759,7 +851,8 @@ extern "C" int tl_batch_autotune(tl_batch *B, double *best_ms_per_pass)
     }
     char buf[512];
     for (auto &c : cls) {
-        snprintf(buf, sizeof buf, kBatchShapeFmt, c.N, c.nf, B->dtype, B->sm_count, c.t.zc, c.t.txt, c.t.prefetch);
+        snprintf(buf, sizeof buf, kBatchShapeFmt, c.N, c.nf, B->dtype, B->sm_count, c.t.variant, c.t.zc, c.t.txt,
+                 c.t.prefetch);
         append_tune_line(buf);
     }
     const std::string comp = composition(B->lats);

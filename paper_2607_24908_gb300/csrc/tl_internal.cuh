@@ -127,14 +127,25 @@ struct BatchJob {
     double *slots;
     int txt, ty, zc, gx, gy;
     unsigned nblocks;
+    int lpad;              // TMA variant: padded-row index of x = 0
+    const TmaMaps *maps;   // TMA variant: tensor maps of this pass's input arrays (global memory)
 };
 
-// Enqueue one grouped pass over every job (all with n_fields == nf) as a
-// persistent launch of `grid` CTAs of 256 threads walking the (job, tile)
-// items; prefetch > 0 runs the variant whose threads prefetch their words
-// three planes ahead (cp.async), the same arithmetic.
-cudaError_t launch_group(int dtype, int nf, int prefetch, const BatchJob *jobs, const unsigned *first_item,
-                         int njobs, unsigned total, const PassCoef &c, int grid, cudaStream_t s);
+// Enqueue one grouped pass over every job (all with n_fields == nf).
+// variant kVariantLdg: a persistent launch of `grid` CTAs of 256 threads
+// walking the (job, tile) items of the register-streaming pass; prefetch > 0
+// runs the variant whose threads prefetch their words three planes ahead
+// (cp.async), the same arithmetic.  variant kVariantTma: one CTA of 7 + 1 warps
+// per item (`total` CTAs) of the TMA pass, `stages` ring stages in `smem`
+// bytes of dynamic shared memory.
+cudaError_t launch_group(int dtype, int nf, int variant, int prefetch, int stages, size_t smem, const BatchJob *jobs,
+                         const unsigned *first_item, int njobs, unsigned total, const PassCoef &c, int grid,
+                         cudaStream_t s);
+
+// Shared memory a TMA group launch needs: `stages` stages of 2 nf boxes of at
+// most (ty + 2) x (txt W + 2W) elements (128-byte aligned regions), for the
+// largest (txt, ty) among its jobs.
+size_t tma_group_smem(int elem_bytes, int nf, int stages, int max_txt_w_plus_2w, int max_ty_plus_2);
 
 // Enqueue one fused pass (measure_only: energies of the stored state, no writes).
 cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,

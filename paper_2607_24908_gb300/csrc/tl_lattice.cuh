@@ -63,4 +63,7 @@ void invalidate_launches(tl_lattice *L);
 // Switch a lattice to launch shape t (grows its reduction slots if needed and
 // re-encodes tensor maps at the next TMA launch).
 int set_geometry(tl_lattice *L, const PassTuning &t);
+// Encode (if needed) the tensor maps of L's arrays for its current tile shape;
+// L->maps[p] then holds those of the arrays of buffer parity p.
+int lattice_tma_maps(tl_lattice *L);
 }  // namespace tl

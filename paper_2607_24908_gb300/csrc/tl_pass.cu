@@ -121,16 +121,27 @@ cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const Pa
                            : launch_pass_f64(m, fp, c, g, sc, slots, measure_only, s, maps);
 }
 
-cudaError_t launch_group_f32(int nf, int prefetch, const BatchJob *jobs, const unsigned *first_item, int njobs,
-                             unsigned total, const PassCoef &c, int grid, cudaStream_t s);
-cudaError_t launch_group_f64(int nf, int prefetch, const BatchJob *jobs, const unsigned *first_item, int njobs,
-                             unsigned total, const PassCoef &c, int grid, cudaStream_t s);
+cudaError_t launch_group_f32(int nf, int variant, int prefetch, int stages, size_t smem, const BatchJob *jobs,
+                             const unsigned *first_item, int njobs, unsigned total, const PassCoef &c, int grid,
+                             cudaStream_t s);
+cudaError_t launch_group_f64(int nf, int variant, int prefetch, int stages, size_t smem, const BatchJob *jobs,
+                             const unsigned *first_item, int njobs, unsigned total, const PassCoef &c, int grid,
+                             cudaStream_t s);
 
-cudaError_t launch_group(int dtype, int nf, int prefetch, const BatchJob *jobs, const unsigned *first_item,
-                         int njobs, unsigned total, const PassCoef &c, int grid, cudaStream_t s)
+cudaError_t launch_group(int dtype, int nf, int variant, int prefetch, int stages, size_t smem, const BatchJob *jobs,
+                         const unsigned *first_item, int njobs, unsigned total, const PassCoef &c, int grid,
+                         cudaStream_t s)
 {
-    return dtype == TL_F32 ? launch_group_f32(nf, prefetch, jobs, first_item, njobs, total, c, grid, s)
-                           : launch_group_f64(nf, prefetch, jobs, first_item, njobs, total, c, grid, s);
+    return dtype == TL_F32
+               ? launch_group_f32(nf, variant, prefetch, stages, smem, jobs, first_item, njobs, total, c, grid, s)
+               : launch_group_f64(nf, variant, prefetch, stages, smem, jobs, first_item, njobs, total, c, grid, s);
+}
+
+size_t tma_group_smem(int elem_bytes, int nf, int stages, int max_txt_w_plus_2w, int max_ty_plus_2)
+{
+    const size_t box = (size_t)max_ty_plus_2 * max_txt_w_plus_2w * (size_t)elem_bytes;
+    const size_t region = (box + 127) / 128 * 128;
+    return (size_t)stages * nf * 2 * region;
 }
 
 // Refresh the ghost copies of one array (layout in tl_internal.cuh): the W

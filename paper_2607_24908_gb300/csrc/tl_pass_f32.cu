@@ -15,9 +15,18 @@ cudaError_t launch_pass_f32(const Model &m, const FieldPtrs &fp, const PassCoef 
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_group_f32(int nf, int prefetch, const BatchJob *jobs, const unsigned *first_item, int njobs,
-                              unsigned total, const PassCoef &c, int grid, cudaStream_t s)
+cudaError_t launch_group_f32(int nf, int variant, int prefetch, int stages, size_t smem, const BatchJob *jobs,
+                              const unsigned *first_item, int njobs, unsigned total, const PassCoef &c, int grid,
+                              cudaStream_t s)
 {
+    if (variant == kVariantTma) {
+        switch (nf) {
+        case 1: return launch_tma_group_t<float, 1>(stages, smem, jobs, first_item, njobs, total, c, s);
+        case 2: return launch_tma_group_t<float, 2>(stages, smem, jobs, first_item, njobs, total, c, s);
+        case 3: return launch_tma_group_t<float, 3>(stages, smem, jobs, first_item, njobs, total, c, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (nf) {
     case 1: return launch_group_t<float, 1>(prefetch, jobs, first_item, njobs, total, c, grid, s);
     case 2: return launch_group_t<float, 2>(prefetch, jobs, first_item, njobs, total, c, grid, s);

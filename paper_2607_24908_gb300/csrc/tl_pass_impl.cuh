@@ -743,10 +743,15 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 
 constexpr int kMaxStages = 8;
 
-template <typename T, int NF, bool MEASURE, int NTHR>
-__global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
-                                                         int S, int lpad, const __grid_constant__ TmaMaps maps,
-                                                         Scalars *sc, double *slots)
+// One CTA tile (bx, by, bz) of the TMA pass; bid/nblocks index the tile among
+// the lattice's tiles for the reduction; maps points to the tensor maps of the
+// lattice's input arrays (a kernel parameter or a copy in global memory).
+// GLOBAL_MAPS: the maps live in global memory, written by the host; the
+// producer makes them visible to the tensor-map proxy before their first use.
+template <typename T, int NF, bool MEASURE, bool GLOBAL_MAPS = false>
+__device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, const PassCoef &c, int txt, int ty,
+                                         int zc, int S, int lpad, const TmaMaps *maps, Scalars *sc, double *slots,
+                                         int bx, int by, int bz, unsigned bid, unsigned nblocks)
 {
     constexpr int W = Vec<T>::W;
     constexpr int NQ = 2 * NF + 1;
@@ -760,7 +765,7 @@ __global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Mo
     const int lane = tid & 31;
     const int CW = (blockDim.x >> 5) - 1;
     const bool producer = (tid >> 5) == CW;
-    const int x_tile = blockIdx.x * txt * W, y_tile = blockIdx.y * ty;
+    const int x_tile = bx * txt * W, y_tile = by * ty;
     const int tx = tid % txt, tyi = tid / txt;
     const int x0 = x_tile + tx * W;
     const int y = y_tile + tyi;
@@ -773,7 +778,7 @@ __global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Mo
     __syncthreads();
     if (lane == 0 && warp_active) atomicAdd(&s_warps, 1);
     __syncthreads();
-    const int z0 = blockIdx.z * zc;
+    const int z0 = bz * zc;
     const int z1 = min(z0 + zc, N);
     const int K = (z1 - z0) + 2;  // planes z0-1 .. z1
     const int rowe = txt * W + 2 * W;
@@ -800,6 +805,12 @@ __global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Mo
 
     if (producer) {
         if ((tid & 31) == 0) {
+            if constexpr (GLOBAL_MAPS) {
+#pragma unroll
+                for (int i = 0; i < 2 * NF; ++i)
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->map[i])
+                                 : "memory");
+            }
             for (int k = 0; k < K; ++k) {
                 const int s = k % S;
                 if (k >= S && !mbar_wait_bounded(&empty[s], ((k / S) - 1) & 1u, sc)) {
@@ -813,7 +824,7 @@ __global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Mo
                 for (int f = 0; f < NF; ++f)
 #pragma unroll
                     for (int a = 0; a < 2; ++a)
-                        tma_load_3d(arr(s, f, a), &maps.map[2 * f + a], lpad + x_tile - W, y_tile, zg, &full[s]);
+                        tma_load_3d(arr(s, f, a), &maps->map[2 * f + a], lpad + x_tile - W, y_tile, zg, &full[s]);
                 issued = k + 1;
             }
         }
@@ -927,7 +938,46 @@ __global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Mo
     if (s_failed && producer && (tid & 31) == 0)
         for (int kk = (issued > S ? issued - S : 0); kk < issued; ++kk)
             mbar_wait_bounded(&full[kk % S], (kk / S) & 1u, sc);
-    cta_reduce_finalize<NQ, sizeof(T) == 4>(accd, m, c, sc, slots, grid_bid(), grid_nblocks());
+    cta_reduce_finalize<NQ, sizeof(T) == 4>(accd, m, c, sc, slots, bid, nblocks);
+}
+
+template <typename T, int NF, bool MEASURE, int NTHR>
+__global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
+                                                         int S, int lpad, const __grid_constant__ TmaMaps maps,
+                                                         Scalars *sc, double *slots)
+{
+    tma_tile<T, NF, MEASURE>(m, fp, c, txt, ty, zc, S, lpad, &maps, sc, slots, blockIdx.x, blockIdx.y, blockIdx.z,
+                             grid_bid(), grid_nblocks());
+}
+
+// Batched form of the TMA pass: one CTA per (job, tile) item of all jobs of a
+// group (same precision and field count, 7 + 1 warps), each job with its own
+// model, fields, scalars, reduction slots, tile geometry and tensor maps (in
+// global memory), so every job's results are bitwise those of fused_pass_tma on
+// it alone with the same geometry.  S stages of at most `region` bytes per box.
+template <typename T, int NF>
+__global__ void __launch_bounds__(256, 2) fused_pass_tma_group(const BatchJob *__restrict__ jobs,
+                                                               const unsigned *__restrict__ first_item, int njobs,
+                                                               PassCoef c, int S)
+{
+    __shared__ int s_job;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = njobs - 1;  // last job whose first item <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(first_item + mid) <= blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const BatchJob &j = jobs[s_job];
+    const unsigned local = blockIdx.x - __ldg(first_item + s_job);
+    const int bx = (int)(local % (unsigned)j.gx);
+    const int by = (int)((local / (unsigned)j.gx) % (unsigned)j.gy);
+    const int bz = (int)(local / ((unsigned)j.gx * (unsigned)j.gy));
+    tma_tile<T, NF, false, true>(j.m, j.fp, c, j.txt, j.ty, j.zc, S, j.lpad, j.maps, j.sc, j.slots, bx, by, bz, local,
+                                 j.nblocks);
 }
 
 // The dynamic shared-memory limit of a kernel is a per-device attribute: raise
@@ -964,6 +1014,19 @@ static cudaError_t launch_tma(const Model &m, const FieldPtrs &fp, const PassCoe
     cudaError_t e = ensure_smem_attribute(kern, g.smem, configured, big);
     if (e != cudaSuccess) return e;
     kern<<<g.grid, 32 * (g.cwarps + 1), g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, g.stages, g.lpad, maps, sc, slots);
+    return cudaGetLastError();
+}
+
+template <typename T, int NF>
+static cudaError_t launch_tma_group_t(int stages, size_t smem, const BatchJob *jobs, const unsigned *first_item,
+                                      int njobs, unsigned total, const PassCoef &c, cudaStream_t s)
+{
+    static std::atomic<size_t> configured[kMaxDevices][2];
+    auto kern = fused_pass_tma_group<T, NF>;
+    cudaError_t e = ensure_smem_attribute(kern, smem, configured, 0);
+    if (e != cudaSuccess) return e;
+    if (total == 0) return cudaSuccess;
+    kern<<<total, 256, smem, s>>>(jobs, first_item, njobs, c, stages);
     return cudaGetLastError();
 }
 

@@ -227,3 +227,78 @@ def test_batch_autotune_keeps_state_and_steps_bitwise_like_each_member_alone(dty
             if ex:
                 assert abs(E.a - oa) / oa < 1e-12 and abs(E.b - ob) / ob < 1e-12
         lat.close()
+
+
+_TMA_GROUP_SCRIPT = r"""
+import json, math, os, sys
+import numpy as np
+import torch
+sys.path.insert(0, os.getcwd())
+import oracle as o
+from paper_2607_24908_gb300 import tl as T
+from paper_2607_24908_gb300.workloads import white_noise_state
+jobs = json.loads(sys.argv[1])
+sms = torch.cuda.get_device_properties(0).multi_processor_count
+path = sys.argv[2]
+with open(path, "w") as fh:  # batch shapes on the TMA pass for every class, read at the first batch call
+    for dt in (0, 1):
+        for N, nf, q, ex, seed, zc in jobs:
+            fh.write(json.dumps({"batch_shape": {"N": N, "fields": nf, "dtype": dt, "sms": sms, "variant": 1,
+                                                 "z_chunk": zc, "tile_x": 0, "prefetch": 0}}) + "\n")
+os.environ["TL_TUNE_FILE"] = path
+out = {}
+for dtype in ("f32", "f64"):
+    npd = np.float32 if dtype == "f32" else np.float64
+    def make(N, nf, q, ex):
+        lat = T.Lattice(N, 0.5, nf, dtype, ex, 1.0, 1.0, 1.0)
+        cfg = T.batch_pass_config(N, nf, dtype)
+        assert cfg["kind"] == "tma", cfg
+        lat.set_pass_config(**cfg)
+        lat.set_potential(1.0, q, (0.0, 0.1, 0.0))
+        return lat
+    def fill(lat, N, nf, seed, ex):
+        phi, pi = white_noise_state(N, nf, seed=seed, phi0=(1.0, 0.0), sigma_phi=1e-3, sigma_pi=1e-3)
+        lat.set_state(phi.astype(npd), pi.astype(npd), 1.0, 0.0, b_from_constraint=ex)
+        return phi.astype(npd), pi.astype(npd)
+    lats, inputs = [], []
+    for N, nf, q, ex, seed, zc in jobs:
+        lat = make(N, nf, q, ex); inputs.append(fill(lat, N, nf, seed, ex)); lats.append(lat)
+    with T.Batch(lats) as b:
+        b.step(6, 0.01, "verlet")
+        b.step(6, 0.01, "verlet")  # the second call replays the captured graph
+    worst = 0.0
+    for lat, (N, nf, q, ex, seed, zc), (phi0, pi0) in zip(lats, jobs, inputs):
+        assert lat.pass_config()["kind"] == "tma"
+        twin = make(N, nf, q, ex); fill(twin, N, nf, seed, ex)
+        twin.step(6, 0.01, "verlet"); twin.step(6, 0.01, "verlet")
+        phi, pi = lat.get_all(); tphi, tpi = twin.get_all()
+        E, tE = lat.energies(), twin.energies()
+        assert np.array_equal(phi, tphi) and np.array_equal(pi, tpi), (dtype, N, nf)
+        assert np.array_equal(E.vector(), tE.vector()) and E.a == tE.a and E.b == tE.b, (dtype, N, nf)
+        twin.close()
+        if dtype == "f64":
+            p = o.Params(N=N, nf=nf, kIR=0.5, expanding=ex, alpha=1.0, lam=1.0, q=q, m2=(0.0, 0.1, 0.0))
+            b0 = math.sqrt(float(np.sum(o.energies(p, phi0, pi0, 1.0))) / 3.0) if ex else 0.0
+            ophi, opi, oa, ob = o.run(p, phi0, pi0, 1.0, b0, 0.01, 12, o.VERLET)
+            worst = max(worst, float(np.max(np.abs(phi - ophi)) / np.max(np.abs(ophi))),
+                        float(np.max(np.abs(pi - opi)) / np.max(np.abs(opi))))
+            if ex:
+                worst = max(worst, abs(E.a - oa) / oa, abs(E.b - ob) / ob)
+        lat.close()
+    out[dtype] = worst
+print("RESULT " + json.dumps(out))
+"""
+
+
+def test_tma_group_is_bitwise_the_single_lattice_tma_pass(tmp_path):
+    """Members whose batch shape is the TMA pass (here from TL_TUNE_FILE entries, read by a fresh
+    process) run through the grouped TMA kernel (one CTA per item, each job's tensor maps in global
+    memory): fields, energies, a and a' bitwise those of each member alone on the same shape, across a
+    graph replay; FP64 members against the oracle to 1e-12."""
+    jobs = [(N, nf, q, ex, seed, zc) for (N, nf, q, ex, seed), zc in zip(JOBS, (16, 8, 24, 16, 32, 16))]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", _TMA_GROUP_SCRIPT, json.dumps(jobs), str(tmp_path / "tune.txt")],
+                         cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-3000:]
+    res = json.loads(out.stdout.strip().splitlines()[-1][len("RESULT "):])
+    assert res["f64"] < 1e-12, res
