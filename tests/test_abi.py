@@ -106,3 +106,13 @@ def test_product_path_never_imports_or_links_the_oracle():
                 assert "oracle" not in line and "tlo" not in line, (path, line)
     build = pathlib.Path(pkg, "build.py").read_text()
     assert "oracle" not in build and "tlo.c" not in build
+
+
+def test_header_is_plain_c11():
+    """include/tl.h compiles as C11 (no C++ in the boundary's declarations)."""
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = '#include "tl.h"\nint main(void) { tl_energies_t e; (void)e; return TL_OK; }\n'
+    out = subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-pedantic", "-fsyntax-only", "-x", "c",
+                          "-I", os.path.join(root, "include"), "-"], input=src, capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr

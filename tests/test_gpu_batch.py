@@ -257,7 +257,7 @@ for dtype in ("f32", "f64"):
         lat.set_potential(1.0, q, (0.0, 0.1, 0.0))
         return lat
     def fill(lat, N, nf, seed, ex):
-        phi, pi = white_noise_state(N, nf, seed=seed, phi0=(1.0, 0.0), sigma_phi=1e-3, sigma_pi=1e-3)
+        phi, pi = white_noise_state(N, nf, seed=seed, phi0=(1.0, 0.0, 0.0), sigma_phi=1e-3, sigma_pi=1e-3)
         lat.set_state(phi.astype(npd), pi.astype(npd), 1.0, 0.0, b_from_constraint=ex)
         return phi.astype(npd), pi.astype(npd)
     lats, inputs = [], []
@@ -296,9 +296,39 @@ def test_tma_group_is_bitwise_the_single_lattice_tma_pass(tmp_path):
     memory): fields, energies, a and a' bitwise those of each member alone on the same shape, across a
     graph replay; FP64 members against the oracle to 1e-12."""
     jobs = [(N, nf, q, ex, seed, zc) for (N, nf, q, ex, seed), zc in zip(JOBS, (16, 8, 24, 16, 32, 16))]
+    jobs += [(28, 3, 50.0, True, 17, 28), (36, 3, 10.0, False, 18, 12)]  # three-field TMA group
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = subprocess.run([sys.executable, "-c", _TMA_GROUP_SCRIPT, json.dumps(jobs), str(tmp_path / "tune.txt")],
                          cwd=root, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-3000:]
     res = json.loads(out.stdout.strip().splitlines()[-1][len("RESULT "):])
     assert res["f64"] < 1e-12, res
+
+
+def test_batch_membership_rules_and_a_batch_of_one():
+    """A lattice belongs to at most one batch at a time (a second batch is refused until the first
+    is destroyed), lattices of different precisions cannot share a batch, and a batch of one lattice
+    steps bitwise like that lattice alone on its batch shape."""
+    N, nf, q, ex, seed = JOBS[1]
+    a = make(N, nf, q, ex, "f32")
+    fill(a, N, nf, seed, "f32")
+    other = make(32, 1, 0.0, True, "f64")
+    fill(other, 32, 1, 5, "f64")
+    with pytest.raises(T.TLError) as e:
+        T.Batch([a, other])
+    assert e.value.code == T.EINVAL
+    b1 = T.Batch([a])
+    with pytest.raises(T.TLError) as e:
+        T.Batch([a])
+    assert e.value.code == T.EINVAL and "already in a batch" in str(e.value)
+    b1.step(8, 0.01, "verlet")
+    b1.close()
+    T.Batch([a]).close()  # allowed again once the first batch is gone
+    twin = make(N, nf, q, ex, "f32")
+    fill(twin, N, nf, seed, "f32")
+    twin.step(8, 0.01, "verlet")
+    assert np.array_equal(a.get_all()[0], twin.get_all()[0]) and np.array_equal(a.get_all()[1], twin.get_all()[1])
+    Ea, Et = a.energies(), twin.energies()
+    assert np.array_equal(Ea.vector(), Et.vector()) and Ea.a == Et.a and Ea.b == Et.b
+    for lat in (a, other, twin):
+        lat.close()
