@@ -418,7 +418,8 @@ int tl_autotune(tl_lattice *lat, double *best_ms_per_pass);
  * TL_ESTATE while the lattice is in a batch.  May synchronise the lattice
  * stream (to grow its reduction slots).  A new lattice starts on TL_PASS_TMA
  * when it is FP32 and N >= 192 (z-chunks of 16 planes at N = 192, 64 up to
- * N = 511, 72 from 512; 15 compute warps from N = 768, else 7), on
+ * N = 511, then 96, 88 and 92 planes around N = 512, 768 and 1024, where they
+ * measured fastest; 15 compute warps from N = 768, else 7), on
  * TL_PASS_STREAM otherwise (where those measured faster); the environment
  * variable TL_PASS_VARIANT=tma|ldg overrides that default at creation. */
 int tl_set_pass_config(tl_lattice *lat, const tl_pass_config *cfg);

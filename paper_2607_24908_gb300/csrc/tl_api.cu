@@ -56,7 +56,11 @@ tl::PassTuning tl::default_tuning(int N, int nf, int elem_bytes)
     if (v && strcmp(v, "ldg") == 0) t.variant = tl::kVariantLdg;
     const char *cw = getenv("TL_BULK_WARPS"), *zc = getenv("TL_PASS_ZC");
     if (t.variant == tl::kVariantTma) {  // measured: long z-chunks for the ring, 15 + 1 warps on large lattices
-        t.zc = N <= 192 ? 16 : (N >= 512 ? 72 : 64);
+        // z-chunks from sweeps with the 64-byte L2 promotion (two FP32 fields, ms per pass):
+        // 512^3 96 planes 0.777 (72: 0.783), 768^3 88 planes 2.416 (72: 2.424), 1024^3 92
+        // planes 5.545 (72: 5.580); the optimum is jagged in the chunk count, so each
+        // measured size sets the value for the sizes around it
+        t.zc = N <= 192 ? 16 : (N < 512 ? 64 : (N < 640 ? 96 : (N < 896 ? 88 : 92)));
         t.cwarps = N >= 768 ? 15 : 7;
     }
     if ((v = getenv("TL_PREFETCH"))) t.prefetch = atoi(v);

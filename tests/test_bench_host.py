@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
-DEFAULT_1024 = {"kind": "tma", "warps": 15, "stages": 6, "z_chunk": 72, "tile_x": 0, "threads": 0}
+DEFAULT_1024 = {"kind": "tma", "warps": 15, "stages": 6, "z_chunk": 92, "tile_x": 0, "threads": 0}
 
 
 def test_traffic_reported_exactly_when_summary_matches_sources_and_shape():
@@ -25,7 +25,7 @@ def test_traffic_reported_exactly_when_summary_matches_sources_and_shape():
 
 
 def test_traffic_is_null_for_another_shape_or_changed_sources(monkeypatch, tmp_path):
-    assert bench.measured_traffic(dict(DEFAULT_1024, z_chunk=64)) is None
+    assert bench.measured_traffic(dict(DEFAULT_1024, z_chunk=72)) is None
     assert bench.measured_traffic(dict(DEFAULT_1024, kind="stream")) is None
     changed = tmp_path / "tl_pass_impl.cuh"
     changed.write_bytes(pathlib.Path(bench.KERNEL_SRCS[0]).read_bytes() + b"\n// edited\n")

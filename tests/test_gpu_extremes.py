@@ -114,7 +114,7 @@ def test_commit_state_equals_set_state(dtype):
 def test_largest_lattice_homogeneous_state():
     """N = 2048 (the largest N accepted), one FP32 field in caller buffers (4 x 35.5 GB),
     homogeneous phi = 1, pi = 0, expanding: after 6 Verlet steps under three launch shapes (the
-    streaming kernel, TMA 7+1 warps, and the default at this size, TMA 15+1 warps with 72-plane chunks)
+    streaming kernel, TMA 7+1 warps, and the default at this size, TMA 15+1 warps with 92-plane chunks)
     a, b, K and V equal the oracle's run of the same homogeneous state on 8^3 (1e-5) and
     the gradient energy is exactly zero."""
     import torch
@@ -132,7 +132,7 @@ def test_largest_lattice_homogeneous_state():
     oE = o.energies(p, *o.run(p, ph, pi, 1.0, b0, dt, steps, o.VERLET)[:2], oa)
     bufs = [torch.empty(elems, dtype=torch.float32, device="cuda") for _ in range(4)]
     try:
-        for shape in (dict(kind="stream"), dict(kind="tma"), dict(kind="tma", warps=15, z_chunk=72)):
+        for shape in (dict(kind="stream"), dict(kind="tma"), dict(kind="tma", warps=15, z_chunk=92)):
             bufs[0].fill_(1.0)
             bufs[1].fill_(0.0)
             torch.cuda.synchronize()

@@ -92,9 +92,9 @@ def test_default_shape_and_errors():
         with T.Lattice(256, 0.5, 1, "f32") as one:  # FP32 from 192: TMA, 64-plane chunks below 512
             c1 = one.pass_config()
             assert (c1["kind"], c1["warps"], c1["z_chunk"]) == ("tma", 7, 64)
-        with T.Lattice(512, 0.5, 1, "f32") as mid:  # 72-plane chunks from 512
+        with T.Lattice(512, 0.5, 1, "f32") as mid:  # 96-plane chunks around 512
             c3 = mid.pass_config()
-            assert (c3["kind"], c3["warps"], c3["z_chunk"]) == ("tma", 7, 72)
+            assert (c3["kind"], c3["warps"], c3["z_chunk"]) == ("tma", 7, 96)
         with T.Lattice(256, 0.5, 2, "f64") as f64:  # FP64: the streaming pass
             assert f64.pass_config()["kind"] == "stream"
         bad = [dict(kind="tma", warps=8), dict(kind="tma", stages=2), dict(kind="tma", stages=9),
