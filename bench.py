@@ -45,12 +45,13 @@ PASSES = {"leapfrog": 1, "verlet": 1, "yoshida4": 3}[WL.integrator]
 BYTES_PER_SITE_FIELD_PASS = 4 * (4 if WL.dtype == "f32" else 8)  # read phi, pi; write phi, pi
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fused_pass_1024cubed_2f_f32.md")
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2607_24908_gb300", "csrc", n)
-               for n in ("tl_pass_impl.cuh", "tl_pass.cu", "tl_pass_f32.cu", "tl_api.cu")]
+               for n in ("tl_pass_impl.cuh", "tl_pass.cu", "tl_pass_f32.cu", "tl_tma_maps.cu", "tl_lattice.cuh")]
 
 
 def kernel_hash() -> str:
-    """sha256 of the fused-pass sources (kernel, geometry, FP32 instantiation,
-    and the host runtime that encodes the tensor maps)."""
+    """sha256 of what fixes the fused pass's DRAM traffic: the kernel, its
+    geometry and FP32 instantiation, the tensor-map encoding and the padded
+    array layout."""
     h = hashlib.sha256()
     for p in KERNEL_SRCS:
         with open(p, "rb") as f:

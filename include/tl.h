@@ -219,6 +219,29 @@ int tl_set_state(tl_lattice *lat, int field, int which, const void *host, size_t
  * b = a^(1+alpha) sqrt(mu2 rho/3) from the current state's energies. */
 int tl_set_background(tl_lattice *lat, double a, double b, int from_constraint);
 
+/* No counterpart in the paper (checkpoint and resume of a run).
+ * The lattice's counters: completed time steps and program time eta since the
+ * last tl_init_fluctuations / tl_set_state / tl_commit_state, and the Langevin
+ * steps taken since then (the noise counter of tl_langevin_step). */
+typedef struct {
+    int64_t step;
+    double time;
+    int64_t langevin_steps;
+} tl_clock;
+
+/* Read the counters.  Synchronises the lattice stream.
+ * Errors: TL_EINVAL (NULL), TL_ECUDA. */
+int tl_get_clock(tl_lattice *lat, tl_clock *out);
+
+/* Restore the counters of a checkpoint: after tl_set_state of every array and
+ * tl_set_background(a, b, 0) with a, b of tl_energies, a lattice of the same
+ * size, fields, precision, potential and pass shape then continues bitwise as
+ * the one the checkpoint was taken from, under the same tl_step calls.  Call it
+ * last (tl_set_state and tl_set_background reset the counters).
+ * Synchronises.  Errors: TL_EINVAL (NULL, negative counts, non-finite time),
+ * TL_ESTATE (no state, or in a batch), TL_ECUDA. */
+int tl_set_clock(tl_lattice *lat, const tl_clock *clock);
+
 /* No counterpart in the paper (zero-copy access for callers on the device).
  * Device address of element (0, 0, 0) of phi_field / pi_field of the current
  * state (padded layout, see tl_array_layout; valid until the next tl_step). */
@@ -420,7 +443,8 @@ int tl_autotune(tl_lattice *lat, double *best_ms_per_pass);
  * when it is FP32 and N >= 192 (z-chunks of 16 planes at N = 192, 64 up to
  * N = 511, then 96, 88 and 92 planes around N = 512, 768 and 1024, where they
  * measured fastest; 15 compute warps from N = 768, else 7), on
- * TL_PASS_STREAM otherwise (where those measured faster); the environment
+ * TL_PASS_STREAM otherwise (where those measured faster; FP64 from N = 128
+ * with z-chunks of 32 planes, 64 from N = 512); the environment
  * variable TL_PASS_VARIANT=tma|ldg overrides that default at creation. */
 int tl_set_pass_config(tl_lattice *lat, const tl_pass_config *cfg);
 

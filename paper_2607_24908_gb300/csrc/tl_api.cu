@@ -1,9 +1,8 @@
 // Host runtime behind include/tl.h: lattice objects, the integrator schedule
 // (pass list), launches, state transfer, initial fields and spectra.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cufft.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -62,6 +61,12 @@ tl::PassTuning tl::default_tuning(int N, int nf, int elem_bytes)
         // measured size sets the value for the sizes around it
         t.zc = N <= 192 ? 16 : (N < 512 ? 64 : (N < 640 ? 96 : (N < 896 ? 88 : 92)));
         t.cwarps = N >= 768 ? 15 : 7;
+    } else if (elem_bytes == 8 && N >= 128) {
+        // FP64 streaming pass (bound by the FP64 pipe): 32-plane chunks from 128^3 (one and two
+        // fields, 128^3 ... 384^3: 0.7316 ms at 256^3 against 0.7465 with the 16 of the automatic
+        // rule), 64 from 512^3 (5.465 vs 5.525 ms); tile row widths 8, 16, 32 measured alike.
+        // Smaller FP64 lattices keep the automatic rule, which spreads them over more SMs.
+        t.zc = N >= 512 ? 64 : 32;
     }
     if ((v = getenv("TL_PREFETCH"))) t.prefetch = atoi(v);
     if ((v = getenv("TL_LDG_THREADS"))) t.threads = atoi(v);
@@ -131,27 +136,6 @@ namespace {
 
 size_t n3_of(int N) { return (size_t)N * (size_t)N * (size_t)N; }
 
-// Padded array layout (see tl_internal.cuh): W = 16/esz ghost elements on
-// each side of a row (the left ones inside a 128-byte pad so that x = 0 of
-// every row starts a 128-byte line), rows padded to a multiple of 128 bytes,
-// one ghost row on each side of a plane, no z ghosts.
-struct Layout {
-    long long W, lpad, pitch, pplane;
-    size_t elems, origin;
-};
-Layout layout_of(int N, size_t esz)
-{
-    Layout l;
-    const long long line = (long long)(128 / esz);
-    l.W = (long long)(16 / esz);
-    l.lpad = line;
-    l.pitch = (l.lpad + N + l.W + line - 1) / line * line;
-    l.pplane = (long long)(N + 2) * l.pitch;
-    l.elems = (size_t)N * (size_t)l.pplane;
-    l.origin = (size_t)(l.pitch + l.lpad);
-    return l;
-}
-
 // Bytes between consecutive field arrays beyond their size (TL_ARRAY_STAGGER,
 // rounded to 256 bytes; default 0).
 size_t array_stagger()
@@ -179,7 +163,7 @@ int check_dims(int N, double kIR, int n_fields, tl_dtype dtype, const tl_expansi
 void refresh_model(tl_lattice *L)
 {
     Model &m = L->model;
-    const Layout lay = layout_of(L->N, L->esz);
+    const tl::Layout lay = tl::layout_of(L->N, L->esz);
     m.N = L->N;
     m.nf = L->nf;
     m.ghosts = 1;
@@ -224,76 +208,13 @@ int finish_create(tl_lattice *L, int N, double kIR, int nf, tl_dtype dtype, cons
     return TL_OK;
 }
 
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
-// Encode the tensor maps of both buffer parities for the current tile shape:
-// 3-D (padded row, row incl. ghost rows, plane) over each array, box
-// (txt W + 2W) x (ty + 2) x 1.
-int ensure_tma_maps(tl_lattice *L)
-{
-    const tl::PassGeom &g = L->geom;
-    if (L->maps_txt == g.txt && L->maps_ty == g.ty) return TL_OK;
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc) return fail(TL_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    const size_t esz = L->esz;
-    const int W = (int)(16 / esz);
-    const Layout lay = layout_of(L->N, esz);
-    const cuuint64_t dims[3] = {(cuuint64_t)lay.pitch, (cuuint64_t)(L->N + 2), (cuuint64_t)L->N};
-    const cuuint64_t strides[2] = {(cuuint64_t)lay.pitch * esz, (cuuint64_t)lay.pplane * esz};
-    // Test hook (host-side fault injection): TL_TEST_STALL_TMA encodes boxes one
-    // row short, so every stage receives fewer bytes than its barrier expects and
-    // the kernel's bounded waits expire (TL_ETIMEOUT) -- a wait that runs out,
-    // with every copy inside its stage region.
-    const bool stall = getenv("TL_TEST_STALL_TMA") != nullptr;
-    const cuuint32_t box[3] = {(cuuint32_t)(g.txt * W + 2 * W), (cuuint32_t)(g.ty + (stall ? 1 : 2)), 1u};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    // L2 promotion of the copies: 64 bytes (measured at N = 256 ... 1024 two
-    // fields, 256^3 one field and the grouped ensemble: 0.1-0.5% faster than
-    // 256 bytes, 3.4% fewer DRAM reads at 1024^3).  Environment override for
-    // tuning experiments: TL_TMA_L2_PROMOTION = none, 64, 128 or 256.
-    CUtensorMapL2promotion promo = CU_TENSOR_MAP_L2_PROMOTION_L2_64B;
-    if (const char *v = getenv("TL_TMA_L2_PROMOTION")) {
-        if (strcmp(v, "none") == 0) promo = CU_TENSOR_MAP_L2_PROMOTION_NONE;
-        else if (strcmp(v, "128") == 0) promo = CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
-        else if (strcmp(v, "256") == 0) promo = CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
-    }
-    for (int par = 0; par < 2; ++par)
-        for (int f = 0; f < L->nf; ++f)
-            for (int a = 0; a < 2; ++a) {
-                void *base = static_cast<char *>(L->buf[par][a][f]) - lay.origin * esz;
-                CUresult r = enc(&L->maps[par].map[2 * f + a],
-                                 esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base,
-                                 dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                 promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                if (r != CUDA_SUCCESS) return fail(TL_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-            }
-    L->maps_txt = g.txt;
-    L->maps_ty = g.ty;
-    return TL_OK;
-}
-
 int launch(tl_lattice *L, const PassCoef &c, bool measure_only, cudaStream_t stream);
 int launch(tl_lattice *L, const PassCoef &c, bool measure_only) { return launch(L, c, measure_only, L->stream); }
 int launch(tl_lattice *L, const PassCoef &c, bool measure_only, cudaStream_t stream)
 {
     const tl::TmaMaps *maps = nullptr;
     if (L->geom.variant == tl::kVariantTma) {
-        int rc = ensure_tma_maps(L);
+        int rc = tl::lattice_tma_maps(L);
         if (rc) return rc;
         maps = &L->maps[L->cur];
     }
@@ -396,8 +317,6 @@ int tl::set_geometry(tl_lattice *L, const PassTuning &t)
     return TL_OK;
 }
 
-int tl::lattice_tma_maps(tl_lattice *L) { return ensure_tma_maps(L); }
-
 void tl::invalidate_launches(tl_lattice *L)
 {
     for (auto &g : L->graphs)
@@ -415,13 +334,13 @@ size_t tl_state_bytes(int N, int n_fields, tl_dtype dtype)
 {
     if (N <= 0 || n_fields <= 0) return 0;
     const size_t esz = dtype == TL_F64 ? 8 : 4;
-    return 4 * (size_t)n_fields * layout_of(N, esz).elems * esz;
+    return 4 * (size_t)n_fields * tl::layout_of(N, esz).elems * esz;
 }
 
 int tl_array_layout(int N, tl_dtype dtype, size_t *elems, size_t *row_pitch, size_t *plane_pitch, size_t *origin)
 {
     if (N < 8 || N % 4 != 0 || (dtype != TL_F32 && dtype != TL_F64)) return fail(TL_EINVAL, "bad N or dtype");
-    const Layout l = layout_of(N, dtype == TL_F64 ? 8 : 4);
+    const tl::Layout l = tl::layout_of(N, dtype == TL_F64 ? 8 : 4);
     if (elems) *elems = l.elems;
     if (row_pitch) *row_pitch = (size_t)l.pitch;
     if (plane_pitch) *plane_pitch = (size_t)l.pplane;
@@ -458,7 +377,7 @@ int tl_lattice_create(tl_lattice **out, int N, double kIR, int n_fields, tl_dtyp
     }
     L->own = true;
     const size_t esz = dtype == TL_F64 ? 8 : 4;
-    const Layout lay = layout_of(N, esz);
+    const tl::Layout lay = tl::layout_of(N, esz);
     const size_t arr = lay.elems * esz;
     char *p = static_cast<char *>(L->base);
     memset(L->buf, 0, sizeof L->buf);
@@ -493,7 +412,7 @@ int tl_lattice_create_with_buffers(tl_lattice **out, int N, double kIR, int n_fi
     if (!L) return fail(TL_ENOMEM, "host allocation failed");
     memset(L->buf, 0, sizeof L->buf);
     const size_t esz = dtype == TL_F64 ? 8 : 4;
-    const size_t org = layout_of(N, esz).origin * esz;
+    const size_t org = tl::layout_of(N, esz).origin * esz;
     for (int f = 0; f < n_fields; ++f) {
         L->buf[0][0][f] = static_cast<char *>(dev_ptrs[4 * f + 0]) + org;
         L->buf[0][1][f] = static_cast<char *>(dev_ptrs[4 * f + 1]) + org;
@@ -620,6 +539,7 @@ extern "C" {
 
 int tl_step(tl_lattice *L, int n, double dt, tl_integrator integrator)
 {
+    tl::NvtxScope nvtx_range("tl_step");
     g_err[0] = 0;
     if (!L) return fail(TL_EINVAL, "NULL lattice");
     if (n < 0) return fail(TL_EINVAL, "n must be >= 0");
@@ -638,6 +558,7 @@ int tl_step(tl_lattice *L, int n, double dt, tl_integrator integrator)
 
 int tl_energies(tl_lattice *L, tl_energies_t *out)
 {
+    tl::NvtxScope nvtx_range("tl_energies");
     g_err[0] = 0;
     if (!L || !out) return fail(TL_EINVAL, "NULL argument");
     if (!L->has_state || !L->has_pot) return fail(TL_ESTATE, "no state or potential");
@@ -733,6 +654,36 @@ int tl_set_background(tl_lattice *L, double a, double b, int from_constraint)
     return TL_OK;
 }
 
+int tl_get_clock(tl_lattice *L, tl_clock *out)
+{
+    g_err[0] = 0;
+    if (!L || !out) return fail(TL_EINVAL, "NULL argument");
+    Scalars h;
+    int rc = read_scalars(L, &h);
+    if (rc) return rc;
+    out->step = L->step;
+    out->time = h.time;
+    out->langevin_steps = L->langevin_steps;
+    return TL_OK;
+}
+
+int tl_set_clock(tl_lattice *L, const tl_clock *c)
+{
+    g_err[0] = 0;
+    if (!L || !c) return fail(TL_EINVAL, "NULL argument");
+    if (c->step < 0 || c->langevin_steps < 0 || !isfinite(c->time))
+        return fail(TL_EINVAL, "step counts must be >= 0 and time finite");
+    if (!L->has_state) return fail(TL_ESTATE, "no state: set every array first");
+    if (L->batch_refs > 0) return fail(TL_ESTATE, "lattice is part of a batch");
+    const double t = c->time;
+    TL_CK(cudaMemcpyAsync(reinterpret_cast<char *>(L->d_sc) + offsetof(Scalars, time), &t, sizeof t,
+                          cudaMemcpyHostToDevice, L->stream));
+    TL_CK(cudaStreamSynchronize(L->stream));
+    L->step = c->step;
+    L->langevin_steps = c->langevin_steps;
+    return TL_OK;
+}
+
 int tl_state_device_ptr(tl_lattice *L, int field, int which, void **dev_ptr)
 {
     g_err[0] = 0;
@@ -794,6 +745,7 @@ int tl_spectrum_bins(int N)
 
 int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
 {
+    tl::NvtxScope nvtx_range("tl_init_fluctuations");
     g_err[0] = 0;
     if (!L || !spec) return fail(TL_EINVAL, "NULL argument");
     if (!L->has_pot) return fail(TL_ESTATE, "tl_set_potential must come first (b0 needs the potential)");
@@ -861,6 +813,7 @@ int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
 
 int tl_spectrum(tl_lattice *L, int field, int which, int nbins, double *k, double *P, int64_t *count)
 {
+    tl::NvtxScope nvtx_range("tl_spectrum");
     g_err[0] = 0;
     int rc = check_field(L, field, which);
     if (rc) return rc;

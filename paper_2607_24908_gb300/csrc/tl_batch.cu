@@ -379,6 +379,7 @@ int tl_batch_pass_config(int N, int n_fields, tl_dtype dtype, tl_pass_config *ou
 
 int tl_batch_create(tl_batch **out, tl_lattice *const *lats, int n, void *cuda_stream)
 {
+    tl::NvtxScope nvtx_range("tl_batch_create");
     tl::set_error(TL_OK, "", "");
     if (!out || !lats || n <= 0) return tl::fail(TL_EINVAL, "need a non-empty list of lattices");
     *out = nullptr;
@@ -469,6 +470,7 @@ int check_members(tl_batch *B)
 
 int tl_batch_step(tl_batch *B, int n, double dt, tl_integrator integrator)
 {
+    tl::NvtxScope nvtx_range("tl_batch_step");
     tl::set_error(TL_OK, "", "");
     if (!B) return tl::fail(TL_EINVAL, "NULL batch");
     if (n < 0) return tl::fail(TL_EINVAL, "n must be >= 0");
@@ -601,6 +603,7 @@ void save_tune_entry(const TuneKey &k, const TuneVal &v)
 
 extern "C" int tl_autotune(tl_lattice *L, double *best_ms_per_pass)
 {
+    tl::NvtxScope nvtx_range("tl_autotune");
     tl::set_error(TL_OK, "", "");
     if (!L) return tl::fail(TL_EINVAL, "NULL lattice");
     if (L->batch_refs > 0) return tl::fail(TL_ESTATE, "lattice is part of a batch");
@@ -730,6 +733,7 @@ int time_identity(tl_batch *B, cudaEvent_t e0, cudaEvent_t e1, double *ms_out)
 
 extern "C" int tl_batch_autotune(tl_batch *B, double *best_ms_per_pass)
 {
+    tl::NvtxScope nvtx_range("tl_batch_autotune");
     tl::set_error(TL_OK, "", "");
     if (!B) return tl::fail(TL_EINVAL, "NULL batch");
     int rc = check_members(B);

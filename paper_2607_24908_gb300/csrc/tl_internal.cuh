@@ -3,11 +3,22 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/tl.h"
 
 namespace tl {
+
+// A named NVTX range over a scope: the library's public calls show on a
+// profiler's timeline (nvtx3 is header-only; with no tool attached a push or
+// pop is a test of one function pointer).
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 constexpr int kMaxFields = TL_MAX_FIELDS;
 constexpr int kMaxQ = 2 * kMaxFields + 1;  // K_f, G_f, V

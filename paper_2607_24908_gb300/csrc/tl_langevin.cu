@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(256) langevin_pass(const T *__restrict__ in, T
 
 extern "C" int tl_langevin_step(tl_lattice *L, int n, double dt, const tl_langevin_params *p, uint64_t seed)
 {
+    tl::NvtxScope nvtx_range("tl_langevin_step");
     tl::set_error(TL_OK, "", "");
     if (!L || !p) return tl::fail(TL_EINVAL, "NULL argument");
     if (n < 0 || !(dt > 0.0) || !isfinite(dt)) return tl::fail(TL_EINVAL, "n >= 0 and a positive finite dt needed");

@@ -51,6 +51,28 @@ struct tl_lattice {
 };
 
 namespace tl {
+// Padded array layout (see tl_internal.cuh): W = 16/esz ghost elements on
+// each side of a row (the left ones inside a 128-byte pad so that x = 0 of
+// every row starts a 128-byte line), rows padded to a multiple of 128 bytes,
+// one ghost row on each side of a plane, no z ghosts.
+struct Layout {
+    long long W, lpad, pitch, pplane;
+    size_t elems, origin;
+};
+inline Layout layout_of(int N, size_t esz)
+{
+    Layout l;
+    const long long line = (long long)(128 / esz);
+    l.W = (long long)(16 / esz);
+    l.lpad = line;
+    l.pitch = (l.lpad + N + l.W + line - 1) / line * line;
+    l.pplane = (long long)(N + 2) * l.pitch;
+    l.elems = (size_t)N * (size_t)l.pplane;
+    l.origin = (size_t)(l.pitch + l.lpad);
+    return l;
+}
+
+
 // Launch one fused pass of a lattice on its stream and flip its buffers.
 int lattice_launch(tl_lattice *L, const PassCoef &c, bool measure_only);
 // Record an error message for tl_last_error(); returns code.

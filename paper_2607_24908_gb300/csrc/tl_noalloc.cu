@@ -78,6 +78,7 @@ extern "C" int tl_energies_noalloc(int N, double kIR, int n_fields, tl_dtype dty
                                    const tl_expansion *expansion, double a, const void *const *phi,
                                    const void *const *pi, void *cuda_stream, double *out)
 {
+    tl::NvtxScope nvtx_range("tl_energies_noalloc");
     tl::set_error(TL_OK, "", "");
     if (N < 8 || N % 4 != 0 || N > 2048) return fail(TL_EINVAL, "N must be a multiple of 4 in [8, 2048]");
     if (!(kIR > 0.0)) return fail(TL_EINVAL, "kIR must be positive");

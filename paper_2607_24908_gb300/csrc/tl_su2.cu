@@ -643,6 +643,7 @@ int tl_su2_init_random(tl_su2 *Y, uint64_t seed, double amp)
 
 int tl_su2_step(tl_su2 *Y, int n, double dt)
 {
+    tl::NvtxScope nvtx_range("tl_su2_step");
     tl::set_error(TL_OK, "", "");
     if (!Y) return tl::fail(TL_EINVAL, "NULL lattice");
     if (n < 0 || !isfinite(dt) || dt == 0.0) return tl::fail(TL_EINVAL, "n >= 0 and a finite nonzero dt needed");
@@ -687,6 +688,7 @@ int tl_su2_step(tl_su2 *Y, int n, double dt)
 
 int tl_su2_measure(tl_su2 *Y, double *out4)
 {
+    tl::NvtxScope nvtx_range("tl_su2_measure");
     tl::set_error(TL_OK, "", "");
     if (!Y || !out4) return tl::fail(TL_EINVAL, "NULL argument");
     const size_t n3 = (size_t)Y->N * Y->N * Y->N;

@@ -84,10 +84,19 @@ class JobResult:
     hubble_resid: float
     spectrum: np.ndarray          # binned P_b of field 0 at the last step
     state: Optional[Tuple[np.ndarray, np.ndarray]] = None  # (phi, pi) [field, z, y, x] if kept
+    status: str = "done"          # "done", "failed" (its lattice could not be set up) or "cancelled"
+    error: str = ""               # the library's message for a failed job
 
     @property
     def latency(self) -> float:
         return self.finished - self.arrival
+
+
+def _no_result(spec: JobSpec, admitted: float, finished: float, status: str, error: str = "") -> JobResult:
+    """The result of a job that did not run to its end."""
+    nan = float("nan")
+    return JobResult(spec.job_id, spec.arrival, admitted, finished, np.zeros(0), nan, nan, nan, np.zeros(0), None,
+                     status, error)
 
 
 def job_cost(spec: JobSpec) -> float:
@@ -110,11 +119,15 @@ def _new_lattice(spec: JobSpec, stream: int, shape: str = "served") -> T.Lattice
     if shape not in ("served", "default"):
         raise ValueError(f"unknown shape {shape!r}")
     lat = T.Lattice(spec.N, spec.kIR, spec.n_fields, spec.dtype, True, 1.0, 1.0, 1.0, stream=stream)
-    if shape == "served" and is_batched(spec):
-        lat.set_pass_config(**T.batch_pass_config(spec.N, spec.n_fields, spec.dtype))
-    lat.set_potential(1.0, spec.q, (0.0, 0.0, 0.0))
-    meff2 = (3.0,) + (spec.q,) * (spec.n_fields - 1)
-    lat.init_fluctuations(spec.seed, A=spec.A, meff2=meff2, phi0=(1.0, 0.0, 0.0))
+    try:
+        if shape == "served" and is_batched(spec):
+            lat.set_pass_config(**T.batch_pass_config(spec.N, spec.n_fields, spec.dtype))
+        lat.set_potential(1.0, spec.q, (0.0, 0.0, 0.0))
+        meff2 = (3.0,) + (spec.q,) * (spec.n_fields - 1)
+        lat.init_fluctuations(spec.seed, A=spec.A, meff2=meff2, phi0=(1.0, 0.0, 0.0))
+    except BaseException:
+        lat.close()
+        raise
     return lat
 
 
@@ -173,6 +186,7 @@ class Server:
         self._streams: list = []  # streams of closed solo lanes, reused
         self.used = 0
         self.lane_log: List[tuple] = []
+        self.cancelled: set = set()  # resident jobs to drop when their lane is next idle
 
     @property
     def active(self) -> List[_Active]:
@@ -195,7 +209,10 @@ class Server:
             self.lanes[key] = _Lane(key, stream, is_batched(spec), float(spec.dt), spec.integrator)
         return self.lanes[key]
 
-    def admit(self, spec: JobSpec, now: float) -> None:
+    def admit(self, spec: JobSpec, now: float) -> Optional[JobResult]:
+        """Make the job resident.  If the library cannot set up its lattice (a
+        device allocation that fails, say) the job is not admitted and its
+        "failed" result is returned; otherwise None."""
         if spec.steps % self.chunk != 0:
             raise ValueError(f"job {spec.job_id}: steps must be a multiple of {self.chunk}")
         if spec.integrator not in T.INTEGRATORS:
@@ -205,9 +222,22 @@ class Server:
         if not is_batched(spec) and self.lane_key(spec) in self.lanes:
             raise ValueError(f"job id {spec.job_id} is already resident")
         lane = self.lane_of(spec)
-        lat = _new_lattice(spec, lane.stream.cuda_stream, "served")
+        try:
+            lat = _new_lattice(spec, lane.stream.cuda_stream, "served")
+        except T.TLError as e:
+            if not lane.jobs and not lane.batched:  # the solo lane opened for this job
+                self._streams.append(lane.stream)
+                del self.lanes[self.lane_key(spec)]
+            return _no_result(spec, now, now, "failed", str(e))
         lane.jobs.append(_Active(spec, lat, 0, now))
         self.used += spec.budget_bytes()
+        return None
+
+    def cancel(self, job_id: int) -> None:
+        """Drop a resident job: at the next service of its lane, once any chunk
+        in flight is done, its lattice is destroyed, its memory returned and a
+        "cancelled" result reported (a "done" one if that chunk was its last)."""
+        self.cancelled.add(job_id)
 
     def service(self, t0: float) -> List[JobResult]:
         """Reap finished jobs of idle lanes and start their next chunk.  Returns
@@ -223,14 +253,18 @@ class Server:
             for a in lane.inflight:
                 a.done_steps += self.chunk
             lane.inflight = []
-            finished = [a for a in lane.jobs if a.done_steps >= a.spec.steps]
+            finished = [a for a in lane.jobs if a.done_steps >= a.spec.steps or a.spec.job_id in self.cancelled]
             if finished:
-                lane.jobs = [a for a in lane.jobs if a.done_steps < a.spec.steps]
+                lane.jobs = [a for a in lane.jobs if a not in finished]
                 if lane.batch is not None:
                     lane.batch.close()
                     lane.batch, lane.members = None, ()
                 for a in finished:
-                    done.append(_result(a.spec, a.lat, a.admitted, t0, self.clock, self.keep_state))
+                    self.cancelled.discard(a.spec.job_id)
+                    if a.done_steps >= a.spec.steps:  # a job that completed before its cancel is done
+                        done.append(_result(a.spec, a.lat, a.admitted, t0, self.clock, self.keep_state))
+                    else:
+                        done.append(_no_result(a.spec, a.admitted, self.clock() - t0, "cancelled"))
                     a.lat.close()
                     self.used -= a.spec.budget_bytes()
             if not lane.jobs:
@@ -267,23 +301,41 @@ class Server:
 
 
 def serve(jobs: List[JobSpec], budget_bytes: int, chunk: int = 100,
-          clock: Callable[[], float] = time.perf_counter, keep_state: bool = False, log: Optional[list] = None):
+          clock: Callable[[], float] = time.perf_counter, keep_state: bool = False, log: Optional[list] = None,
+          cancel: Optional[List[Tuple[float, int]]] = None):
     """Run ``jobs`` (sorted by arrival) through a continuous-batching server in
-    real time.  Returns (results in completion order, makespan seconds); with
+    real time.  Returns (results in completion order, makespan seconds); every
+    job gives one result, "done", "failed" or "cancelled".  ``cancel``: (time,
+    job id) requests, applied when their time has come (a job not yet admitted
+    is dropped at once, a resident one at its lane's next idle point).  With
     ``log`` a list, the server's lane_log is appended to it."""
     srv = Server(budget_bytes, chunk, clock, keep_state)
     pending = sorted(jobs, key=lambda j: j.arrival)
     for j in pending:
         if j.budget_bytes() > budget_bytes:
             raise ValueError(f"job {j.job_id} alone exceeds the budget")
+    requests = sorted(cancel or [])
+    dropped: set = set()
     t0 = clock()
     results: List[JobResult] = []
     i = 0
     try:
         while len(results) < len(jobs):
             now = clock() - t0
-            while i < len(pending) and pending[i].arrival <= now and srv.fits(pending[i]):
-                srv.admit(pending[i], now)
+            while requests and requests[0][0] <= now:
+                _, jid = requests.pop(0)
+                if any(j.job_id == jid for j in pending[i:]):
+                    dropped.add(jid)
+                elif any(a.spec.job_id == jid for a in srv.active):
+                    srv.cancel(jid)
+            while i < len(pending) and (pending[i].job_id in dropped or
+                                        (pending[i].arrival <= now and srv.fits(pending[i]))):
+                if pending[i].job_id in dropped:
+                    results.append(_no_result(pending[i], now, now, "cancelled"))
+                else:
+                    failed = srv.admit(pending[i], now)
+                    if failed is not None:
+                        results.append(failed)
                 i += 1
             got = srv.service(t0)
             results.extend(got)

@@ -59,6 +59,10 @@ class tl_energies_t(ctypes.Structure):
                 ("hubble_resid", ctypes.c_double)]
 
 
+class tl_clock(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("time", ctypes.c_double), ("langevin_steps", ctypes.c_int64)]
+
+
 PASS_STREAM, PASS_TMA = 0, 1
 PASS_KINDS = {"stream": PASS_STREAM, "tma": PASS_TMA}
 
@@ -93,6 +97,8 @@ _SIGS = {
     "tl_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
     "tl_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
     "tl_set_background": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+    "tl_get_clock": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_clock)]),
+    "tl_set_clock": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tl_clock)]),
     "tl_state_device_ptr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_void_p)]),
     "tl_energies_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
@@ -240,6 +246,17 @@ def tl_set_state(h, field: int, which: int, arr: np.ndarray):
 
 def tl_set_background(h, a: float, b: float, from_constraint: bool):
     _check(lib().tl_set_background(h, a, b, int(bool(from_constraint))))
+
+
+def tl_get_clock(h) -> tl_clock:
+    c = tl_clock()
+    _check(lib().tl_get_clock(h, ctypes.byref(c)))
+    return c
+
+
+def tl_set_clock(h, step: int, time: float, langevin_steps: int = 0):
+    c = tl_clock(step, time, langevin_steps)
+    _check(lib().tl_set_clock(h, ctypes.byref(c)))
 
 
 def tl_state_device_ptr(h, field: int, which: int) -> int:
@@ -454,6 +471,7 @@ class Lattice:
         self.np_dtype = np.float32 if dtype == "f32" else np.float64
         ex = tl_expansion(int(bool(expanding)), alpha, fstar_over_mp, a0)
         self.h = tl_lattice_create(N, kIR, n_fields, DTYPES[dtype], ex, stream)
+        self.potential = None  # (lambda, q, m2) once set
 
     def close(self):
         if getattr(self, "h", None):
@@ -474,6 +492,7 @@ class Lattice:
 
     def set_potential(self, lam: float = 1.0, q: float = 0.0, m2=(0.0, 0.0, 0.0)):
         tl_set_potential(self.h, lam, q, m2)
+        self.potential = (float(lam), float(q), tuple(float(v) for v in _f3(m2)))
 
     def init_fluctuations(self, seed: int, A: float = 1e-10, meff2=(3.0, 0, 0), phi0=(1.0, 0, 0), pi0=(0, 0, 0),
                           fluct_pi: bool = False, fixed_modulus: bool = False):
@@ -507,6 +526,40 @@ class Lattice:
             tl_set_state(self.h, f, 1, np.ascontiguousarray(pi[f], dtype=self.np_dtype))
         tl_set_background(self.h, a, b, b_from_constraint)
 
+    def clock(self) -> dict:
+        """Completed steps and program time since the state was set, and Langevin steps."""
+        c = tl_get_clock(self.h)
+        return {"step": c.step, "time": c.time, "langevin_steps": c.langevin_steps}
+
+    def set_clock(self, step: int, time: float = 0.0, langevin_steps: int = 0):
+        tl_set_clock(self.h, step, time, langevin_steps)
+
+    def checkpoint(self) -> dict:
+        """What a resumed run needs: the lattice's size, fields, precision and
+        kIR (checked on restore), the potential, the pass shape, the state at
+        the current integer time, a, a' and the clock (see tl_set_clock)."""
+        E = self.energies()
+        phi, pi = self.get_all()
+        ck = {"N": self.N, "n_fields": self.nf, "dtype": self.dtype, "kIR": self.kIR, "phi": phi, "pi": pi,
+              "a": E.a, "b": E.b, "pass_config": self.pass_config(), **self.clock()}
+        if self.potential is not None:
+            ck["potential"] = self.potential
+        return ck
+
+    def restore(self, ck: dict):
+        """Continue from ``checkpoint()`` of a lattice created with the same
+        arguments: the same tl_step calls then give bitwise its results."""
+        for key, mine in (("N", self.N), ("n_fields", self.nf), ("dtype", self.dtype), ("kIR", self.kIR)):
+            if ck[key] != mine:
+                raise ValueError(f"checkpoint {key} {ck[key]!r} does not match the lattice's {mine!r}")
+        if ck.get("potential") is not None:
+            lam, q, m2 = ck["potential"]
+            self.set_potential(lam, q, m2)
+        if ck["pass_config"] != self.pass_config():
+            self.set_pass_config(**ck["pass_config"])
+        self.set_state(ck["phi"], ck["pi"], ck["a"], ck["b"], b_from_constraint=False)
+        self.set_clock(int(ck["step"]), float(ck["time"]), int(ck["langevin_steps"]))
+
     def device_ptr(self, field: int, which: int) -> int:
         return tl_state_device_ptr(self.h, field, which)
 
@@ -526,3 +579,34 @@ class Lattice:
     def pass_config(self) -> dict:
         """The launch shape in use, automatic values resolved."""
         return tl_get_pass_config(self.h)
+
+
+def save_checkpoint(path, ck: dict):
+    """Write a ``Lattice.checkpoint()`` to an .npz file (no pickled objects)."""
+    flat = {k: v for k, v in ck.items() if k not in ("potential", "pass_config")}
+    if ck.get("potential") is not None:
+        lam, q, m2 = ck["potential"]
+        flat["potential"] = np.array([lam, q, *m2])
+    pc = ck["pass_config"]
+    flat["pass_config_kind"] = pc["kind"]
+    flat["pass_config"] = np.array([pc[k] for k in _PASS_INTS], dtype=np.int64)
+    np.savez(path, **flat)
+
+
+def load_checkpoint(path) -> dict:
+    """Read a checkpoint written by ``save_checkpoint``."""
+    with np.load(path, allow_pickle=False) as z:
+        ck = {k: z[k] for k in z.files}
+    out = {"N": int(ck["N"]), "n_fields": int(ck["n_fields"]), "dtype": str(ck["dtype"]), "kIR": float(ck["kIR"]),
+           "phi": ck["phi"], "pi": ck["pi"], "a": float(ck["a"]), "b": float(ck["b"]), "step": int(ck["step"]),
+           "time": float(ck["time"]), "langevin_steps": int(ck["langevin_steps"])}
+    pc = {k: int(v) for k, v in zip(_PASS_INTS, ck["pass_config"])}
+    pc["kind"] = str(ck["pass_config_kind"])
+    out["pass_config"] = pc
+    if "potential" in ck:
+        p = ck["potential"]
+        out["potential"] = (float(p[0]), float(p[1]), tuple(float(v) for v in p[2:]))
+    return out
+
+
+_PASS_INTS = ("warps", "stages", "z_chunk", "tile_x", "threads")

@@ -95,8 +95,9 @@ def test_default_shape_and_errors():
         with T.Lattice(512, 0.5, 1, "f32") as mid:  # 96-plane chunks around 512
             c3 = mid.pass_config()
             assert (c3["kind"], c3["warps"], c3["z_chunk"]) == ("tma", 7, 96)
-        with T.Lattice(256, 0.5, 2, "f64") as f64:  # FP64: the streaming pass
-            assert f64.pass_config()["kind"] == "stream"
+        with T.Lattice(256, 0.5, 2, "f64") as f64:  # FP64: the streaming pass, 32-plane chunks from 128
+            c4 = f64.pass_config()
+            assert (c4["kind"], c4["z_chunk"]) == ("stream", 32)
         bad = [dict(kind="tma", warps=8), dict(kind="tma", stages=2), dict(kind="tma", stages=9),
                dict(kind="tma", tile_x=16), dict(kind="stream", warps=7), dict(kind="stream", tile_x=12),
                dict(kind="stream", threads=128), dict(kind="stream", z_chunk=193)]

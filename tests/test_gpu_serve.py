@@ -13,7 +13,10 @@
   parity tolerances (FP64 1e-12, FP32 1e-5, FP32 momenta ``f32_pi_tol``;
   Hubble residual as ``check_hubble``).
 - The plain loop on the library's default shapes agrees with the served
-  results within the same tolerances."""
+  results within the same tolerances.
+- Cancelling resident jobs (one in a batched lane, one solo) mid-run leaves
+  every other job bitwise equal to the job run alone, and every cancelled
+  lattice's memory returned."""
 import numpy as np
 import pytest
 
@@ -48,7 +51,7 @@ def test_served_results_equal_alone_and_budget_respected():
     orig_admit = S.Server.admit
 
     def admit(self, spec, now):
-        orig_admit(self, spec, now)
+        assert orig_admit(self, spec, now) is None
         peak["used"] = max(peak["used"], self.used)
         assert self.used <= self.budget
     S.Server.admit = admit
@@ -109,3 +112,42 @@ def test_served_jobs_match_the_oracle():
         assert np.max(np.abs(r.energies - oE)) / float(np.sum(oE)) < tol, (j.job_id, r.energies, oE)
         assert abs(r.a - oa) / oa < tol and abs(r.b - ob) / abs(ob) < tol, (j.job_id, r.a, oa, r.b, ob)
         check_hubble(p, r.hubble_resid, r.energies, r.a, r.b, oE, oa, ob)
+
+
+def test_cancelled_jobs_leave_the_others_bitwise_unchanged():
+    """All jobs resident at once; after the first chunk is started, one job of a
+    batched lane and one solo job are cancelled.  Their lanes go on without them
+    (the batch rebuilt), and every other job is bitwise the job run alone."""
+    import time
+    import torch
+    jobs = mixed_jobs()
+    small = [j for j in jobs if S.is_batched(j) and j.steps >= 200][0]
+    solo = [j for j in jobs if not S.is_batched(j) and j.steps >= 200][0]
+    lane_mates = [j for j in jobs if S.is_batched(j) and j.job_id != small.job_id
+                  and S.Server.lane_key(j) == S.Server.lane_key(small)]
+    assert lane_mates, "the cancelled batched job must share its lane"
+    srv = S.Server(sum(j.budget_bytes() for j in jobs), chunk=100)
+    results = []
+    try:
+        for j in jobs:
+            assert srv.admit(j, 0.0) is None
+        t0 = time.perf_counter()
+        results += srv.service(t0)  # every lane's first chunk is in flight
+        srv.cancel(small.job_id)
+        srv.cancel(solo.job_id)
+        while len(results) < len(jobs):
+            results += srv.service(t0)
+        assert srv.used == 0
+    finally:
+        srv.close()
+    torch.cuda.synchronize()
+    status = {r.job_id: r.status for r in results}
+    assert status.pop(small.job_id) == "cancelled" and status.pop(solo.job_id) == "cancelled"
+    assert set(status.values()) == {"done"}
+    alone = {r.job_id: r for r in S.run_alone([j for j in jobs if j.job_id in status], chunk=100,
+                                              shape="served")[0]}
+    for r in results:
+        if r.job_id in status:
+            a = alone[r.job_id]
+            assert np.array_equal(r.energies, a.energies), r.job_id
+            assert r.a == a.a and r.b == a.b

@@ -1,7 +1,7 @@
 """The serving loop's host logic on the CPU: admission by budget in arrival
 order, batched lanes per (precision, dt, integrator) and solo lanes for big
 jobs, the step size and integrator each job is advanced with, reaping, batch
-rebuilds and clean-up, with the device calls (lattices, batches, streams,
+rebuilds and clean-up, failed and cancelled jobs, with the device calls (lattices, batches, streams,
 events) replaced by fakes that record what the server asks of them."""
 import types
 
@@ -118,7 +118,7 @@ def test_serve_loop_completes_every_job_within_budget(fakes, monkeypatch):
     orig_admit = S.Server.admit
 
     def admit(self, spec, now):
-        orig_admit(self, spec, now)
+        assert orig_admit(self, spec, now) is None
         used_after_admit.append(self.used)
         admitted_ids.append(spec.job_id)
         for key, lane in self.lanes.items():  # batched lanes: one precision, dt, integrator; solo: one job
@@ -237,3 +237,69 @@ def test_lane_overlap_accounting():
     assert abs(o["any_lane_busy"] - 5.0 / 8.0) < 1e-12
     assert abs(o["two_or_more_lanes_busy"] - 2.0 / 8.0) < 1e-12
     assert o["busy_s_by_lane_kind"] == {"solo": 5.0, "batch-f32": 2.0}
+
+
+def test_a_job_whose_lattice_cannot_be_set_up_fails_alone(fakes, monkeypatch):
+    """A lattice creation that the library refuses (a failed device
+    allocation, say) gives that job a "failed" result with the library's
+    message; its budget is never taken, the lane it opened is dropped and every
+    other job still runs to its end."""
+    jobs = _jobs()[:10]
+    doomed = {jobs[2].job_id, jobs[5].job_id}
+    seeds = {j.seed: j.job_id for j in jobs}
+
+    class Refusing(FakeLattice):
+        def init_fluctuations(self, seed, A, meff2, phi0):
+            if seeds[seed] in doomed:
+                raise realT.TLError(-3, "cudaMalloc: out of memory")
+            super().init_fluctuations(seed, A, meff2, phi0)
+
+    fakes.TLError = realT.TLError
+    fakes.Lattice = Refusing
+    budget = max(j.budget_bytes() for j in jobs) * 3
+    log = []
+    results, _ = S.serve(jobs, budget, chunk=100, log=log)
+    assert sorted(r.job_id for r in results) == [j.job_id for j in jobs]
+    by_id = {r.job_id: r for r in results}
+    steps = {j.job_id: j.steps for j in jobs}
+    for jid, r in by_id.items():
+        if jid in doomed:
+            assert r.status == "failed" and "out of memory" in r.error and r.energies.size == 0
+        else:
+            assert r.status == "done" and r.energies[0] == steps[jid]
+    assert all(lat.closed for lat in FakeLattice.created)  # the refused lattices too
+    assert not any(key == ("solo", jid) for key, _, _ in log for jid in doomed)
+
+
+def test_cancelled_jobs_release_their_memory(fakes, monkeypatch):
+    """A cancel request drops a waiting job at once and a resident one at its
+    lane's next idle point: the lattice is closed, its budget returned, the
+    batch rebuilt without it, and the job reported "cancelled"; the others are
+    unaffected."""
+    jobs = S.poisson_jobs(12, seed=3, rate=1e6, sizes=(32, 64), steps=(600, 1000))
+    budget = max(j.budget_bytes() for j in jobs) * 2  # the first jobs are resident, the rest wait
+    ticks = iter(range(10 ** 9))
+    clock = lambda: next(ticks) * 1e-3  # noqa: E731
+    resident, waiting = jobs[1].job_id, jobs[-1].job_id
+    used = []
+    orig = S.Server.service
+
+    def service(self, t0):
+        out = orig(self, t0)
+        used.append(self.used)
+        assert 0 <= self.used <= budget
+        return out
+
+    monkeypatch.setattr(S.Server, "service", service)
+    results, _ = S.serve(jobs, budget, chunk=100, clock=clock, cancel=[(0.004, resident), (0.004, waiting)])
+    by_id = {r.job_id: r for r in results}
+    assert sorted(by_id) == sorted(j.job_id for j in jobs)
+    assert by_id[resident].status == "cancelled" and by_id[waiting].status == "cancelled"
+    lat_of = {lat.seed: lat for lat in FakeLattice.created}
+    seed = {j.job_id: j.seed for j in jobs}
+    assert seed[waiting] not in lat_of  # never admitted
+    assert lat_of[seed[resident]].closed and lat_of[seed[resident]].steps < jobs[1].steps
+    for j in jobs:
+        if j.job_id not in (resident, waiting):
+            assert by_id[j.job_id].status == "done" and by_id[j.job_id].energies[0] == j.steps
+    assert used[-1] == 0 and all(lat.closed for lat in FakeLattice.created)
