@@ -437,7 +437,12 @@ void tl_batch_destroy(tl_batch *batch);
 int tl_autotune(tl_lattice *lat, double *best_ms_per_pass);
 
 /* Set the launch shape of lat's fused pass (takes effect at the next launch;
- * the lattice's state is untouched).  Values out of range are TL_EINVAL;
+ * the lattice's state is untouched).  tl_pass_config fields: tile_x 0, 8, 16
+ * or 32 (threads along x of the streaming kernel's tiles; a lattice whose rows
+ * need fewer threads, N/4 FP32 or N/2 FP64 below 32, also takes that count,
+ * as tl_get_pass_config reports it), threads 0, 256 or 512, TMA warps 0, 7 or
+ * 15, stages 0 or 3..8, z_chunk 0..N (0: automatic), so every shape
+ * tl_get_pass_config returns can be set again.  Values out of range are TL_EINVAL;
  * TL_ESTATE while the lattice is in a batch.  May synchronise the lattice
  * stream (to grow its reduction slots).  A new lattice starts on TL_PASS_TMA
  * when it is FP32 and N >= 192 (z-chunks of 16 planes at N = 192, 64 up to

@@ -711,12 +711,16 @@ int tl_set_pass_config(tl_lattice *L, const tl_pass_config *cfg)
         t.cwarps = cfg->warps ? cfg->warps : 7;
         t.stages = cfg->stages;
     } else {
-        if (cfg->tile_x != 0 && cfg->tile_x != 8 && cfg->tile_x != 16 && cfg->tile_x != 32)
-            return fail(TL_EINVAL, "tile_x must be 0, 8, 16 or 32");
+        // a row narrower than 32 threads: its own width is what
+        // tl_get_pass_config reports for the widths above it, and means the same
+        const int per_row = L->N / (int)(16 / L->esz);
+        const bool own_row = per_row < 32 && cfg->tile_x == per_row;
+        if (cfg->tile_x != 0 && cfg->tile_x != 8 && cfg->tile_x != 16 && cfg->tile_x != 32 && !own_row)
+            return fail(TL_EINVAL, "tile_x must be 0, 8, 16, 32 or the lattice's row width in threads (N/4 FP32, N/2 FP64) below 32");
         if (cfg->threads != 0 && cfg->threads != 256 && cfg->threads != 512)
             return fail(TL_EINVAL, "threads must be 0, 256 or 512");
         if (cfg->warps != 0 || cfg->stages != 0) return fail(TL_EINVAL, "warps and stages apply to TL_PASS_TMA");
-        t.txt = cfg->tile_x;
+        t.txt = own_row ? 0 : cfg->tile_x;
         t.threads = cfg->threads ? cfg->threads : 256;
     }
     return tl::set_geometry(L, t);

@@ -167,3 +167,19 @@ def test_ragged_at_scale_tma_default_equals_stream():
             lat.step(2, 0.01, "verlet")
             out.append(lat.get_all())
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_every_reported_shape_can_be_set_again():
+    """tl_get_pass_config's resolved shape (automatic values filled in, a row
+    narrower than the requested tile width reported as its own width) is
+    accepted by tl_set_pass_config and gives the same shape: what a checkpoint
+    restores."""
+    for N, dtype in ((16, "f32"), (48, "f32"), (100, "f32"), (256, "f32"), (12, "f64"), (40, "f64"), (96, "f64")):
+        for shape in [None] + SHAPES:
+            with T.Lattice(N, 0.5, 2, dtype) as lat:
+                if shape is not None:
+                    lat.set_pass_config(**shape)
+                cfg = lat.pass_config()
+            with T.Lattice(N, 0.5, 2, dtype) as other:
+                other.set_pass_config(**cfg)
+                assert other.pass_config() == cfg, (N, dtype, shape, cfg, other.pass_config())
