@@ -132,11 +132,12 @@ int tl_lattice_create_with_buffers(tl_lattice **out, int N, double kIR, int n_fi
 size_t tl_state_bytes(int N, int n_fields, tl_dtype dtype);
 
 /* Device layout of one field array of a lattice (Sec. 3.3: row-major on
- * every device; Sec. 3.1 and Sec. 4: one ghost layer).  Every row carries W =
- * 16/sizeof ghost elements on each side (x in [-W, 0) and [N, N + W)) and
- * every z-plane one ghost row above and below: one-site ghost copies of the
- * periodic neighbours, kept current by every pass, so that a tile plus its
- * halo is one in-bounds box.  Element (x, y, z) is at
+ * every device; Sec. 3.1 and Sec. 4: one ghost layer).  Every z-plane carries
+ * one ghost row above and below (copies of rows N - 1 and 0, kept current by
+ * every pass), so that a tile's rows plus the rows around it are one in-bounds
+ * box; every row has W = 16/sizeof reserved elements on each side (x in
+ * [-W, 0) and [N, N + W)), which the library does not keep (at the x-edges the
+ * pass reads the periodic image itself).  Element (x, y, z) is at
  * origin + z plane_pitch + y row_pitch + x; rows start x = 0 on a 128-byte
  * boundary (a left pad of 128 bytes) and row_pitch is a multiple of 128
  * bytes; plane_pitch = (N + 2) row_pitch, origin = row_pitch + 128/sizeof,
@@ -251,7 +252,7 @@ int tl_state_device_ptr(tl_lattice *lat, int field, int which, void **dev_ptr);
  * The caller has written every phi_f and pi_f of the current state directly on
  * the device (through tl_state_device_ptr or its own buffers of
  * tl_lattice_create_with_buffers, interior sites in the padded layout): refresh
- * their ghost copies and take them as the state, like tl_set_state of every
+ * their ghost rows and take them as the state, like tl_set_state of every
  * array without a host copy (step and time reset to 0, a = a0, b = 0; call
  * tl_set_background afterwards when expanding).  Synchronises the lattice
  * stream (the caller's writes must be ordered before the call on that stream

@@ -142,23 +142,21 @@ int refresh_groups(tl_batch *B)
             // one CTA per item; the ring as deep as two CTAs per SM allow for the
             // largest box among the members; each member's tensor maps (both
             // buffer parities) copied to device memory for the kernel to read
-            int wmax = 0, hmax = 0;
+            int txt_max = 0, ty_max = 0;
             std::vector<tl::TmaMaps> maps;
             for (int i : g.idx) {
                 tl_lattice *L = B->lats[i];
-                const int W = (int)(16 / L->esz);
-                wmax = std::max(wmax, L->geom.txt * W + 2 * W);
-                hmax = std::max(hmax, L->geom.ty + 2);
+                txt_max = std::max(txt_max, L->geom.txt);
+                ty_max = std::max(ty_max, L->geom.ty);
                 int rc = tl::lattice_tma_maps(L);
                 if (rc) return rc;
                 maps.push_back(L->maps[0]);
                 maps.push_back(L->maps[1]);
             }
-            const int esz = B->dtype == TL_F64 ? 8 : 4;
             int S = 8;
-            while (S > 3 && tl::tma_group_smem(esz, g.nf, S, wmax, hmax) > 113u * 1024u) --S;
+            while (S > 3 && tl::tma_group_smem(g.nf, S, txt_max, ty_max) > 113u * 1024u) --S;
             g.stages = S;
-            g.smem = tl::tma_group_smem(esz, g.nf, S, wmax, hmax);
+            g.smem = tl::tma_group_smem(g.nf, S, txt_max, ty_max);
             g.grid = (int)g.total;
             TB_CK(cudaMemcpyAsync(g.d_maps, maps.data(), maps.size() * sizeof(tl::TmaMaps), cudaMemcpyHostToDevice,
                                   B->stream));

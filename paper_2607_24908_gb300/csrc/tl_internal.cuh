@@ -43,11 +43,13 @@ struct Scalars {
 // Scalar constants of a lattice/model passed by value to every pass.
 // Field arrays are addressed from their element (0, 0, 0) as
 // z * pplane + y * pitch + x.  A dense array has pitch = N, pplane = N^2;
-// the lattice's own arrays carry ghost copies (ghosts = 1): W = 16/sizeof(T)
-// elements left and right of every row (x in [-W, 0) and [N, N + W)) and one
-// row above and below every z-plane, which every pass keeps current for the
-// sites it writes; rows are padded to a multiple of 128 bytes with x = 0 on a
-// 128-byte boundary, pplane = (N + 2) pitch.
+// the lattice's own arrays carry ghost rows (ghosts = 1): one row above and
+// below every z-plane, copies of rows N - 1 and 0 that every pass keeps
+// current for the sites it writes, and W = 16/sizeof(T) reserved elements
+// left and right of every row (x in [-W, 0) and [N, N + W); not kept: the TMA
+// pass takes the x-halo at the lattice's x-edges from the periodic image);
+// rows are padded to a multiple of 128 bytes with x = 0 on a 128-byte
+// boundary, pplane = (N + 2) pitch.
 struct Model {
     int N;
     int nf;
@@ -96,12 +98,35 @@ struct PassTuning {
     int txt;      // ldg: threads along x per tile row, 32 (default), 16 or 8
 };
 
-// Tensor maps of the input arrays of a TMA pass: [2 f + a], a = 0 phi, 1 pi,
-// each 3-D over the padded array (x incl. pads, rows incl. ghost rows, planes)
-// with the pass's tile-plus-halo box.
+// Tensor maps of the input arrays of a TMA pass: map[k][2 f + a], a = 0 phi,
+// 1 pi, each 3-D over the padded array (x incl. pads, rows incl. ghost rows,
+// planes), one plane deep and ty + 2 rows high, txt W + 2W sites wide for
+// k = kMapTile (a tile with its x-halo: tiles inside the lattice), txt W for
+// kMapBody (the tile alone) and W for kMapSide (one halo column: tiles at an
+// x-edge of the lattice, whose halo on the far side of the edge is the
+// periodic image).
+constexpr int kMapTile = 0, kMapBody = 1, kMapSide = 2;
 struct TmaMaps {
-    CUtensorMap map[2 * kMaxFields];
+    CUtensorMap map[3][2 * kMaxFields];
 };
+
+// Bytes of one array's slot in a stage of the TMA ring (128-byte aligned
+// parts; W sizeof(T) = 16 bytes in both precisions): a tile-plus-halo box
+// ((ty + 2) x (txt + 2) 16-byte words), or at an x-edge the body box
+// ((ty + 2) x txt words) followed by the left and right halo columns
+// ((ty + 2) words each) at tma_side_offset(.., 0) and (.., 1).
+__host__ __device__ constexpr size_t tma_r128(size_t b) { return (b + 127) / 128 * 128; }
+__host__ __device__ constexpr size_t tma_side_offset(int txt, int ty, int side)
+{
+    return side == 0 ? tma_r128((size_t)(ty + 2) * txt * 16)
+                     : tma_r128(tma_r128((size_t)(ty + 2) * txt * 16) + (size_t)(ty + 2) * 16);
+}
+__host__ __device__ constexpr size_t tma_slot_bytes(int txt, int ty)
+{
+    return tma_r128((size_t)(ty + 2) * (txt + 2) * 16 > tma_side_offset(txt, ty, 1) + (size_t)(ty + 2) * 16
+                        ? (size_t)(ty + 2) * (txt + 2) * 16
+                        : tma_side_offset(txt, ty, 1) + (size_t)(ty + 2) * 16);
+}
 
 // Launch geometry of the fused pass.
 struct PassGeom {
@@ -153,10 +178,9 @@ cudaError_t launch_group(int dtype, int nf, int variant, int prefetch, int stage
                          const unsigned *first_item, int njobs, unsigned total, const PassCoef &c, int grid,
                          cudaStream_t s);
 
-// Shared memory a TMA group launch needs: `stages` stages of 2 nf boxes of at
-// most (ty + 2) x (txt W + 2W) elements (128-byte aligned regions), for the
-// largest (txt, ty) among its jobs.
-size_t tma_group_smem(int elem_bytes, int nf, int stages, int max_txt_w_plus_2w, int max_ty_plus_2);
+// Shared memory a TMA group launch needs: `stages` stages of 2 nf slots
+// (tma_slot_bytes) for the largest txt and ty among its jobs.
+size_t tma_group_smem(int nf, int stages, int max_txt, int max_ty);
 
 // Enqueue one fused pass (measure_only: energies of the stored state, no writes).
 cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const PassCoef &c, const PassGeom &g,
@@ -166,7 +190,7 @@ cudaError_t launch_pass(int dtype, const Model &m, const FieldPtrs &fp, const Pa
 // Record msg+detail as this thread's tl_last_error() text; returns code.
 int set_error(int code, const char *msg, const char *detail);
 
-// Refresh the ghost copies of one padded array from its interior.
+// Refresh the ghost rows of one padded array from its interior.
 cudaError_t launch_fill_ghosts(int dtype, void *origin, int N, long long P, long long PP, cudaStream_t s);
 
 // Set a, b (and the derived weights) on the device; drift = 0.

@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(256) langevin_pass(const T *__restrict__ in, T
     const size_t NN = (size_t)PP;
     const size_t row = (size_t)y * P, rowm = (size_t)(y == 0 ? N - 1 : y - 1) * P,
                  rowp = (size_t)(y + 1 == N ? 0 : y + 1) * P;
-    // ghost copies of this thread's sites (padded arrays carry one-site ghosts)
-    const long long gx = x0 == 0 ? (long long)N : (x0 + W == N ? -(long long)N : 0);
+    // ghost rows of this thread's sites (padded arrays carry one ghost row on
+    // each side of a plane; the x-edges need no copies)
     const long long gy = y == 0 ? (long long)N * P : (y == N - 1 ? -(long long)N * P : 0);
     const int xl = x0 == 0 ? N - 1 : x0 - 1, xr = x0 + W == N ? 0 : x0 + W;
     T zm[W], cu[W], zp[W];
@@ -147,7 +147,6 @@ __global__ void __launch_bounds__(256) langevin_pass(const T *__restrict__ in, T
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             out[pz + row + x0 + j] = o[j];
-            if (gx) out[pz + row + x0 + j + gx] = o[j];
             if (gy) out[pz + row + x0 + j + gy] = o[j];
         }
 #pragma unroll

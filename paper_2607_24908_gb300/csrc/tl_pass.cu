@@ -92,11 +92,8 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
     if (g.variant == kVariantTma) {
         // ring depth: as deep as fits two CTAs per SM (<= 113 KB each), at
         // least 3 (two planes read + one in flight), at most 8; each stage
-        // holds 2 nf boxes of (ty + 2) x (txt W + 2W) elements in 128-byte
-        // aligned regions.
-        const size_t box = (size_t)(g.ty + 2) * (g.txt * W + 2 * W) * (size_t)elem_bytes;
-        const size_t region = (box + 127) / 128 * 128;
-        const size_t per_stage = (size_t)nf * 2 * region;
+        // holds 2 nf slots of tma_slot_bytes.
+        const size_t per_stage = (size_t)nf * 2 * tma_slot_bytes(g.txt, g.ty);
         int S = t.stages > 0 ? t.stages : 8;
         if (S > 8) S = 8;
         // two CTAs per SM for 7 compute warps, one for 15
@@ -137,28 +134,13 @@ cudaError_t launch_group(int dtype, int nf, int variant, int prefetch, int stage
                : launch_group_f64(nf, variant, prefetch, stages, smem, jobs, first_item, njobs, total, c, grid, s);
 }
 
-size_t tma_group_smem(int elem_bytes, int nf, int stages, int max_txt_w_plus_2w, int max_ty_plus_2)
+size_t tma_group_smem(int nf, int stages, int max_txt, int max_ty)
 {
-    const size_t box = (size_t)max_ty_plus_2 * max_txt_w_plus_2w * (size_t)elem_bytes;
-    const size_t region = (box + 127) / 128 * 128;
-    return (size_t)stages * nf * 2 * region;
+    return (size_t)stages * nf * 2 * tma_slot_bytes(max_txt, max_ty);
 }
 
-// Refresh the ghost copies of one array (layout in tl_internal.cuh): the W
-// ghost elements left and right of every row, then the ghost rows above and
-// below every plane.
-template <typename T>
-__global__ void fill_ghosts_x(T *a, int N, long long P, long long PP, int W)
-{
-    const long long rows = (long long)N * N;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
-        T *row = a + (r / N) * PP + (r % N) * P;
-        for (int j = 0; j < W; ++j) {
-            row[-W + j] = row[N - W + j];
-            row[N + j] = row[j];
-        }
-    }
-}
+// Refresh the ghost rows of one array (layout in tl_internal.cuh): the rows
+// above and below every plane, copies of rows N - 1 and 0.
 template <typename T>
 __global__ void fill_ghosts_y(T *a, int N, long long P, long long PP)
 {
@@ -175,13 +157,10 @@ cudaError_t launch_fill_ghosts(int dtype, void *origin, int N, long long P, long
 {
     const long long n = (long long)N * N;
     const unsigned grid = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    if (dtype == TL_F32) {
-        fill_ghosts_x<float><<<grid, 256, 0, s>>>(static_cast<float *>(origin), N, P, PP, 4);
+    if (dtype == TL_F32)
         fill_ghosts_y<float><<<grid, 256, 0, s>>>(static_cast<float *>(origin), N, P, PP);
-    } else {
-        fill_ghosts_x<double><<<grid, 256, 0, s>>>(static_cast<double *>(origin), N, P, PP, 2);
+    else
         fill_ghosts_y<double><<<grid, 256, 0, s>>>(static_cast<double *>(origin), N, P, PP);
-    }
     return cudaGetLastError();
 }
 

@@ -367,40 +367,22 @@ __device__ __forceinline__ void cta_reduce_finalize(const double (&accd)[NQ], co
 __device__ __forceinline__ unsigned grid_bid() { return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z); }
 __device__ __forceinline__ unsigned grid_nblocks() { return gridDim.x * gridDim.y * gridDim.z; }
 
-// Ghost copies of this thread's W output sites: a site in the first or last
-// W columns also goes to the right or left ghost columns, a site in the first
-// or last row to the ghost row below or above the plane (corners not needed:
-// the 7-point stencil never reads them).  Column ghosts are written as whole
-// 32-byte sectors (the ghost word plus the unused pad word beside it) so that
-// the memory system never has to merge a partial sector.
+// Ghost rows of this thread's W output sites: a site in the first or last row
+// also goes to the ghost row below or above the plane (the x-edges need no
+// copies: the TMA pass reads the periodic image there).
 template <typename T, int NF, int W>
 __device__ __forceinline__ void store_ghosts(T *const (&pho)[NF], T *const (&pio)[NF], const T (&ph)[NF][W],
                                              const T (&pp)[NF][W], size_t pz, int x0, int y, int N, long long P)
 {
-    long long dx = 0, dy = 0;
-    bool left = false;
-    if (x0 == 0) dx = N;  // right ghost columns [N, N + W), pad [N + W, N + 2W)
-    else if (x0 + W == N) {
-        dx = -(long long)N;  // left ghost columns [-W, 0), pad [-2W, -W)
-        left = true;
-    }
-    if (y == 0) dy = (long long)N * P;    // ghost row after the last row
+    long long dy = 0;
+    if (y == 0) dy = (long long)N * P;  // ghost row after the last row
     else if (y == N - 1) dy = -(long long)N * P;
-    if (dx == 0 && dy == 0) return;
+    if (dy == 0) return;
     const size_t base = pz + (size_t)y * P + x0;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        if (dx) {
-            const long long o = (long long)base + dx;
-            store_vec_cs(pho[f] + o, ph[f]);
-            store_vec_cs(pio[f] + o, pp[f]);
-            store_vec_cs(pho[f] + (left ? o - W : o + W), ph[f]);  // fill the rest of the sector
-            store_vec_cs(pio[f] + (left ? o - W : o + W), pp[f]);
-        }
-        if (dy) {
-            store_vec_cs(pho[f] + base + dy, ph[f]);
-            store_vec_cs(pio[f] + base + dy, pp[f]);
-        }
+        store_vec_cs(pho[f] + base + dy, ph[f]);
+        store_vec_cs(pio[f] + base + dy, pp[f]);
     }
 }
 
@@ -723,14 +705,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 
 // ---- variant 2: tiled TMA staging on the ghost-padded layout ---------------------
 // Warps 0..CW-1 compute, warp CW produces.  A CTA owns a tile of txt W x ty
-// sites and a chunk of z-planes.  For every plane its producer lane issues one
-// 3-D tensor copy per array (cp.async.bulk.tensor: a box of txt W + 2W by ty + 2
-// sites and one plane, starting at the tile's left ghost column and the row
-// above it; with the ghost layer the box never wraps) into a ring of S stages,
-// completing on the stage's "full" mbarrier; consumers release a stage on its
-// "empty" mbarrier once they are done with it.  Consumers read the centre of
-// plane z+1 and the halo of plane z from shared memory and run the same
-// per-site update as the register-streaming variant.
+// sites and a chunk of z-planes.  For every plane its producer lane issues, per
+// array, 3-D tensor copies (cp.async.bulk.tensor) of ty + 2 rows (the tile's
+// rows and the rows above and below it; the ghost rows make this in-bounds at
+// the y-edges) into a ring of S stages, completing on the stage's "full"
+// mbarrier: a tile inside the lattice takes one box txt W + 2W sites wide (the
+// tile and its x-halo); a tile at an x-edge takes its body (txt W wide) and
+// the two W-wide columns that hold its left and right halo sites, the one on
+// the far side of the edge from the periodic image (x = N - W or 0), so no
+// copy reads past the lattice's rows.  Consumers release a stage on its
+// "empty" mbarrier once they are done with it; they read the centre of plane
+// z+1 and the halo of plane z from shared memory and run the same per-site
+// update as the register-streaming variant.
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
 {
@@ -781,9 +767,15 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
     const int z0 = bz * zc;
     const int z1 = min(z0 + zc, N);
     const int K = (z1 - z0) + 2;  // planes z0-1 .. z1
-    const int rowe = txt * W + 2 * W;
-    const uint32_t box_bytes = (uint32_t)((ty + 2) * rowe * sizeof(T));
-    const uint32_t region = (box_bytes + 127u) & ~127u;  // 128-byte aligned stage regions
+    // tile at an x-edge of the lattice: body box plus two halo columns, else
+    // one tile-plus-halo box; either way (ty + 2) (txt + 2) 16-byte words per
+    // array and plane
+    const bool edge = x_tile == 0 || x_tile + txt * W >= N;
+    const int rowe = edge ? txt * W : txt * W + 2 * W;  // row pitch of the staged body
+    const uint32_t box_bytes = (uint32_t)((ty + 2) * (txt + 2) * 16);
+    const uint32_t region = (uint32_t)tma_slot_bytes(txt, ty);  // one array's slot in a stage
+    const int side_l = (int)(tma_side_offset(txt, ty, 0) / sizeof(T));
+    const int side_r = (int)(tma_side_offset(txt, ty, 1) / sizeof(T));
     auto arr = [&](int s, int f, int a) -> T * {
         return reinterpret_cast<T *>(smem_raw + (size_t)((s * NF + f) * 2 + a) * region);
     };
@@ -807,10 +799,16 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
         if ((tid & 31) == 0) {
             if constexpr (GLOBAL_MAPS) {
 #pragma unroll
-                for (int i = 0; i < 2 * NF; ++i)
-                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->map[i])
-                                 : "memory");
+                for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+                    for (int i = 0; i < 2 * NF; ++i)
+                        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->map[kk][i])
+                                     : "memory");
             }
+            // source columns of the halo columns of an edge tile (16-byte aligned:
+            // W divides N and the tile offsets)
+            const int xl_src = x_tile == 0 ? N - W : x_tile - W;
+            const int xr_src = x_tile + txt * W >= N ? 0 : x_tile + txt * W;
             for (int k = 0; k < K; ++k) {
                 const int s = k % S;
                 if (k >= S && !mbar_wait_bounded(&empty[s], ((k / S) - 1) & 1u, sc)) {
@@ -823,8 +821,18 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
 #pragma unroll
                 for (int f = 0; f < NF; ++f)
 #pragma unroll
-                    for (int a = 0; a < 2; ++a)
-                        tma_load_3d(arr(s, f, a), &maps->map[2 * f + a], lpad + x_tile - W, y_tile, zg, &full[s]);
+                    for (int a = 0; a < 2; ++a) {
+                        T *dst = arr(s, f, a);
+                        if (!edge) {
+                            tma_load_3d(dst, &maps->map[kMapTile][2 * f + a], lpad + x_tile - W, y_tile, zg, &full[s]);
+                        } else {
+                            tma_load_3d(dst, &maps->map[kMapBody][2 * f + a], lpad + x_tile, y_tile, zg, &full[s]);
+                            tma_load_3d(dst + side_l, &maps->map[kMapSide][2 * f + a], lpad + xl_src, y_tile, zg,
+                                        &full[s]);
+                            tma_load_3d(dst + side_r, &maps->map[kMapSide][2 * f + a], lpad + xr_src, y_tile, zg,
+                                        &full[s]);
+                        }
+                    }
                 issued = k + 1;
             }
         }
@@ -836,9 +844,13 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
         const unsigned amask = __ballot_sync(0xffffffffu, active);
         const bool own_l = tx == 0 || lane == 0;
         const bool own_r = tx == txt - 1 || x0 + W >= N || lane == 31;
+        // at an x-edge tile the sites beyond the tile come from the halo columns
+        const bool col_l = edge && tx == 0;
+        const bool col_r = edge && (tx == txt - 1 || x0 + W >= N);
+        const int col = (tyi + 1) * W;  // this thread's row in a halo column
         const int src_l = own_l ? lane : lane - 1, src_r = own_r ? lane : lane + 1;
         const Coefs<T, NF> k = make_coefs<T, NF>(m, c, sc);
-        const int ctr = (tyi + 1) * rowe + (tx + 1) * W;
+        const int ctr = (tyi + 1) * rowe + (edge ? 0 : W) + tx * W;
         const size_t P = (size_t)m.pitch, PP = (size_t)m.pplane;
         T *pho[NF], *pio[NF];
 #pragma unroll
@@ -897,8 +909,10 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
                     for (int j = 0; j < W; ++j) yp[f][j] = fma_t(k.drift, b[j], a[j]);
                     const T l = __shfl_sync(amask, cu[f][W - 1], src_l);
                     const T r = __shfl_sync(amask, cu[f][0], src_r);
-                    xlv[f] = own_l ? fma_t(k.drift, pp[ctr - 1], ph[ctr - 1]) : l;
-                    xrv[f] = own_r ? fma_t(k.drift, pp[ctr + W], ph[ctr + W]) : r;
+                    const int il = col_l ? side_l + col + W - 1 : ctr - 1;
+                    const int ir = col_r ? side_r + col : ctr + W;
+                    xlv[f] = own_l ? fma_t(k.drift, pp[il], ph[il]) : l;
+                    xrv[f] = own_r ? fma_t(k.drift, pp[ir], ph[ir]) : r;
                 }
                 T pnew[NF][W];
                 site_update<T, NF, W>(k, cu, zm, zp, ym, yp, xlv, xrv, pc, pnew, acc);

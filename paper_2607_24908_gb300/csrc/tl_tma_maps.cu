@@ -31,8 +31,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 }
 
 // Encode the tensor maps of both buffer parities for the current tile shape:
-// 3-D (padded row, row incl. ghost rows, plane) over each array, box
-// (txt W + 2W) x (ty + 2) x 1.
+// 3-D (padded row, row incl. ghost rows, plane) over each array, boxes
+// (txt W + 2W, txt W or W) x (ty + 2) x 1 (TmaMaps).
 int encode_maps(tl_lattice *L)
 {
     const tl::PassGeom &g = L->geom;
@@ -49,7 +49,10 @@ int encode_maps(tl_lattice *L)
     // the kernel's bounded waits expire (TL_ETIMEOUT) -- a wait that runs out,
     // with every copy inside its stage region.
     const bool stall = getenv("TL_TEST_STALL_TMA") != nullptr;
-    const cuuint32_t box[3] = {(cuuint32_t)(g.txt * W + 2 * W), (cuuint32_t)(g.ty + (stall ? 1 : 2)), 1u};
+    const cuuint32_t rows = (cuuint32_t)(g.ty + (stall ? 1 : 2));
+    const cuuint32_t boxes[3][3] = {{(cuuint32_t)(g.txt * W + 2 * W), rows, 1u},  // kMapTile
+                                    {(cuuint32_t)(g.txt * W), rows, 1u},          // kMapBody
+                                    {(cuuint32_t)W, rows, 1u}};                   // kMapSide
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     // L2 promotion of the copies: 64 bytes (measured at N = 256 ... 1024 two
     // fields, 256^3 one field and the grouped ensemble: 0.1-0.5% faster than
@@ -62,15 +65,16 @@ int encode_maps(tl_lattice *L)
         else if (strcmp(v, "256") == 0) promo = CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
     }
     for (int par = 0; par < 2; ++par)
-        for (int f = 0; f < L->nf; ++f)
-            for (int a = 0; a < 2; ++a) {
-                void *base = static_cast<char *>(L->buf[par][a][f]) - lay.origin * esz;
-                CUresult r = enc(&L->maps[par].map[2 * f + a],
-                                 esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base,
-                                 dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                 promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-                if (r != CUDA_SUCCESS) return fail(TL_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-            }
+        for (int k = 0; k < 3; ++k)
+            for (int f = 0; f < L->nf; ++f)
+                for (int a = 0; a < 2; ++a) {
+                    void *base = static_cast<char *>(L->buf[par][a][f]) - lay.origin * esz;
+                    CUresult r = enc(&L->maps[par].map[k][2 * f + a],
+                                     esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                                     base, dims, strides, boxes[k], estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                     CU_TENSOR_MAP_SWIZZLE_NONE, promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    if (r != CUDA_SUCCESS) return fail(TL_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+                }
     L->maps_txt = g.txt;
     L->maps_ty = g.ty;
     return TL_OK;

@@ -342,14 +342,14 @@ def test_chaotic_regime_energies_and_spectra_within_one_percent(dtype):
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_caller_buffers_and_ghost_cells(dtype):
     """tl_lattice_create_with_buffers on torch-allocated padded arrays: after
-    init and several passes every ghost equals its periodic image, and the
-    results are bitwise those of a library-allocated lattice."""
+    init and several passes every ghost row equals its periodic image (the
+    reserved x-edge elements are not kept), and the results are bitwise those
+    of a library-allocated lattice."""
     import torch
     N, nf = 24, 2
     esz = 4 if dtype == "f32" else 8
     tdt = torch.float32 if dtype == "f32" else torch.float64
     elems, P, PP, origin = T.tl_array_layout(N, T.DTYPES[dtype])
-    W = 16 // esz
     bufs = [torch.zeros(elems, dtype=tdt, device="cuda") for _ in range(4 * nf)]
     ex = T.tl_expansion(1, 1.0, 1.0, 1.0)
     h = T.tl_lattice_create_with_buffers(N, 0.5, nf, T.DTYPES[dtype], ex, 0, [b.data_ptr() for b in bufs])
@@ -366,8 +366,6 @@ def test_caller_buffers_and_ghost_cells(dtype):
                 a = b.view(N, N + 2, P)  # [z][row incl. ghost rows][padded row]
                 L0 = origin - P  # x = 0 within a padded row
                 inner = a[:, 1:N + 1, L0:L0 + N]
-                assert torch.equal(a[:, 1:N + 1, L0 - W:L0], inner[:, :, N - W:])       # left ghosts
-                assert torch.equal(a[:, 1:N + 1, L0 + N:L0 + N + W], inner[:, :, :W])   # right ghosts
                 assert torch.equal(a[:, 0, L0:L0 + N], inner[:, N - 1, :])              # row above
                 assert torch.equal(a[:, N + 1, L0:L0 + N], inner[:, 0, :])              # row below
                 out = np.empty((N, N, N), np.float32 if dtype == "f32" else np.float64)
