@@ -234,13 +234,14 @@ def gpu_vs_oracle(final):
 
 
 # FP64 operations a fused pass must do per site of one field, as the pass is
-# written: drift 1; phi^2, dV/dphi and V(phi) in factored form 5; Laplacian
-# (neighbour sum minus 6 phi) 6; force 2; momentum at the evaluation time and the
-# kicked momentum 2; kinetic, gradient (summation by parts: -phi Lap phi) and
-# potential sums 3.  The FP64 pass is bound by the FP64 pipe; each thread also
-# redoes the drift of its four in-plane neighbours (3 more per site), which is
-# not counted here.
-FP64_OPS_PER_SITE_1F = 19
+# written: drift 1; phi^2 1; the weighted dV/dphi in factored form 2 (the force's
+# weight a^(3+alpha) folded into the coefficients); Laplacian (neighbour sum
+# minus 6 phi) 6; force 1; momentum at the evaluation time and the kicked
+# momentum 2; kinetic and gradient sums (summation by parts: -phi Lap phi) 2;
+# V(phi) in factored form accumulated straight into its sum 2.  The FP64 pass
+# is bound by the FP64 pipe; each thread also redoes the drift of its four
+# in-plane neighbours (3 more per site), which is not counted here.
+FP64_OPS_PER_SITE_1F = 17
 
 
 def fp64_pass():

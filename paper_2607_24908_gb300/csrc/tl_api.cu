@@ -54,13 +54,22 @@ tl::PassTuning tl::default_tuning(int N, int nf, int elem_bytes)
     if (v && strcmp(v, "tma") == 0) t.variant = tl::kVariantTma;
     if (v && strcmp(v, "ldg") == 0) t.variant = tl::kVariantLdg;
     const char *cw = getenv("TL_BULK_WARPS"), *zc = getenv("TL_PASS_ZC");
-    if (t.variant == tl::kVariantTma) {  // measured: long z-chunks for the ring, 15 + 1 warps on large lattices
-        // z-chunks from sweeps with the 64-byte L2 promotion (two FP32 fields, ms per pass):
-        // 512^3 96 planes 0.777 (72: 0.783), 768^3 88 planes 2.416 (72: 2.424), 1024^3 92
-        // planes 5.545 (72: 5.580); the optimum is jagged in the chunk count, so each
-        // measured size sets the value for the sizes around it
-        t.zc = N <= 192 ? 16 : (N < 512 ? 64 : (N < 640 ? 96 : (N < 896 ? 88 : 92)));
-        t.cwarps = N >= 768 ? 15 : 7;
+    if (t.variant == tl::kVariantTma) {  // measured: long z-chunks for the ring, 15 + 1 warps from 416
+        // warps x z-chunk sweeps with halo columns at the x-edges (FP32, ms per pass, one /
+        // two fields): 384^3 7 + 1 warps, 56 planes 0.247 / 0.340 (64: 0.261 / 0.354); 448^3
+        // 15 + 1, 96 planes 0.562 (7 + 1, 64: 0.578); 512^3 15 + 1, 160 planes 0.487 /
+        // 0.691 (7 + 1, 96: 0.534 / 0.746); 576^3 ... 768^3 15 + 1, 104 planes (576^3 1.085
+        // against 1.173, 704^3 1.895 against 2.015, 768^3 2.299 against 2.329 two fields);
+        // 896^3 and 1024^3 92 planes.  The optimum is jagged in the chunk count, so each
+        // measured size sets the value for the sizes around it.
+        if (N <= 192) t.zc = 16;
+        else if (N < 320) t.zc = 64;
+        else if (N < 416) t.zc = 56;
+        else if (N < 480) t.zc = 96;
+        else if (N < 544) t.zc = 160;
+        else if (N < 832) t.zc = 104;
+        else t.zc = 92;
+        t.cwarps = N >= 416 ? 15 : 7;
     } else if (elem_bytes == 8 && N >= 128) {
         // FP64 streaming pass (bound by the FP64 pipe): 32-plane chunks from 128^3 (one and two
         // fields, 128^3 ... 384^3: 0.7316 ms at 256^3 against 0.7465 with the 16 of the automatic

@@ -170,6 +170,8 @@ struct Coefs {
     T m2[NF];
     T qlam, hq;  // lambda/4, q/2 (the potential's own coefficients, FP64 form)
     T hm2[NF];   // m2/2
+    T wlam, wq;  // a^(3+alpha) lambda, a^(3+alpha) q (the force's weight folded in, FP64 form)
+    T wm2[NF];   // a^(3+alpha) m2
 };
 
 template <typename T, int NF>
@@ -190,6 +192,10 @@ __device__ __forceinline__ Coefs<T, NF> make_coefs(const Model &m, const PassCoe
     }
     k.qlam = (T)(0.25 * m.lambda);
     k.hq = (T)(0.5 * m.q);
+    k.wlam = (T)(sc->wv * m.lambda);
+    k.wq = (T)(sc->wv * m.q);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) k.wm2[f] = (T)(sc->wv * m.m2[f]);
     return k;
 }
 
@@ -203,9 +209,11 @@ __device__ __forceinline__ Coefs<T, NF> make_coefs(const Model &m, const PassCoe
 //
 // FP64 (bound by the FP64 pipe) takes the same quantities with fewer FP64
 // operations: the Laplacian as the neighbour sum minus 6 phi; the potential and
-// its derivative in factored form, phi (m2 + lambda phi^2) and
-// phi^2 (m2/2 + lambda phi^2/4); and the gradient energy by summation by
-// parts, which on a periodic lattice is exact: sum_x sum_i (phi(x+i) - phi(x))^2
+// its derivative in factored form, phi^2 (m2/2 + lambda phi^2/4) accumulated
+// straight into the sum, and a^(3+alpha) dV/dphi = phi (a^(3+alpha) m2 +
+// a^(3+alpha) lambda phi^2) with the force's weight folded into the
+// coefficients; and the gradient energy by summation by parts, which on a
+// periodic lattice is exact: sum_x sum_i (phi(x+i) - phi(x))^2
 // = -sum_x phi(x) (sum_i [phi(x+i) + phi(x-i)] - 6 phi(x)), so each site adds
 // -phi times the Laplacian it has already formed (one fma instead of three
 // differences and three squares).  The lattice-wide sums are the same
@@ -223,22 +231,22 @@ __device__ __forceinline__ void site_update(const Coefs<T, NF> &k, const T (&cu)
 #pragma unroll
             for (int f = 0; f < NF; ++f) v[f] = cu[f][j];
             const T v02 = v[0] * v[0];
-            T dv[NF];
-            T Vs;
+            T dvw[NF];  // a^(3+alpha) dV/dphi_f
             if constexpr (NF > 1) {
-                T others = (T)0, mo = (T)0;  // sum_{f>0} phi_f^2 and sum_{f>0} m2_f phi_f^2/2
+                // sum_{f>0} phi_f^2, and the potential sum plus sum_{f>0} m2_f phi_f^2/2
+                T others = (T)0, vsum = acc[2 * NF];
 #pragma unroll
                 for (int f = 1; f < NF; ++f) {
                     const T vf2 = v[f] * v[f];
                     others += vf2;
-                    mo = fma_t(k.hm2[f], vf2, mo);
-                    dv[f] = v[f] * fma_t(k.q, v02, k.m2[f]);
+                    vsum = fma_t(k.hm2[f], vf2, vsum);
+                    dvw[f] = v[f] * fma_t(k.wq, v02, k.wm2[f]);
                 }
-                dv[0] = v[0] * fma_t(k.q, others, fma_t(k.lam, v02, k.m2[0]));
-                Vs = fma_t(k.hq * v02, others, fma_t(v02, fma_t(k.qlam, v02, k.hm2[0]), mo));
+                dvw[0] = v[0] * fma_t(k.wq, others, fma_t(k.wlam, v02, k.wm2[0]));
+                acc[2 * NF] = fma_t(k.hq * v02, others, fma_t(v02, fma_t(k.qlam, v02, k.hm2[0]), vsum));
             } else {
-                dv[0] = v[0] * fma_t(k.lam, v02, k.m2[0]);
-                Vs = v02 * fma_t(k.qlam, v02, k.hm2[0]);
+                dvw[0] = v[0] * fma_t(k.wlam, v02, k.wm2[0]);
+                acc[2 * NF] = fma_t(v02, fma_t(k.qlam, v02, k.hm2[0]), acc[2 * NF]);
             }
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -246,13 +254,12 @@ __device__ __forceinline__ void site_update(const Coefs<T, NF> &k, const T (&cu)
                 const T left = (j == 0) ? xl[f] : cu[f][j - 1];
                 const T right = (j == W - 1) ? xr[f] : cu[f][j + 1];
                 const T lap = fma_t((T)-6, cc, ((left + right) + (ym[f][j] + yp[f][j])) + (zm[f][j] + zp[f][j]));
-                const T F = fma_t(k.wlx, lap, -k.wv * dv[f]);
+                const T F = fma_t(k.wlx, lap, -dvw[f]);
                 const T pint = fma_t(k.hdt, F, pc[f][j]);
                 pnew[f][j] = fma_t(k.kdt, F, pc[f][j]);
                 acc[f] = fma_t(pint, pint, acc[f]);
                 acc[NF + f] = fma_t(-cc, lap, acc[NF + f]);
             }
-            acc[2 * NF] += Vs;
         }
         return;
     }

@@ -92,9 +92,12 @@ def test_default_shape_and_errors():
         with T.Lattice(256, 0.5, 1, "f32") as one:  # FP32 from 192: TMA, 64-plane chunks below 512
             c1 = one.pass_config()
             assert (c1["kind"], c1["warps"], c1["z_chunk"]) == ("tma", 7, 64)
-        with T.Lattice(512, 0.5, 1, "f32") as mid:  # 96-plane chunks around 512
+        with T.Lattice(512, 0.5, 1, "f32") as mid:  # 15 + 1 warps, 160-plane chunks around 512
             c3 = mid.pass_config()
-            assert (c3["kind"], c3["warps"], c3["z_chunk"]) == ("tma", 7, 96)
+            assert (c3["kind"], c3["warps"], c3["z_chunk"]) == ("tma", 15, 160)
+        with T.Lattice(384, 0.5, 1, "f32") as mid:  # 7 + 1 warps, 56-plane chunks around 384
+            c5 = mid.pass_config()
+            assert (c5["kind"], c5["warps"], c5["z_chunk"]) == ("tma", 7, 56)
         with T.Lattice(256, 0.5, 2, "f64") as f64:  # FP64: the streaming pass, 32-plane chunks from 128
             c4 = f64.pass_config()
             assert (c4["kind"], c4["z_chunk"]) == ("stream", 32)
@@ -145,28 +148,30 @@ def test_batch_moves_members_to_the_batch_shape():
 
 
 def test_ragged_at_scale_tma_default_equals_stream():
-    """N = 500, two FP32 fields: the default TMA shape has ragged tiles in every direction
-    (x tiles of 128 with a last one of 116 sites, y tiles of 7 rows with a last one of 3,
-    z-chunks of 64 planes with a last one of 52); two Verlet steps give bitwise the fields
-    of the streaming kernel."""
+    """N = 500, two FP32 fields: TMA shapes with ragged tiles in every direction (x tiles
+    of 128 with a last one of 116 sites; 7 + 1 warps: y tiles of 7 rows with a last one
+    of 3, z-chunks of 64 planes with a last one of 52; the default 15 + 1 warps: y tiles
+    of 15 rows with a last one of 5, z-chunks of 160 with a last one of 20); two Verlet
+    steps give bitwise the fields of the streaming kernel."""
     N, nf = 500, 2
     rng = np.random.default_rng(17)
     phi = (rng.standard_normal((nf, N, N, N), dtype=np.float32) * np.float32(1e-2)
            + np.array([1.0, 0.0], np.float32)[:, None, None, None])
     pi = rng.standard_normal((nf, N, N, N), dtype=np.float32) * np.float32(1e-2)
     out = []
-    for shape in (None, dict(kind="stream")):
+    for shape in (None, dict(kind="tma", warps=7, z_chunk=64), dict(kind="stream")):
         with T.Lattice(N, 0.1, nf, "f32") as lat:
             if shape:
                 lat.set_pass_config(**shape)
             else:
                 cfg = lat.pass_config()
-                assert cfg["kind"] == "tma" and cfg["z_chunk"] == 64
+                assert (cfg["kind"], cfg["warps"], cfg["z_chunk"]) == ("tma", 15, 160)
             lat.set_potential(1.0, 10.0, (0.0, 0.2, 0.0))
             lat.set_state(phi, pi)
             lat.step(2, 0.01, "verlet")
             out.append(lat.get_all())
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for o in out[:2]:
+        assert np.array_equal(o[0], out[2][0]) and np.array_equal(o[1], out[2][1])
 
 
 def test_every_reported_shape_can_be_set_again():
@@ -183,3 +188,4 @@ def test_every_reported_shape_can_be_set_again():
             with T.Lattice(N, 0.5, 2, dtype) as other:
                 other.set_pass_config(**cfg)
                 assert other.pass_config() == cfg, (N, dtype, shape, cfg, other.pass_config())
+
