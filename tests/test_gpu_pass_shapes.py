@@ -189,3 +189,32 @@ def test_every_reported_shape_can_be_set_again():
                 other.set_pass_config(**cfg)
                 assert other.pass_config() == cfg, (N, dtype, shape, cfg, other.pass_config())
 
+
+
+@pytest.mark.parametrize("N,nf,dtype", [(300, 2, "f32"), (136, 2, "f64"), (72, 1, "f64")])
+def test_tma_interior_and_edge_tiles_equal_stream(N, nf, dtype):
+    """Lattices with tiles inside the lattice and at both x-edges, the last one
+    ragged (FP32 300 = 128 + 128 + 44 sites, FP64 136 = 64 + 64 + 8 and
+    72 = 64 + 8): the edge tiles' halo columns (the periodic image beyond each
+    edge) give bitwise the fields of the streaming kernel, under the default
+    and a 15 + 1 warp TMA shape, in a static and an expanding background."""
+    rng = np.random.default_rng(N)
+    npd = np.float32 if dtype == "f32" else np.float64
+    phi = (rng.standard_normal((nf, N, N, N)) * 1e-2 + np.array([1.0, 0.0][:nf])[:, None, None, None]).astype(npd)
+    pi = (rng.standard_normal((nf, N, N, N)) * 1e-2).astype(npd)
+    for expanding in (False, True):
+        out = []
+        for shape in (dict(kind="stream"), dict(kind="tma"), dict(kind="tma", warps=15, z_chunk=40)):
+            with T.Lattice(N, 0.3, nf, dtype, expanding, 1.0, 1.0, 1.0) as lat:
+                lat.set_pass_config(**shape)
+                lat.set_potential(1.0, 10.0, (0.0, 0.2, 0.0))
+                lat.set_state(phi, pi, 1.0, 0.0, b_from_constraint=expanding)
+                lat.step(3, 0.01, "verlet")
+                out.append((*lat.get_all(), lat.energies()))
+        for o in out[1:]:
+            if not expanding:  # fields do not depend on the reduction order
+                assert np.array_equal(o[0], out[0][0]) and np.array_equal(o[1], out[0][1])
+            else:  # a, a' do (energy sums per tile): agree to rounding
+                tol = 1e-5 if dtype == "f32" else 1e-12
+                assert np.max(np.abs(o[0] - out[0][0])) <= tol * np.max(np.abs(out[0][0]))
+                assert abs(o[2].a - out[0][2].a) <= tol * out[0][2].a
