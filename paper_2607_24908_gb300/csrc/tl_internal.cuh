@@ -127,6 +127,25 @@ __host__ __device__ constexpr size_t tma_slot_bytes(int txt, int ty)
                         ? (size_t)(ty + 2) * (txt + 2) * 16
                         : tma_side_offset(txt, ty, 1) + (size_t)(ty + 2) * 16);
 }
+// The slot layout, checked for every tile the pass can have (txt up to 32
+// threads along x, ty up to 64 rows): the tile-plus-halo box fits the slot,
+// and so do the body and the two halo columns after it, each part on a
+// 128-byte boundary and the columns clear of the body and of each other.
+constexpr bool tma_slot_layout_holds()
+{
+    for (int txt = 1; txt <= 32; ++txt)
+        for (int ty = 1; ty <= 64; ++ty) {
+            const size_t slot = tma_slot_bytes(txt, ty), l = tma_side_offset(txt, ty, 0),
+                         r = tma_side_offset(txt, ty, 1), col = (size_t)(ty + 2) * 16;
+            if (slot % 128 || l % 128 || r % 128) return false;
+            if ((size_t)(ty + 2) * (txt + 2) * 16 > slot) return false;
+            if ((size_t)(ty + 2) * txt * 16 > l || l + col > r || r + col > slot) return false;
+        }
+    return true;
+}
+static_assert(tma_slot_layout_holds(), "TMA stage slots must hold every tile's copies on 128-byte boundaries");
+static_assert(tma_slot_bytes(32, 15) == 9472 && tma_slot_bytes(32, 7) == 5120,
+              "slot sizes of the default tiles (two-field ring: 6 x 37.9 KB and 5 x 20.5 KB)");
 
 // Launch geometry of the fused pass.
 struct PassGeom {
