@@ -343,6 +343,16 @@ def run_ours(args):
     lat.set_potential(WL.lam, WL.q, WL.m2)
     lat.init_fluctuations(replica_seed(rank), A=WL.A, meff2=WL.meff2, phi0=WL.phi0)
     args.pass_shape = lat.pass_config()
+    # the end-to-end leg's pinned host buffers, allocated and touched now: pinning
+    # tens of GB makes the host rearrange memory for a while, which would slow the
+    # transfers if it happened inside that leg's timed region
+    host = []
+    if not args.no_e2e:
+        host = [torch.empty((N,) * 3, dtype=torch.float32 if WL.dtype == "f32" else torch.float64,
+                            pin_memory=True) for _ in range(2 * WL.nf)]
+        for f in range(WL.nf):
+            for w in range(2):
+                T.tl_get_state(lat.h, f, w, host[2 * f + w].numpy())
 
     # warm-up: W steps (one call each)
     for _ in range(args.warmup):
@@ -374,7 +384,8 @@ def run_ours(args):
 
     # end-to-end through the C ABI with host buffers: H2D of the state from
     # pinned memory, K steps, energies and D2H of the state, every call inside
-    # the timed region.
+    # the timed region; three such jobs, the median reported (the host link's
+    # speed varies between jobs on a busy host; all three are in the phases).
     npd = np.float32 if WL.dtype == "f32" else np.float64
     if args.no_e2e:
         lat.close()
@@ -382,26 +393,32 @@ def run_ours(args):
         state_bytes = 2 * WL.nf * sites * np.dtype(npd).itemsize
         return _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_rank, t_e2e, state_bytes,
                        E, E2, clk)
-    host = [torch.empty((N,) * 3, dtype=torch.float32 if WL.dtype == "f32" else torch.float64,
-                        pin_memory=True) for _ in range(2 * WL.nf)]
-    for f in range(WL.nf):
+    runs = []
+    for f in range(WL.nf):  # the state the first job starts from
         for w in range(2):
             T.tl_get_state(lat.h, f, w, host[2 * f + w].numpy())
-    barrier()
-    t0 = time.perf_counter()
-    for f in range(WL.nf):
-        for w in range(2):
-            T.tl_set_state(lat.h, f, w, host[2 * f + w].numpy())
-    T.tl_set_background(lat.h, E.a, E.b, False)
-    t1 = time.perf_counter()
-    lat.step(args.steps, WL.dt, integ)
-    E2 = lat.energies()
-    t2 = time.perf_counter()
-    for f in range(WL.nf):
-        for w in range(2):
-            T.tl_get_state(lat.h, f, w, host[2 * f + w].numpy())
-    t_e2e = time.perf_counter() - t0
-    args.e2e_phases = {"set_state_s": t1 - t0, "steps_and_energies_s": t2 - t1, "get_state_s": t0 + t_e2e - t2}
+    a_in, b_in = E.a, E.b
+    for rep in range(3):  # each job continues from the previous job's returned state
+        barrier()
+        t0 = time.perf_counter()
+        for f in range(WL.nf):
+            for w in range(2):
+                T.tl_set_state(lat.h, f, w, host[2 * f + w].numpy())
+        T.tl_set_background(lat.h, a_in, b_in, False)
+        t1 = time.perf_counter()
+        lat.step(args.steps, WL.dt, integ)
+        E2 = lat.energies()
+        t2 = time.perf_counter()
+        for f in range(WL.nf):
+            for w in range(2):
+                T.tl_get_state(lat.h, f, w, host[2 * f + w].numpy())
+        t3 = time.perf_counter()
+        runs.append({"total_s": t3 - t0, "set_state_s": t1 - t0, "steps_and_energies_s": t2 - t1,
+                     "get_state_s": t3 - t2})
+        a_in, b_in = E2.a, E2.b
+    mid = sorted(runs, key=lambda r: r["total_s"])[1]
+    t_e2e = mid["total_s"]
+    args.e2e_phases = {"median_job": mid, "jobs": runs}
     t_e2e = max_over_ranks(t_e2e, ws, "cuda")
     state_bytes = 2 * WL.nf * sites * np.dtype(npd).itemsize
     lat.close()
@@ -442,7 +459,7 @@ def _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_ran
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": state_bytes / args.steps,
                     "d2h_bytes_per_step": (state_bytes + 136) / args.steps,
-                    "note": "state H2D once, K steps, energies + state D2H, per K-step job",
+                    "note": "state H2D once, K steps, energies + state D2H, per K-step job; median of 3 jobs",
                     "phases": getattr(args, "e2e_phases", None)},
             "gpu_launches": launches,
             "clocks": clk,
