@@ -446,10 +446,10 @@ int tl_autotune(tl_lattice *lat, double *best_ms_per_pass);
  * tl_get_pass_config returns can be set again.  Values out of range are TL_EINVAL;
  * TL_ESTATE while the lattice is in a batch.  May synchronise the lattice
  * stream (to grow its reduction slots).  A new lattice starts on TL_PASS_TMA
- * when it is FP32 and N >= 192 (z-chunks of 16 planes at N = 192, 64 up to
- * N = 319, then 56, 96, 160, 104 and 92 planes around N = 384, 448, 512,
- * 576 ... 768 and from 832, where they measured fastest; 15 compute warps from
- * N = 416, else 7), on
+ * when it is FP32 and N >= 192 (z-chunks of 48 planes at N = 192, 64 up to
+ * N = 319, then 56, 80, 160 (one field) or 96, 104, 72 and 76 planes around
+ * N = 384, 448, 512, 576 ... 768, 896 and 1024, where they measured fastest;
+ * 15 compute warps from N = 416, else 7), on
  * TL_PASS_STREAM otherwise (where those measured faster; FP64 from N = 128
  * with z-chunks of 32 planes, 64 from N = 512); the environment
  * variable TL_PASS_VARIANT=tma|ldg overrides that default at creation. */

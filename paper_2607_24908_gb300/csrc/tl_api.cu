@@ -47,7 +47,6 @@ thread_local char g_err[512] = "";
 
 tl::PassTuning tl::default_tuning(int N, int nf, int elem_bytes)
 {
-    (void)nf;
     tl::PassTuning t{elem_bytes == 4 && N >= 192 ? tl::kVariantTma : tl::kVariantLdg, 7, 0, 0, 0, 256, 0};
     // environment overrides (tuning experiments)
     const char *v = getenv("TL_PASS_VARIANT");
@@ -55,20 +54,21 @@ tl::PassTuning tl::default_tuning(int N, int nf, int elem_bytes)
     if (v && strcmp(v, "ldg") == 0) t.variant = tl::kVariantLdg;
     const char *cw = getenv("TL_BULK_WARPS"), *zc = getenv("TL_PASS_ZC");
     if (t.variant == tl::kVariantTma) {  // measured: long z-chunks for the ring, 15 + 1 warps from 416
-        // warps x z-chunk sweeps with halo columns at the x-edges (FP32, ms per pass, one /
-        // two fields): 384^3 7 + 1 warps, 56 planes 0.247 / 0.340 (64: 0.261 / 0.354); 448^3
-        // 15 + 1, 96 planes 0.562 (7 + 1, 64: 0.578); 512^3 15 + 1, 160 planes 0.487 /
-        // 0.691 (7 + 1, 96: 0.534 / 0.746); 576^3 ... 768^3 15 + 1, 104 planes (576^3 1.085
-        // against 1.173, 704^3 1.895 against 2.015, 768^3 2.299 against 2.329 two fields);
-        // 896^3 and 1024^3 92 planes.  The optimum is jagged in the chunk count, so each
-        // measured size sets the value for the sizes around it.
-        if (N <= 192) t.zc = 16;
+        // warps x z-chunk sweeps of the current kernel (FP32, ms per pass, one / two fields):
+        // 192^3 48 planes 0.083 two fields (16: 0.091); 384^3 7 + 1 warps, 56 planes 0.205 /
+        // 0.325; 448^3 15 + 1, 80 planes 0.524 two fields (96: 0.531); 512^3 15 + 1, 160
+        // planes 0.417 one field, 96 planes 0.705 two (160: 0.714); 576^3 ... 768^3 104
+        // planes (640^3 1.330, 768^3 2.297 two fields); 896^3 72 planes 3.623 (92: 3.634);
+        // 1024^3 76 planes 5.380 (92: 5.391).  The optimum is jagged in the chunk count, so
+        // each measured size sets the value for the sizes around it.
+        if (N <= 192) t.zc = 48;
         else if (N < 320) t.zc = 64;
         else if (N < 416) t.zc = 56;
-        else if (N < 480) t.zc = 96;
-        else if (N < 544) t.zc = 160;
+        else if (N < 480) t.zc = 80;
+        else if (N < 544) t.zc = nf == 1 ? 160 : 96;
         else if (N < 832) t.zc = 104;
-        else t.zc = 92;
+        else if (N < 960) t.zc = 72;
+        else t.zc = 76;
         t.cwarps = N >= 416 ? 15 : 7;
     } else if (elem_bytes == 8 && N >= 128) {
         // FP64 streaming pass (bound by the FP64 pipe): 32-plane chunks from 128^3 (one and two

@@ -736,6 +736,71 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 
 constexpr int kMaxStages = 8;
 
+// The fixed-order sum of cta_reduce_finalize for the compute warps of a TMA
+// CTA alone (threads 0 .. nthr-1, named barrier 1), so that the producer warp
+// can go on loading the next tile's planes meanwhile.  The same numbers as the
+// whole-CTA form: the producer warp's share was zero.  The last tile to arrive
+// sums all slots with a fixed stride of 128 threads.
+template <int NQ, bool F32TREE>
+__device__ __forceinline__ void consumer_reduce_finalize(const double (&accd)[NQ], const Model &m, const PassCoef &c,
+                                                         Scalars *sc, double *slots, unsigned bid, unsigned nblocks,
+                                                         unsigned nthr)
+{
+    __shared__ double red[32][NQ];
+    __shared__ bool last;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = (int)(nthr >> 5);
+    auto sync = [&] { asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory"); };
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        double v;
+        if constexpr (F32TREE) {
+            float w = (float)accd[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            v = (double)w;
+        } else {
+            v = warp_sum(accd[i]);
+        }
+        if (lane == 0) red[warp][i] = v;
+    }
+    sync();
+    if (tid < NQ) {
+        double s = 0.0;
+        for (int w = 0; w < nwarps; ++w) s += red[w][tid];
+        slots[(size_t)bid * NQ + tid] = s;
+    }
+    __threadfence();
+    sync();
+    if (tid == 0) last = (atomicAdd(&sc->ticket, 1u) == nblocks - 1);
+    sync();
+    if (last) {
+        __threadfence();
+        double part[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) part[i] = 0.0;
+        if (tid < 128)
+            for (unsigned b = tid; b < nblocks; b += 128)
+#pragma unroll
+                for (int i = 0; i < NQ; ++i) part[i] += __ldcg(slots + (size_t)b * NQ + i);
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            double v = warp_sum(part[i]);
+            if (lane == 0 && warp < 4) red[warp][i] = v;
+        }
+        sync();
+        if (tid == 0) {
+            double tot[kMaxQ];
+            for (int i = 0; i < NQ; ++i) tot[i] = ((red[0][i] + red[1][i]) + red[2][i]) + red[3][i];
+            finalize(m, c, sc, tot);
+            sc->ticket = 0u;
+            __threadfence();
+        }
+    }
+    sync();  // red[] and last are reused by the next tile
+}
+
 // One CTA tile (bx, by, bz) of the TMA pass; bid/nblocks index the tile among
 // the lattice's tiles for the reduction; maps points to the tensor maps of the
 // lattice's input arrays (a kernel parameter or a copy in global memory).
@@ -816,14 +881,22 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
             // W divides N and the tile offsets)
             const int xl_src = x_tile == 0 ? N - W : x_tile - W;
             const int xr_src = x_tile + txt * W >= N ? 0 : x_tile + txt * W;
+            int ps = 0;
+            unsigned pph = 0;
             for (int k = 0; k < K; ++k) {
-                const int s = k % S;
-                if (k >= S && !mbar_wait_bounded(&empty[s], ((k / S) - 1) & 1u, sc)) {
+                const int s = ps;
+                if (k >= S && !mbar_wait_bounded(&empty[s], pph ^ 1u, sc)) {
                     s_failed = 1;
                     break;
                 }
                 if (s_failed) break;
-                const int zg = (z0 - 1 + k + N) % N;
+                int zg = z0 - 1 + k;
+                if (zg < 0) zg += N;
+                else if (zg >= N) zg -= N;
+                if (++ps == S) {
+                    ps = 0;
+                    pph ^= 1u;
+                }
                 mbar_arrive_expect_tx(&full[s], (uint32_t)(NF * 2) * box_bytes);
 #pragma unroll
                 for (int f = 0; f < NF; ++f)
@@ -869,8 +942,7 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
         T acc[NQ];
 #pragma unroll
         for (int i = 0; i < NQ; ++i) acc[i] = (T)0;
-        auto centre = [&](int kk, T (&ph)[NF][W], T (&pp)[NF][W]) {
-            const int s = kk % S;
+        auto centre = [&](int s, T (&ph)[NF][W], T (&pp)[NF][W]) {
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 T a[W];
@@ -880,27 +952,40 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
                 for (int j = 0; j < W; ++j) ph[f][j] = fma_t(k.drift, pp[f][j], a[j]);
             }
         };
-        auto release = [&](int kk) {
+        int ws = 0, rs = 0;
+        unsigned wph = 0;
+        auto adv_w = [&] {
+            if (++ws == S) {
+                ws = 0;
+                wph ^= 1u;
+            }
+        };
+        auto release = [&](int) {
             __syncwarp();
             if (lane == 0)
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[kk % S])) : "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[rs])) : "memory");
+            if (++rs == S) rs = 0;
         };
         bool ok = true;
         if (active) {
-            ok = mbar_wait_bounded(&full[0], 0u, sc);
-            centre(0, zm, pn);
-            ok = ok && mbar_wait_bounded(&full[1 % S], (1 / S) & 1u, sc);
-            centre(1, cu, pc);
+            ok = mbar_wait_bounded(&full[ws], wph, sc);
+            centre(ws, zm, pn);
         }
+        adv_w();
+        if (active) {
+            ok = ok && mbar_wait_bounded(&full[ws], wph, sc);
+            centre(ws, cu, pc);
+        }
+        adv_w();
         if (!ok) s_failed = 1;
         release(0);
         for (int z = z0; z < z1; ++z) {
             if (__any_sync(0xffffffffu, s_failed != 0)) break;  // warp-uniform exit
             const int kz = z - z0 + 1;
             if (active) {
-                if (!mbar_wait_bounded(&full[(kz + 1) % S], ((kz + 1) / S) & 1u, sc)) s_failed = 1;
-                centre(kz + 1, zp, pn);
-                const int s0 = kz % S;
+                if (!mbar_wait_bounded(&full[ws], wph, sc)) s_failed = 1;
+                centre(ws, zp, pn);
+                const int s0 = rs;
                 T ym[NF][W], yp[NF][W], xlv[NF], xrv[NF];
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
@@ -948,27 +1033,334 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
                         pc[f][j] = pn[f][j];
                     }
             }
+            adv_w();
             release(kz);
         }
 #pragma unroll
         for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
     }
+    if (producer) {
+        // After a timeout, wait (bounded) for the copies still in flight before the
+        // CTA's shared memory goes away.
+        if (s_failed && (tid & 31) == 0)
+            for (int kk = (issued > S ? issued - S : 0); kk < issued; ++kk)
+                mbar_wait_bounded(&full[kk % S], (kk / S) & 1u, sc);
+        return;
+    }
+    consumer_reduce_finalize<NQ, sizeof(T) == 4>(accd, m, c, sc, slots, bid, nblocks, (unsigned)CW * 32u);
+}
+
+// Tiles first, first + stride, ... (< nitems) of the TMA pass, in a CTA whose
+// stage ring carries on from tile to tile: the producer warp streams the
+// planes of all its tiles through the ring (a global plane count gives each
+// plane its stage and barrier phase), so it loads the next tile's first
+// planes while the compute warps finish a tile and sum its energies.  Tile
+// `item` is (bx, by, bz) = (item % gx, item / gx % gy, item / (gx gy)) and owns
+// reduction slot `item` of nitems.  maps points to the tensor maps of the
+// lattice's input arrays (a kernel parameter or a copy in global memory);
+// GLOBAL_MAPS: the maps live in global memory, written by the host, and the
+// producer makes them visible to the tensor-map proxy before their first use.
+// Every compute warp takes part in every tile's ring traffic (a warp without
+// sites only waits and releases), so the "empty" barriers count all of them.
+template <typename T, int NF, bool MEASURE, bool GLOBAL_MAPS = false>
+__device__ __forceinline__ void tma_items(const Model &m, const FieldPtrs &fp, const PassCoef &c, int txt, int ty,
+                                          int zc, int S, int lpad, const TmaMaps *maps, Scalars *sc, double *slots,
+                                          unsigned first, unsigned stride, unsigned nitems, int gx, int gy)
+{
+    constexpr int W = Vec<T>::W;
+    constexpr int NQ = 2 * NF + 1;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages];
+    __shared__ volatile int s_failed;
+    __shared__ int s_stop;
+
+    const int N = m.N;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int CW = (blockDim.x >> 5) - 1;
+    const bool producer = (tid >> 5) == CW;
+    const int tx = tid % txt, tyi = tid / txt;
+    // (ty + 2) (txt + 2) 16-byte words per array and plane for every tile (a
+    // tile-plus-halo box, or at an x-edge the body box and two halo columns)
+    const uint32_t box_bytes = (uint32_t)((ty + 2) * (txt + 2) * 16);
+    const uint32_t region = (uint32_t)tma_slot_bytes(txt, ty);  // one array's slot in a stage
+    const int side_l = (int)(tma_side_offset(txt, ty, 0) / sizeof(T));
+    const int side_r = (int)(tma_side_offset(txt, ty, 1) / sizeof(T));
+    auto arr = [&](int s, int f, int a) -> T * {
+        return reinterpret_cast<T *>(smem_raw + (size_t)((s * NF + f) * 2 + a) * region);
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CW);
+        }
+        s_failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
-    // After a timeout, wait (bounded) for the copies still in flight before the
-    // CTA's shared memory goes away.
-    if (s_failed && producer && (tid & 31) == 0)
-        for (int kk = (issued > S ? issued - S : 0); kk < issued; ++kk)
-            mbar_wait_bounded(&full[kk % S], (kk / S) & 1u, sc);
-    cta_reduce_finalize<NQ, sizeof(T) == 4>(accd, m, c, sc, slots, bid, nblocks);
+
+    if (producer) {
+        if (lane == 0) {
+            if constexpr (GLOBAL_MAPS) {
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+                    for (int i = 0; i < 2 * NF; ++i)
+                        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&maps->map[kk][i])
+                                     : "memory");
+            }
+            // plane count g and its ring stage ps and phase pph, advanced
+            // incrementally (no division in the loop)
+            unsigned g = 0, issued = 0, pph = 0;
+            int ps = 0;
+            bool stop = false;
+            for (unsigned item = first; item < nitems && !stop; item += stride) {
+                const int bx = (int)(item % (unsigned)gx), by = (int)((item / (unsigned)gx) % (unsigned)gy);
+                const int bz = (int)(item / ((unsigned)gx * (unsigned)gy));
+                const int x_tile = bx * txt * W, y_tile = by * ty;
+                const int z0 = bz * zc, z1 = min(z0 + zc, N), K = z1 - z0 + 2;
+                const bool edge = x_tile == 0 || x_tile + txt * W >= N;
+                // source columns of the halo columns of an edge tile (16-byte
+                // aligned: W divides N and the tile offsets)
+                const int xl_src = x_tile == 0 ? N - W : x_tile - W;
+                const int xr_src = x_tile + txt * W >= N ? 0 : x_tile + txt * W;
+                for (int k = 0; k < K; ++k) {
+                    const int s = ps;
+                    // the stage's previous plane (g - S) completed phase pph ^ 1
+                    if (g >= (unsigned)S && !mbar_wait_bounded(&empty[s], pph ^ 1u, sc)) {
+                        s_failed = 1;
+                        stop = true;
+                        break;
+                    }
+                    if (s_failed) {
+                        stop = true;
+                        break;
+                    }
+                    int zg = z0 - 1 + k;
+                    if (zg < 0) zg += N;
+                    else if (zg >= N) zg -= N;
+                    mbar_arrive_expect_tx(&full[s], (uint32_t)(NF * 2) * box_bytes);
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+#pragma unroll
+                        for (int a = 0; a < 2; ++a) {
+                            T *dst = arr(s, f, a);
+                            if (!edge) {
+                                tma_load_3d(dst, &maps->map[kMapTile][2 * f + a], lpad + x_tile - W, y_tile, zg,
+                                            &full[s]);
+                            } else {
+                                tma_load_3d(dst, &maps->map[kMapBody][2 * f + a], lpad + x_tile, y_tile, zg, &full[s]);
+                                tma_load_3d(dst + side_l, &maps->map[kMapSide][2 * f + a], lpad + xl_src, y_tile, zg,
+                                            &full[s]);
+                                tma_load_3d(dst + side_r, &maps->map[kMapSide][2 * f + a], lpad + xr_src, y_tile, zg,
+                                            &full[s]);
+                            }
+                        }
+                    issued = g + 1;
+                    ++g;
+                    if (++ps == S) {
+                        ps = 0;
+                        pph ^= 1u;
+                    }
+                }
+            }
+            // After a timeout, wait (bounded) for the copies still in flight
+            // before the CTA's shared memory can go away.
+            if (s_failed)
+                for (unsigned gg = (issued > (unsigned)S ? issued - S : 0); gg < issued; ++gg)
+                    mbar_wait_bounded(&full[gg % S], (gg / S) & 1u, sc);
+        }
+        return;  // the producer warp takes no part in the tiles' sums
+    }
+
+    const unsigned nthr = (unsigned)CW * 32u;
+    const size_t P = (size_t)m.pitch, PP = (size_t)m.pplane;
+    T *pho[NF], *pio[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        pho[f] = static_cast<T *>(fp.phi_out[f]);
+        pio[f] = static_cast<T *>(fp.pi_out[f]);
+    }
+    // Two ring pointers, carried from tile to tile: the next plane to wait for
+    // (stage ws, phase wph) and the next plane to release (stage rs).
+    int ws = 0, rs = 0;
+    unsigned wph = 0;
+    auto wait_next = [&]() -> bool { return mbar_wait_bounded(&full[ws], wph, sc); };
+    auto advance_wait = [&] {
+        if (++ws == S) {
+            ws = 0;
+            wph ^= 1u;
+        }
+    };
+    auto release_next = [&] {
+        __syncwarp();
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&empty[rs])) : "memory");
+        if (++rs == S) rs = 0;
+    };
+
+    for (unsigned item = first; item < nitems; item += stride) {
+        const int bx = (int)(item % (unsigned)gx), by = (int)((item / (unsigned)gx) % (unsigned)gy);
+        const int bz = (int)(item / ((unsigned)gx * (unsigned)gy));
+        const int x_tile = bx * txt * W, y_tile = by * ty;
+        const int z0 = bz * zc, z1 = min(z0 + zc, N), K = z1 - z0 + 2;
+        const bool edge = x_tile == 0 || x_tile + txt * W >= N;
+        const int rowe = edge ? txt * W : txt * W + 2 * W;  // row pitch of the staged body
+        const int x0 = x_tile + tx * W;
+        const int y = y_tile + tyi;
+        const bool active = (tyi < ty) && (x0 < N) && (y < N);
+        const bool warp_active = __any_sync(0xffffffffu, active);
+        double accd[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) accd[i] = 0.0;
+        if (warp_active) {
+            // x-neighbours: the left site is the last one of the thread to the
+            // left in the same row and warp, the right site the first one of the
+            // thread to the right (warp shuffles, no shared-memory bank
+            // conflicts); threads at a row end or a warp edge read theirs from
+            // the stage, at a lattice x-edge from the halo columns.
+            const unsigned amask = __ballot_sync(0xffffffffu, active);
+            const bool own_l = tx == 0 || lane == 0;
+            const bool own_r = tx == txt - 1 || x0 + W >= N || lane == 31;
+            const bool col_l = edge && tx == 0;
+            const bool col_r = edge && (tx == txt - 1 || x0 + W >= N);
+            const int col = (tyi + 1) * W;  // this thread's row in a halo column
+            const int src_l = own_l ? lane : lane - 1, src_r = own_r ? lane : lane + 1;
+            const Coefs<T, NF> k = make_coefs<T, NF>(m, c, sc);
+            const int ctr = (tyi + 1) * rowe + (edge ? 0 : W) + tx * W;
+            T zm[NF][W], cu[NF][W], zp[NF][W], pc[NF][W], pn[NF][W];
+            T acc[NQ];
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) acc[i] = (T)0;
+            auto centre = [&](int s, T (&ph)[NF][W], T (&pp)[NF][W]) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    T a[W];
+                    load_vec_s(arr(s, f, 0) + ctr, a);
+                    load_vec_s(arr(s, f, 1) + ctr, pp[f]);
+#pragma unroll
+                    for (int j = 0; j < W; ++j) ph[f][j] = fma_t(k.drift, pp[f][j], a[j]);
+                }
+            };
+            bool ok = true;
+            if (active) {
+                ok = wait_next();
+                centre(ws, zm, pn);
+            }
+            advance_wait();
+            if (active) {
+                ok = ok && wait_next();
+                centre(ws, cu, pc);
+            }
+            advance_wait();
+            if (!ok) s_failed = 1;
+            release_next();  // plane 0 (z0 - 1)
+            int kz_done = 0;  // planes 0 .. kz_done of the tile released
+            for (int z = z0; z < z1; ++z) {
+                if (__any_sync(0xffffffffu, s_failed != 0)) break;  // warp-uniform exit
+                const int kz = z - z0 + 1;
+                if (active) {
+                    if (!wait_next()) s_failed = 1;
+                    centre(ws, zp, pn);
+                    const int s0 = rs;  // plane kz, the next to release
+                    T ym[NF][W], yp[NF][W], xlv[NF], xrv[NF];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const T *ph = arr(s0, f, 0), *pp = arr(s0, f, 1);
+                        T a[W], b[W];
+                        load_vec_s(ph + ctr - rowe, a);
+                        load_vec_s(pp + ctr - rowe, b);
+#pragma unroll
+                        for (int j = 0; j < W; ++j) ym[f][j] = fma_t(k.drift, b[j], a[j]);
+                        load_vec_s(ph + ctr + rowe, a);
+                        load_vec_s(pp + ctr + rowe, b);
+#pragma unroll
+                        for (int j = 0; j < W; ++j) yp[f][j] = fma_t(k.drift, b[j], a[j]);
+                        const T l = __shfl_sync(amask, cu[f][W - 1], src_l);
+                        const T r = __shfl_sync(amask, cu[f][0], src_r);
+                        const int il = col_l ? side_l + col + W - 1 : ctr - 1;
+                        const int ir = col_r ? side_r + col : ctr + W;
+                        xlv[f] = own_l ? fma_t(k.drift, pp[il], ph[il]) : l;
+                        xrv[f] = own_r ? fma_t(k.drift, pp[ir], ph[ir]) : r;
+                    }
+                    T pnew[NF][W];
+                    site_update<T, NF, W>(k, cu, zm, zp, ym, yp, xlv, xrv, pc, pnew, acc);
+                    if (!MEASURE) {
+                        const size_t pz = (size_t)z * PP;
+#pragma unroll
+                        for (int f = 0; f < NF; ++f) {
+                            store_vec_cs(pho[f] + pz + (size_t)y * P + x0, cu[f]);
+                            store_vec_cs(pio[f] + pz + (size_t)y * P + x0, pnew[f]);
+                        }
+                        if (m.ghosts) store_ghosts<T, NF, W>(pho, pio, cu, pnew, pz, x0, y, N, (long long)P);
+                    }
+                    if (((z - z0) & 15) == 15) {
+#pragma unroll
+                        for (int i = 0; i < NQ; ++i) {
+                            accd[i] += (double)acc[i];
+                            acc[i] = (T)0;
+                        }
+                    }
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+#pragma unroll
+                        for (int j = 0; j < W; ++j) {
+                            zm[f][j] = cu[f][j];
+                            cu[f][j] = zp[f][j];
+                            pc[f][j] = pn[f][j];
+                        }
+                }
+                advance_wait();
+                release_next();  // plane kz
+                kz_done = kz;
+            }
+            if (kz_done == K - 2) release_next();  // the top halo plane, read as z + 1 of the last plane
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
+        } else {
+            // no sites in this tile: keep the ring's count, plane by plane
+            for (int kk = 0; kk < K; ++kk) {
+                if (__any_sync(0xffffffffu, s_failed != 0)) break;
+                if (!wait_next()) s_failed = 1;
+                advance_wait();
+                release_next();
+            }
+        }
+        consumer_reduce_finalize<NQ, sizeof(T) == 4>(accd, m, c, sc, slots, item, nitems, nthr);
+        if (tid == 0) s_stop = s_failed;
+        asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
+        if (s_stop) break;
+    }
+}
+
+// The TMA pass for one tile per CTA (tile blockIdx.x of nitems).  Two fields
+// take tma_items, one or three fields tma_tile (the same tile, the same
+// numbers; the two compile differently and each measured faster where it is
+// used: one field 256^3 ... 512^3 0.069 / 0.205 / 0.418 ms against 0.103 /
+// 0.322 / 0.673, two fields 256^3 and 1024^3 0.106 and 5.384 ms against 0.114
+// and 5.42; three fields spill less in tma_tile).
+template <typename T, int NF, bool MEASURE, bool GLOBAL_MAPS = false>
+__device__ __forceinline__ void tma_one_tile(const Model &m, const FieldPtrs &fp, const PassCoef &c, int txt, int ty,
+                                             int zc, int S, int lpad, const TmaMaps *maps, Scalars *sc, double *slots,
+                                             unsigned item, unsigned nitems, int gx, int gy)
+{
+    if constexpr (NF != 2) {
+        const int bx = (int)(item % (unsigned)gx), by = (int)((item / (unsigned)gx) % (unsigned)gy);
+        const int bz = (int)(item / ((unsigned)gx * (unsigned)gy));
+        tma_tile<T, NF, MEASURE, GLOBAL_MAPS>(m, fp, c, txt, ty, zc, S, lpad, maps, sc, slots, bx, by, bz, item, nitems);
+    } else {
+        tma_items<T, NF, MEASURE, GLOBAL_MAPS>(m, fp, c, txt, ty, zc, S, lpad, maps, sc, slots, item, nitems, nitems, gx,
+                                               gy);
+    }
 }
 
 template <typename T, int NF, bool MEASURE, int NTHR>
 __global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
                                                          int S, int lpad, const __grid_constant__ TmaMaps maps,
-                                                         Scalars *sc, double *slots)
+                                                         Scalars *sc, double *slots, int gx, int gy, unsigned nitems)
 {
-    tma_tile<T, NF, MEASURE>(m, fp, c, txt, ty, zc, S, lpad, &maps, sc, slots, blockIdx.x, blockIdx.y, blockIdx.z,
-                             grid_bid(), grid_nblocks());
+    tma_one_tile<T, NF, MEASURE>(m, fp, c, txt, ty, zc, S, lpad, &maps, sc, slots, blockIdx.x, nitems, gx, gy);
 }
 
 // Batched form of the TMA pass: one CTA per (job, tile) item of all jobs of a
@@ -994,11 +1386,8 @@ __global__ void __launch_bounds__(256, 2) fused_pass_tma_group(const BatchJob *_
     __syncthreads();
     const BatchJob &j = jobs[s_job];
     const unsigned local = blockIdx.x - __ldg(first_item + s_job);
-    const int bx = (int)(local % (unsigned)j.gx);
-    const int by = (int)((local / (unsigned)j.gx) % (unsigned)j.gy);
-    const int bz = (int)(local / ((unsigned)j.gx * (unsigned)j.gy));
-    tma_tile<T, NF, false, true>(j.m, j.fp, c, j.txt, j.ty, j.zc, S, j.lpad, j.maps, j.sc, j.slots, bx, by, bz, local,
-                                 j.nblocks);
+    tma_one_tile<T, NF, false, true>(j.m, j.fp, c, j.txt, j.ty, j.zc, S, j.lpad, j.maps, j.sc, j.slots, local, j.nblocks,
+                                     j.gx, j.gy);
 }
 
 // The dynamic shared-memory limit of a kernel is a per-device attribute: raise
@@ -1031,10 +1420,16 @@ static cudaError_t launch_tma(const Model &m, const FieldPtrs &fp, const PassCoe
     // warps per SM, at most 4 per SM sub-partition, so 128 registers a thread
     static std::atomic<size_t> configured[kMaxDevices][2];
     const int big = g.cwarps > 7 ? 1 : 0;
+    const int threads = 32 * (g.cwarps + 1);
     auto kern = big ? fused_pass_tma<T, NF, MEASURE, 512> : fused_pass_tma<T, NF, MEASURE, 256>;
     cudaError_t e = ensure_smem_attribute(kern, g.smem, configured, big);
     if (e != cudaSuccess) return e;
-    kern<<<g.grid, 32 * (g.cwarps + 1), g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, g.stages, g.lpad, maps, sc, slots);
+    // one CTA per tile, in tile order: the hardware starts each CTA as an SM
+    // frees up, which keeps the CTAs in flight a compact band of neighbouring
+    // tiles (their halo rows meet in L2).  A persistent grid walking tiles b,
+    // b + grid, ... measured 11-25% slower: its CTAs drift apart.
+    kern<<<g.nblocks, threads, g.smem, s>>>(m, fp, c, g.txt, g.ty, g.zc, g.stages, g.lpad, maps, sc, slots,
+                                            (int)g.grid.x, (int)g.grid.y, g.nblocks);
     return cudaGetLastError();
 }
 

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
-DEFAULT_1024 = {"kind": "tma", "warps": 15, "stages": 6, "z_chunk": 92, "tile_x": 0, "threads": 0}
+DEFAULT_1024 = {"kind": "tma", "warps": 15, "stages": 6, "z_chunk": 76, "tile_x": 0, "threads": 0}
 
 
 def test_traffic_reported_exactly_when_summary_matches_sources_and_shape():

@@ -87,7 +87,7 @@ def test_each_shape_against_oracle_expanding_fp64(shape):
 def test_default_shape_and_errors():
     with T.Lattice(192, 0.5, 2, "f32") as big, T.Lattice(128, 0.5, 2, "f32") as small:
         cfg = big.pass_config()
-        assert cfg["kind"] == "tma" and cfg["warps"] == 7 and 3 <= cfg["stages"] <= 8 and cfg["z_chunk"] == 16
+        assert cfg["kind"] == "tma" and cfg["warps"] == 7 and 3 <= cfg["stages"] <= 8 and cfg["z_chunk"] == 48
         assert small.pass_config()["kind"] == "stream"
         with T.Lattice(256, 0.5, 1, "f32") as one:  # FP32 from 192: TMA, 64-plane chunks below 512
             c1 = one.pass_config()
@@ -151,7 +151,7 @@ def test_ragged_at_scale_tma_default_equals_stream():
     """N = 500, two FP32 fields: TMA shapes with ragged tiles in every direction (x tiles
     of 128 with a last one of 116 sites; 7 + 1 warps: y tiles of 7 rows with a last one
     of 3, z-chunks of 64 planes with a last one of 52; the default 15 + 1 warps: y tiles
-    of 15 rows with a last one of 5, z-chunks of 160 with a last one of 20); two Verlet
+    of 15 rows with a last one of 5, z-chunks of 96 with a last one of 20); two Verlet
     steps give bitwise the fields of the streaming kernel."""
     N, nf = 500, 2
     rng = np.random.default_rng(17)
@@ -165,7 +165,7 @@ def test_ragged_at_scale_tma_default_equals_stream():
                 lat.set_pass_config(**shape)
             else:
                 cfg = lat.pass_config()
-                assert (cfg["kind"], cfg["warps"], cfg["z_chunk"]) == ("tma", 15, 160)
+                assert (cfg["kind"], cfg["warps"], cfg["z_chunk"]) == ("tma", 15, 96)
             lat.set_potential(1.0, 10.0, (0.0, 0.2, 0.0))
             lat.set_state(phi, pi)
             lat.step(2, 0.01, "verlet")
