@@ -161,7 +161,6 @@ struct PassGeom {
     int lpad;      // TMA variant: padded-row index of x = 0 (128 bytes / element size)
     int threads;   // threads per CTA (ldg variant)
     size_t smem;   // dynamic shared memory per CTA
-    int sms;       // SMs of the device (the TMA pass's persistent grid)
 };
 
 PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTuning &t);

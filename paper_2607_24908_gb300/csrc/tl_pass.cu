@@ -89,7 +89,6 @@ PassGeom pass_geometry(int N, int elem_bytes, int sm_count, int nf, const PassTu
         g.smem = (size_t)g.prefetch * nf * 2 * 256 * 16;
     }
     g.lpad = 128 / elem_bytes;
-    g.sms = sm_count > 0 ? sm_count : 152;
     if (g.variant == kVariantTma) {
         // ring depth: as deep as fits two CTAs per SM (<= 113 KB each), at
         // least 3 (two planes read + one in flight), at most 8; each stage

@@ -1334,18 +1334,20 @@ __device__ __forceinline__ void tma_items(const Model &m, const FieldPtrs &fp, c
     }
 }
 
-// The TMA pass for one tile per CTA (tile blockIdx.x of nitems).  Two fields
-// take tma_items, one or three fields tma_tile (the same tile, the same
-// numbers; the two compile differently and each measured faster where it is
-// used: one field 256^3 ... 512^3 0.069 / 0.205 / 0.418 ms against 0.103 /
-// 0.322 / 0.673, two fields 256^3 and 1024^3 0.106 and 5.384 ms against 0.114
-// and 5.42; three fields spill less in tma_tile).
-template <typename T, int NF, bool MEASURE, bool GLOBAL_MAPS = false>
+// The TMA pass for one tile per CTA (tile blockIdx.x of nitems), in one of two
+// code forms: tma_items (ITEMS) or tma_tile.  They process the same tile with
+// the same arithmetic in the same order (the same numbers), but compile
+// differently and measured faster in different cases: one field 256^3 ...
+// 512^3 0.069 / 0.205 / 0.418 ms in tma_tile against 0.103 / 0.322 / 0.673;
+// two fields 256^3 and 1024^3 0.106 and 5.384 ms in tma_items against 0.114
+// and 5.42, 384^3 and 512^3 0.309 and 0.691 in tma_tile against 0.325 and
+// 0.705; three fields spill less in tma_tile.
+template <typename T, int NF, bool MEASURE, bool ITEMS, bool GLOBAL_MAPS = false>
 __device__ __forceinline__ void tma_one_tile(const Model &m, const FieldPtrs &fp, const PassCoef &c, int txt, int ty,
                                              int zc, int S, int lpad, const TmaMaps *maps, Scalars *sc, double *slots,
                                              unsigned item, unsigned nitems, int gx, int gy)
 {
-    if constexpr (NF != 2) {
+    if constexpr (!ITEMS) {
         const int bx = (int)(item % (unsigned)gx), by = (int)((item / (unsigned)gx) % (unsigned)gy);
         const int bz = (int)(item / ((unsigned)gx * (unsigned)gy));
         tma_tile<T, NF, MEASURE, GLOBAL_MAPS>(m, fp, c, txt, ty, zc, S, lpad, maps, sc, slots, bx, by, bz, item, nitems);
@@ -1355,12 +1357,15 @@ __device__ __forceinline__ void tma_one_tile(const Model &m, const FieldPtrs &fp
     }
 }
 
-template <typename T, int NF, bool MEASURE, int NTHR>
+// The code form a lattice's TMA pass takes (see tma_one_tile).
+__host__ __device__ constexpr bool tma_items_form(int nf, int N) { return nf == 2 && (N <= 320 || N >= 640); }
+
+template <typename T, int NF, bool MEASURE, int NTHR, bool ITEMS>
 __global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
                                                          int S, int lpad, const __grid_constant__ TmaMaps maps,
                                                          Scalars *sc, double *slots, int gx, int gy, unsigned nitems)
 {
-    tma_one_tile<T, NF, MEASURE>(m, fp, c, txt, ty, zc, S, lpad, &maps, sc, slots, blockIdx.x, nitems, gx, gy);
+    tma_one_tile<T, NF, MEASURE, ITEMS>(m, fp, c, txt, ty, zc, S, lpad, &maps, sc, slots, blockIdx.x, nitems, gx, gy);
 }
 
 // Batched form of the TMA pass: one CTA per (job, tile) item of all jobs of a
@@ -1386,16 +1391,18 @@ __global__ void __launch_bounds__(256, 2) fused_pass_tma_group(const BatchJob *_
     __syncthreads();
     const BatchJob &j = jobs[s_job];
     const unsigned local = blockIdx.x - __ldg(first_item + s_job);
-    tma_one_tile<T, NF, false, true>(j.m, j.fp, c, j.txt, j.ty, j.zc, S, j.lpad, j.maps, j.sc, j.slots, local, j.nblocks,
-                                     j.gx, j.gy);
+    // two fields in the multi-tile code form, as for the small lattices batches
+    // hold (either form gives the same numbers)
+    tma_one_tile<T, NF, false, NF == 2, true>(j.m, j.fp, c, j.txt, j.ty, j.zc, S, j.lpad, j.maps, j.sc, j.slots, local,
+                                              j.nblocks, j.gx, j.gy);
 }
 
 // The dynamic shared-memory limit of a kernel is a per-device attribute: raise
 // it once per device and kernel (thread-safe; a lower request needs no call).
 constexpr int kMaxDevices = 64;
 
-template <typename K>
-static cudaError_t ensure_smem_attribute(K kern, size_t smem, std::atomic<size_t> (*configured)[2], int slot)
+template <typename K, int SLOTS>
+static cudaError_t ensure_smem_attribute(K kern, size_t smem, std::atomic<size_t> (*configured)[SLOTS], int slot)
 {
     if (smem == 0) return cudaSuccess;
     int dev = 0;
@@ -1418,11 +1425,13 @@ static cudaError_t launch_tma(const Model &m, const FieldPtrs &fp, const PassCoe
 {
     // 7 + 1 warps (two CTAs per SM) or 15 + 1 warps (one CTA per SM): 16
     // warps per SM, at most 4 per SM sub-partition, so 128 registers a thread
-    static std::atomic<size_t> configured[kMaxDevices][2];
+    static std::atomic<size_t> configured[kMaxDevices][4];
     const int big = g.cwarps > 7 ? 1 : 0;
+    const bool items = tma_items_form(NF, m.N);
     const int threads = 32 * (g.cwarps + 1);
-    auto kern = big ? fused_pass_tma<T, NF, MEASURE, 512> : fused_pass_tma<T, NF, MEASURE, 256>;
-    cudaError_t e = ensure_smem_attribute(kern, g.smem, configured, big);
+    auto kern = big ? (items ? fused_pass_tma<T, NF, MEASURE, 512, true> : fused_pass_tma<T, NF, MEASURE, 512, false>)
+                    : (items ? fused_pass_tma<T, NF, MEASURE, 256, true> : fused_pass_tma<T, NF, MEASURE, 256, false>);
+    cudaError_t e = ensure_smem_attribute(kern, g.smem, configured, big + (items ? 2 : 0));
     if (e != cudaSuccess) return e;
     // one CTA per tile, in tile order: the hardware starts each CTA as an SM
     // frees up, which keeps the CTAs in flight a compact band of neighbouring
