@@ -979,8 +979,15 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
         adv_w();
         if (!ok) s_failed = 1;
         release(0);
-        for (int z = z0; z < z1; ++z) {
-            if (__any_sync(0xffffffffu, s_failed != 0)) break;  // warp-uniform exit
+        // blocks of 16 planes: after each, the FP32 energy sums go into FP64
+        bool stop = false;
+        for (int zb = z0; zb < z1 && !stop; zb += 16) {
+        const int ze = min(zb + 16, z1);
+        for (int z = zb; z < ze; ++z) {
+            if (__any_sync(0xffffffffu, s_failed != 0)) {  // warp-uniform exit
+                stop = true;
+                break;
+            }
             const int kz = z - z0 + 1;
             if (active) {
                 if (!mbar_wait_bounded(&full[ws], wph, sc)) s_failed = 1;
@@ -1017,13 +1024,6 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
                     }
                     if (m.ghosts) store_ghosts<T, NF, W>(pho, pio, cu, pnew, pz, x0, y, N, (long long)P);
                 }
-                if (((z - z0) & 15) == 15) {
-#pragma unroll
-                    for (int i = 0; i < NQ; ++i) {
-                        accd[i] += (double)acc[i];
-                        acc[i] = (T)0;
-                    }
-                }
 #pragma unroll
                 for (int f = 0; f < NF; ++f)
 #pragma unroll
@@ -1035,6 +1035,12 @@ __device__ __forceinline__ void tma_tile(const Model &m, const FieldPtrs &fp, co
             }
             adv_w();
             release(kz);
+        }
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            accd[i] += (double)acc[i];
+            acc[i] = (T)0;
+        }
         }
 #pragma unroll
         for (int i = 0; i < NQ; ++i) accd[i] += (double)acc[i];
