@@ -1345,9 +1345,10 @@ __device__ __forceinline__ void tma_items(const Model &m, const FieldPtrs &fp, c
 // the same arithmetic in the same order (the same numbers), but compile
 // differently and measured faster in different cases: one field 256^3 ...
 // 512^3 0.069 / 0.205 / 0.418 ms in tma_tile against 0.103 / 0.322 / 0.673;
-// two fields 256^3 and 1024^3 0.106 and 5.384 ms in tma_items against 0.114
-// and 5.42, 384^3 and 512^3 0.309 and 0.691 in tma_tile against 0.325 and
-// 0.705; three fields spill less in tma_tile.
+// two fields 256^3, 640^3 and 1024^3 0.106, 1.329 and 5.397 ms in tma_items
+// against 0.111, 1.332 and 5.453, 320^3, 384^3 and 512^3 0.219, 0.309 and
+// 0.691 in tma_tile against 0.244, 0.325 and 0.705; three fields spill less
+// in tma_tile.
 template <typename T, int NF, bool MEASURE, bool ITEMS, bool GLOBAL_MAPS = false>
 __device__ __forceinline__ void tma_one_tile(const Model &m, const FieldPtrs &fp, const PassCoef &c, int txt, int ty,
                                              int zc, int S, int lpad, const TmaMaps *maps, Scalars *sc, double *slots,
@@ -1364,7 +1365,7 @@ __device__ __forceinline__ void tma_one_tile(const Model &m, const FieldPtrs &fp
 }
 
 // The code form a lattice's TMA pass takes (see tma_one_tile).
-__host__ __device__ constexpr bool tma_items_form(int nf, int N) { return nf == 2 && (N <= 320 || N >= 640); }
+__host__ __device__ constexpr bool tma_items_form(int nf, int N) { return nf == 2 && (N <= 256 || N >= 640); }
 
 template <typename T, int NF, bool MEASURE, int NTHR, bool ITEMS>
 __global__ void __launch_bounds__(NTHR, (NTHR <= 256 ? 2 : 1)) fused_pass_tma(Model m, FieldPtrs fp, PassCoef c, int txt, int ty, int zc,
