@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -209,7 +210,7 @@ int finish_create(tl_lattice *L, int N, double kIR, int nf, tl_dtype dtype, cons
     L->tuning = tl::default_tuning(N, nf, (int)L->esz);
     L->geom = tl::pass_geometry(N, (int)L->esz, L->sm_count, nf, L->tuning);
     TL_CK(cudaMalloc(&L->d_sc, sizeof(Scalars)));
-    TL_CK(cudaMemset(L->d_sc, 0, sizeof(Scalars)));
+    TL_CK(cudaMemsetAsync(L->d_sc, 0, sizeof(Scalars), L->stream));
     TL_CK(cudaMalloc(&L->d_slots, sizeof(double) * tl::kMaxQ * L->geom.nblocks));
     L->slots_cap = L->geom.nblocks;
     refresh_model(L);
@@ -283,25 +284,39 @@ int check_field(const tl_lattice *L, int field, int which)
     return TL_OK;
 }
 
-// cuFFT plans shared by all lattices of a size (planning costs milliseconds
-// and a workspace per plan); a plan is bound to the caller's stream for each
-// execution under this mutex.
-std::mutex g_plan_mu;
-std::map<std::pair<int, int>, cufftHandle> g_plans;  // (N, cufftType) -> plan
-
-int shared_plan(int N, cufftType type, cufftHandle *out)
-{
-    auto key = std::make_pair(N, (int)type);
-    auto it = g_plans.find(key);
-    if (it != g_plans.end()) {
-        *out = it->second;
-        return TL_OK;
-    }
+// cuFFT plans shared by all lattices of a size on a device (planning costs
+// milliseconds and a workspace per plan).  Under this mutex a plan is bound
+// to the caller's stream, which first waits for the plan's previous
+// executions (on whatever stream they were enqueued) through the plan's
+// event; the caller records that event after its last execution.  Calls that
+// use a plan therefore only enqueue work: no host wait guards the workspace.
+struct SharedPlan {
     cufftHandle h;
-    cufftResult r = cufftPlan3d(&h, N, N, N, type);
-    if (r != CUFFT_SUCCESS) return fail(TL_ECUDA, "cufftPlan3d(%d) failed (%d)", N, (int)r);
-    g_plans[key] = h;
-    *out = h;
+    cudaEvent_t done;  // recorded after the latest enqueued execution
+};
+std::mutex g_plan_mu;
+std::map<std::tuple<int, int, int>, SharedPlan> g_plans;  // (device, N, cufftType) -> plan
+
+int shared_plan(int N, cufftType type, cudaStream_t s, SharedPlan **out)
+{
+    int dev = 0;
+    TL_CK(cudaGetDevice(&dev));
+    auto key = std::make_tuple(dev, N, (int)type);
+    auto it = g_plans.find(key);
+    if (it == g_plans.end()) {
+        SharedPlan p{};
+        cufftResult r = cufftPlan3d(&p.h, N, N, N, type);
+        if (r != CUFFT_SUCCESS) return fail(TL_ECUDA, "cufftPlan3d(%d) failed (%d)", N, (int)r);
+        cudaError_t e = cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cufftDestroy(p.h);
+            return fail(TL_ECUDA, "cudaEventCreateWithFlags: %s", cudaGetErrorString(e));
+        }
+        it = g_plans.emplace(key, p).first;
+    }
+    TL_CKFFT(cufftSetStream(it->second.h, s));
+    TL_CK(cudaStreamWaitEvent(s, it->second.done, 0));  // a never-recorded event: no wait
+    *out = &it->second;
     return TL_OK;
 }
 
@@ -767,12 +782,12 @@ int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
     const size_t n3 = n3_of(N);
     const size_t nh = (size_t)N * N * (N / 2 + 1);
     std::lock_guard<std::mutex> plan_lock(g_plan_mu);
-    cufftHandle plan;
+    SharedPlan *sp = nullptr;
     {
-        int prc = shared_plan(N, CUFFT_Z2D, &plan);
+        int prc = shared_plan(N, CUFFT_Z2D, L->stream, &sp);
         if (prc) return prc;
     }
-    TL_CKFFT(cufftSetStream(plan, L->stream));
+    const cufftHandle plan = sp->h;
     double2 *modes = nullptr;
     double *real = nullptr;
     TL_CK(cudaMallocAsync((void **)&modes, nh * sizeof(double2), L->stream));
@@ -806,6 +821,10 @@ int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
             }
         }
     }
+    {
+        const cudaError_t re = cudaEventRecord(sp->done, L->stream);  // after this call's executions
+        if (re != cudaSuccess && rc == TL_OK) rc = fail(TL_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(re));
+    }
     cudaFreeAsync(modes, L->stream);
     cudaFreeAsync(real, L->stream);
     if (rc) return rc;
@@ -818,10 +837,7 @@ int tl_init_fluctuations(tl_lattice *L, uint64_t seed, const tl_init_spec *spec)
     L->step = 0;
     L->langevin_steps = 0;
     TL_CK(tl::launch_set_background(L->model, L->d_sc, L->ex.a0, 0.0, L->stream));
-    rc = measure(L, expanding);
-    if (rc) return rc;
-    TL_CK(cudaStreamSynchronize(L->stream));
-    return TL_OK;
+    return measure(L, expanding);
 }
 
 int tl_spectrum(tl_lattice *L, int field, int which, int nbins, double *k, double *P, int64_t *count)
@@ -836,12 +852,12 @@ int tl_spectrum(tl_lattice *L, int field, int which, int nbins, double *k, doubl
     const size_t n3 = n3_of(N);
     const size_t nh = (size_t)N * N * (N / 2 + 1);
     std::lock_guard<std::mutex> plan_lock(g_plan_mu);
-    cufftHandle plan;
+    SharedPlan *sp = nullptr;
     {
-        int prc = shared_plan(N, CUFFT_D2Z, &plan);
+        int prc = shared_plan(N, CUFFT_D2Z, L->stream, &sp);
         if (prc) return prc;
     }
-    TL_CKFFT(cufftSetStream(plan, L->stream));
+    const cufftHandle plan = sp->h;
     double2 *modes = nullptr;
     double *real = nullptr, *acc = nullptr;
     TL_CK(cudaMallocAsync((void **)&modes, nh * sizeof(double2), L->stream));
@@ -852,6 +868,7 @@ int tl_spectrum(tl_lattice *L, int field, int which, int nbins, double *k, doubl
                            L->sm_count, L->stream));
     cufftResult fr = cufftExecD2Z(plan, real, reinterpret_cast<cufftDoubleComplex *>(modes));
     if (fr != CUFFT_SUCCESS) return fail(TL_ECUDA, "cufftExecD2Z failed (%d)", (int)fr);
+    TL_CK(cudaEventRecord(sp->done, L->stream));
     TL_CK(tl::launch_bin(modes, N, nb, acc, acc + nb, reinterpret_cast<unsigned long long *>(acc + 2 * nb),
                          L->sm_count, L->stream));
     std::vector<double> h((size_t)nb * 3);

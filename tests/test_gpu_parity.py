@@ -169,6 +169,40 @@ def test_init_fluctuations_two_fields_parity(dtype, fixed):
     assert E.hubble_resid < 1e-12
 
 
+def test_inits_on_two_streams_share_one_plan():
+    """tl_init_fluctuations only enqueues work; lattices of one size on two
+    streams share one cuFFT plan (and its workspace), each execution ordered
+    after the previous one by the plan's event.  Four inits enqueued back to
+    back, alternating streams, then a spectrum of each: bitwise the results of
+    one lattice at a time."""
+    import torch
+    N, seeds = 96, (31, 32, 33, 34)
+
+    def run(lat, seed):
+        lat.set_potential(1.0, 10.0, (0.0, 0.0, 0.0))
+        lat.init_fluctuations(seed, A=1e-8, meff2=(3.0, 10.0, 0.0), phi0=(1.0, 0.0, 0.0))
+
+    ref = []
+    for sd in seeds:
+        with T.Lattice(N, 0.5, 2, "f64", True, 1.0, 1.0, 1.0) as lat:
+            run(lat, sd)
+            ref.append((lat.get_all(), lat.spectrum(1, 1)[1]))
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    lats = [T.Lattice(N, 0.5, 2, "f64", True, 1.0, 1.0, 1.0, stream=streams[i % 2].cuda_stream)
+            for i in range(len(seeds))]
+    try:
+        for lat, sd in zip(lats, seeds):
+            run(lat, sd)
+        spectra = [lat.spectrum(1, 1)[1] for lat in lats]
+        for lat, P, ((rphi, rpi), rP) in zip(lats, spectra, ref):
+            phi, pi = lat.get_all()
+            assert np.array_equal(phi, rphi) and np.array_equal(pi, rpi)
+            assert np.array_equal(P, rP)
+    finally:
+        for lat in lats:
+            lat.close()
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_spectrum_parity(dtype):
     p = o.Params(N=48, nf=1, kIR=0.1)
