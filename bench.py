@@ -343,16 +343,16 @@ def run_ours(args):
     lat.set_potential(WL.lam, WL.q, WL.m2)
     lat.init_fluctuations(replica_seed(rank), A=WL.A, meff2=WL.meff2, phi0=WL.phi0)
     args.pass_shape = lat.pass_config()
-    # the end-to-end leg's pinned host buffers, allocated and touched now: pinning
-    # tens of GB makes the host rearrange memory for a while, which would slow the
-    # transfers if it happened inside that leg's timed region
+    # the end-to-end leg's page-locked host buffers (tl_host_alloc: huge pages,
+    # registered), allocated and touched now: pinning tens of GB makes the host
+    # rearrange memory for a while, which would slow the transfers if it
+    # happened inside that leg's timed region
     host = []
     if not args.no_e2e:
-        host = [torch.empty((N,) * 3, dtype=torch.float32 if WL.dtype == "f32" else torch.float64,
-                            pin_memory=True) for _ in range(2 * WL.nf)]
+        host = [T.host_empty((N,) * 3, np.float32 if WL.dtype == "f32" else np.float64) for _ in range(2 * WL.nf)]
         for f in range(WL.nf):
             for w in range(2):
-                T.tl_get_state(lat.h, f, w, host[2 * f + w].numpy())
+                T.tl_get_state(lat.h, f, w, host[2 * f + w])
 
     # warm-up: W steps (one call each)
     for _ in range(args.warmup):
@@ -383,7 +383,7 @@ def run_ours(args):
     value = job_value(work_per_rank, ws, t_max)
 
     # end-to-end through the C ABI with host buffers: H2D of the state from
-    # pinned memory, K steps, energies and D2H of the state, every call inside
+    # page-locked memory (tl_host_alloc), K steps, energies and D2H of the state, every call inside
     # the timed region; three such jobs, the median reported (the host link's
     # speed varies between jobs on a busy host; all three are in the phases).
     npd = np.float32 if WL.dtype == "f32" else np.float64
@@ -396,14 +396,14 @@ def run_ours(args):
     runs = []
     for f in range(WL.nf):  # the state the first job starts from
         for w in range(2):
-            T.tl_get_state(lat.h, f, w, host[2 * f + w].numpy())
+            T.tl_get_state(lat.h, f, w, host[2 * f + w])
     a_in, b_in = E.a, E.b
     for rep in range(3):  # each job continues from the previous job's returned state
         barrier()
         t0 = time.perf_counter()
         for f in range(WL.nf):
             for w in range(2):
-                T.tl_set_state(lat.h, f, w, host[2 * f + w].numpy())
+                T.tl_set_state(lat.h, f, w, host[2 * f + w])
         T.tl_set_background(lat.h, a_in, b_in, False)
         t1 = time.perf_counter()
         lat.step(args.steps, WL.dt, integ)
@@ -411,7 +411,7 @@ def run_ours(args):
         t2 = time.perf_counter()
         for f in range(WL.nf):
             for w in range(2):
-                T.tl_get_state(lat.h, f, w, host[2 * f + w].numpy())
+                T.tl_get_state(lat.h, f, w, host[2 * f + w])
         t3 = time.perf_counter()
         runs.append({"total_s": t3 - t0, "set_state_s": t1 - t0, "steps_and_energies_s": t2 - t1,
                      "get_state_s": t3 - t2})
@@ -459,7 +459,8 @@ def _report(args, ws, rank, N, ms, t_max, ms_pass, launches, value, work_per_ran
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "site-updates/s", "h2d_bytes_per_step": state_bytes / args.steps,
                     "d2h_bytes_per_step": (state_bytes + 136) / args.steps,
-                    "note": "state H2D once, K steps, energies + state D2H, per K-step job; median of 3 jobs",
+                    "note": "state H2D once from tl_host_alloc memory, K steps, energies + state D2H, per K-step job; "
+                            "median of 3 jobs",
                     "phases": getattr(args, "e2e_phases", None)},
             "gpu_launches": launches,
             "clocks": clk,

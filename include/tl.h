@@ -284,6 +284,22 @@ int tl_energies_noalloc(int N, double kIR, int n_fields, tl_dtype dtype, const t
                         const tl_expansion *expansion, double a, const void *const *phi, const void *const *pi,
                         void *cuda_stream, double *out);
 
+/* Page-locked host memory for the state copies (tl_get_state, tl_set_state,
+ * tl_su2_get/set and any cudaMemcpy of the caller): anonymous memory with
+ * transparent huge pages requested (start and length aligned to the huge
+ * page size for buffers of at least one), every page faulted in, and the
+ * range registered with CUDA (cudaHostRegister), so that copies run at the
+ * host link's rate.  *out receives a pointer to `bytes` writable bytes
+ * (zero-filled), owned by the caller until tl_host_free.  No counterpart in
+ * the paper.  Errors: TL_EINVAL (NULL out, bytes 0), TL_ENOMEM (the mapping
+ * failed), TL_ECUDA (registration failed; nothing is left allocated). */
+int tl_host_alloc(size_t bytes, void **out);
+
+/* Unregister and unmap memory from tl_host_alloc; NULL is a no-op.  The
+ * caller must have no copy in flight on it.  Errors: TL_EINVAL (a pointer
+ * tl_host_alloc did not return, or one already freed), TL_ECUDA. */
+int tl_host_free(void *ptr);
+
 /* ---- Langevin evolution (Sec. 2, Eq. 1: the paper's interface example) ---- */
 
 typedef struct {

@@ -106,6 +106,8 @@ _SIGS = {
                                            ctypes.c_double, ctypes.POINTER(ctypes.c_void_p),
                                            ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
                                            ctypes.POINTER(ctypes.c_double)]),
+    "tl_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)]),
+    "tl_host_free": (ctypes.c_int, [ctypes.c_void_p]),
     "tl_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                        ctypes.c_void_p]),
     "tl_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
@@ -277,6 +279,43 @@ def tl_energies_noalloc(N: int, kIR: float, n_fields: int, dtype: int, lam: floa
                                      ctypes.byref(expansion) if expansion is not None else None, a, ph, pp,
                                      ctypes.c_void_p(cuda_stream), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def tl_host_alloc(nbytes: int) -> int:
+    p = ctypes.c_void_p()
+    _check(lib().tl_host_alloc(nbytes, ctypes.byref(p)))
+    return int(p.value)
+
+
+def tl_host_free(ptr: int):
+    _check(lib().tl_host_free(ctypes.c_void_p(ptr)))
+
+
+class _HostBuffer:
+    """Bytes from tl_host_alloc, freed when the last numpy view of them goes."""
+
+    def __init__(self, nbytes: int):
+        self.nbytes = nbytes
+        self.ptr = tl_host_alloc(nbytes)
+        self.__array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (self.ptr, False),
+                                    "version": 3}
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            tl_host_free(self.ptr)
+            self.ptr = None
+
+
+def host_empty(shape, dtype) -> np.ndarray:
+    """A numpy array in page-locked host memory from tl_host_alloc (huge pages
+    where the kernel grants them), for state copies at the host link's rate;
+    zero-filled.  The memory lives as long as the array or any view of it."""
+    dtype = np.dtype(dtype)
+    shape = tuple(int(x) for x in np.atleast_1d(shape))
+    nbytes = int(np.prod(shape, dtype=np.int64)) * dtype.itemsize
+    if nbytes == 0:
+        return np.zeros(shape, dtype)
+    return np.asarray(_HostBuffer(nbytes)).view(dtype).reshape(shape)
 
 
 def tl_langevin_step(h, n: int, dt: float, lam: float, m2: float, noise: float, seed: int):

@@ -62,6 +62,27 @@ def test_create_without_gpu_fails_cleanly():
     assert e.value.code == tl.EINVAL
 
 
+def test_host_alloc_argument_errors_and_no_gpu():
+    """tl_host_alloc / tl_host_free: argument errors on any machine; without a
+    GPU the registration fails with TL_ECUDA and nothing stays allocated."""
+    import ctypes
+    import torch
+    from paper_2607_24908_gb300 import tl
+    with pytest.raises(tl.TLError) as e:
+        tl.tl_host_alloc(0)
+    assert e.value.code == tl.EINVAL
+    tl.tl_host_free(0)  # NULL is a no-op
+    junk = ctypes.create_string_buffer(64)
+    with pytest.raises(tl.TLError) as e:
+        tl.tl_host_free(ctypes.addressof(junk))
+    assert e.value.code == tl.EINVAL
+    assert tl.host_empty((0, 4), np.float32).shape == (0, 4)
+    if not torch.cuda.is_available():
+        with pytest.raises(tl.TLError) as e:
+            tl.host_empty((1 << 20,), np.float32)
+        assert e.value.code == tl.ECUDA
+
+
 def test_serving_job_generator_and_budget_arithmetic():
     """Host-side pieces of the server that need no GPU."""
     from paper_2607_24908_gb300 import serve as S
