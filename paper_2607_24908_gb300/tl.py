@@ -301,9 +301,12 @@ class _HostBuffer:
                                     "version": 3}
 
     def __del__(self):
-        if getattr(self, "ptr", None):
-            tl_host_free(self.ptr)
-            self.ptr = None
+        ptr, self.ptr = getattr(self, "ptr", None), None
+        if ptr:
+            try:
+                tl_host_free(ptr)
+            except Exception:  # at interpreter exit the CUDA context may be gone first
+                pass
 
 
 def host_empty(shape, dtype) -> np.ndarray:
