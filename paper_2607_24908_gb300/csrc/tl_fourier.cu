@@ -6,28 +6,10 @@
 #include <math.h>
 
 #include "tl_fourier.cuh"
+#include "tl_philox.cuh"
 
 namespace tl {
 
-// Philox-2x64 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): per round
-// the first counter word is multiplied by the published 64-bit multiplier;
-// the new first word is hi(product) xor key xor second word, the new second
-// word lo(product); the key advances by the published Weyl increment.
-__device__ __forceinline__ void philox2x64_10(uint64_t c0, uint64_t c1, uint64_t key, uint64_t &o0, uint64_t &o1)
-{
-    const uint64_t M = 0xD2B74407B1CE6E93ULL;
-    const uint64_t Wk = 0x9E3779B97F4A7C15ULL;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint64_t hi = __umul64hi(M, c0);
-        const uint64_t lo = M * c0;
-        c0 = hi ^ key ^ c1;
-        c1 = lo;
-        key += Wk;
-    }
-    o0 = c0;
-    o1 = c1;
-}
 
 __device__ __forceinline__ int signed_mode(int i, int N) { return (i < N / 2) ? i : i - N; }
 

@@ -17,25 +17,11 @@
 
 #include "tl_internal.cuh"
 #include "tl_lattice.cuh"
+#include "tl_philox.cuh"
 
 namespace {
 
-// Philox-2x64 with 10 rounds (Salmon et al., SC'11), as in the initial-state draw.
-__device__ __forceinline__ void philox2x64_10(uint64_t c0, uint64_t c1, uint64_t key, uint64_t &o0, uint64_t &o1)
-{
-    const uint64_t M = 0xD2B74407B1CE6E93ULL;
-    const uint64_t Wk = 0x9E3779B97F4A7C15ULL;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint64_t hi = __umul64hi(M, c0);
-        const uint64_t lo = M * c0;
-        c0 = hi ^ key ^ c1;
-        c1 = lo;
-        key += Wk;
-    }
-    o0 = c0;
-    o1 = c1;
-}
+using tl::philox2x64_10;  // the initial-state draw's generator
 
 // The two Gaussians of draw k: (cos, sin) halves of Box-Muller.
 template <typename T>

@@ -22,6 +22,7 @@
 
 #include "tl_internal.cuh"
 #include "tl_lattice.cuh"
+#include "tl_philox.cuh"
 
 namespace {
 
@@ -443,19 +444,6 @@ __global__ void su2_sum_slots(const double *slots, int nblocks, double inv_n3, d
     out[3] = sqrt(g2 * inv_n3);
 }
 
-// Philox-2x64-10 (Salmon et al., SC'11), for random initial links.
-__device__ __forceinline__ void philox(uint64_t c0, uint64_t c1, uint64_t key, uint64_t &o0, uint64_t &o1)
-{
-    const uint64_t M = 0xD2B74407B1CE6E93ULL, Wk = 0x9E3779B97F4A7C15ULL;
-    for (int r = 0; r < 10; ++r) {
-        const uint64_t hi = __umul64hi(M, c0), lo = M * c0;
-        c0 = hi ^ key ^ c1;
-        c1 = lo;
-        key += Wk;
-    }
-    o0 = c0;
-    o1 = c1;
-}
 
 template <typename T>
 __global__ void su2_init(T *U, T *E, int N, uint64_t seed, double amp)
@@ -466,7 +454,7 @@ __global__ void su2_init(T *U, T *E, int N, uint64_t seed, double amp)
             double g[4];
             for (int h = 0; h < 2; ++h) {
                 uint64_t w0, w1;
-                philox(3 * s + i, (1ull << 62) + h, seed, w0, w1);
+                tl::philox2x64_10(3 * s + i, (1ull << 62) + h, seed, w0, w1);  // random initial links
                 const double u1 = ((double)(w0 >> 11) + 1.0) / 9007199254740992.0;
                 const double u2 = (double)(w1 >> 11) / 9007199254740992.0;
                 const double r = sqrt(-2.0 * log(u1));
