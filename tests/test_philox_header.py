@@ -1,8 +1,10 @@
 """The library's Philox-2x64-10 (csrc/tl_philox.cuh, the generator of the
 initial fields, the Langevin noise and the random SU(2) links) compiled for
 the host and checked against the generator's published known answers
-(tests/golden/philox2x64_10_kat.json); its 128-bit product against Python's
-integers.  CPU only: the header is plain integer arithmetic."""
+(tests/golden/philox2x64_10_kat.json): the rounds, constants and word order
+that the device shares; its host 128-bit product against Python's integers.
+CPU only (the device's product, __umul64hi and a 64-bit multiply, is checked
+bitwise through the GPU parity tests of the initial fields and the noise)."""
 import json
 import os
 import random
