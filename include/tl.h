@@ -288,8 +288,9 @@ int tl_energies_noalloc(int N, double kIR, int n_fields, tl_dtype dtype, const t
  * tl_su2_get/set and any cudaMemcpy of the caller): anonymous memory with
  * transparent huge pages requested (start and length aligned to the huge
  * page size for buffers of at least one), every page faulted in, and the
- * range registered with CUDA (cudaHostRegister), so that copies run at the
- * host link's rate.  *out receives a pointer to `bytes` writable bytes
+ * range registered with CUDA (cudaHostRegister): one address translation per
+ * huge page instead of per base page for the copies (their measured rates
+ * against cudaHostAlloc memory varied between hosts).  *out receives a pointer to `bytes` writable bytes
  * (zero-filled), owned by the caller until tl_host_free.  No counterpart in
  * the paper.  Errors: TL_EINVAL (NULL out, bytes 0), TL_ENOMEM (the mapping
  * failed), TL_ECUDA (registration failed; nothing is left allocated). */

@@ -1,15 +1,15 @@
 // tl_host_alloc / tl_host_free: page-locked host memory for state copies.
 //
-// Copies between the device and page-locked host memory run at the host
-// link's rate only when the device's address translation keeps up; host memory
-// pinned in base pages (what cudaHostAlloc returns) needs one translation per
-// page, and copies of such memory were measured to drop well below the link's
-// rate from time to time (135-168 GB/s against 211 GB/s host to device), while
-// memory of the same size on transparent huge pages did not.  So this allocator maps anonymous memory,
-// asks for transparent huge pages (madvise), faults every page in, and
-// registers the range with CUDA (cudaHostRegister), which pins it.  Where the
-// kernel grants no huge pages the memory is still pinned and correct, only
-// without that benefit.
+// Host memory pinned in base pages (what cudaHostAlloc returns) needs one
+// address translation per page for the device's copies; on transparent huge
+// pages one translation covers a whole huge page.  This allocator maps
+// anonymous memory, asks for transparent huge pages (madvise), faults every
+// page in, and registers the range with CUDA (cudaHostRegister), which pins
+// it.  Where the kernel grants no huge pages the memory is still pinned and
+// correct.  Measured copy rates of such buffers against cudaHostAlloc ones
+// varied from one host to the next (at the link's full rate in every repeat
+// where cudaHostAlloc buffers dipped, and the other way round elsewhere), so
+// this is an option for callers, not a guarantee of the link's rate.
 #include <stdint.h>
 #include <stdio.h>
 #include <sys/mman.h>

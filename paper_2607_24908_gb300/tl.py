@@ -311,7 +311,7 @@ class _HostBuffer:
 
 def host_empty(shape, dtype) -> np.ndarray:
     """A numpy array in page-locked host memory from tl_host_alloc (huge pages
-    where the kernel grants them), for state copies at the host link's rate;
+    where the kernel grants them), for state copies to and from the device;
     zero-filled.  The memory lives as long as the array or any view of it."""
     dtype = np.dtype(dtype)
     shape = tuple(int(x) for x in np.atleast_1d(shape))
