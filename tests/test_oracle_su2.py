@@ -3,7 +3,6 @@ Gauss-law preservation, O(dt^2) energy conservation, gauge covariance,
 unitarity, and the abelian (compact U(1)) reduction written independently
 with angles."""
 import numpy as np
-import pytest
 
 import oracle.su2 as Y
 from paper_2607_24908_gb300.workloads import random_su2_gauge, random_su2_links
